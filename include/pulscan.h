@@ -1,0 +1,183 @@
+/*
+ * pulscan.h -- C ABI of the GB300 boxcar (unmatched-filter) search.
+ *
+ * The library runs the data-parallel hot path of the Pulscan binary-pulsar
+ * search (White et al., arXiv 2406.15186) on one NVIDIA GB300 (sm_103a):
+ *
+ *   real time series --R2C FFT--> complex spectrum            (§2.2.2)
+ *   --per-block median/MAD normalisation, |X|^2 / 2--> power  (§2.2.3, Eq. 8)
+ *   --boxcar sums of every width 1..z_max at every bin-->     (§2.2.5)
+ *   --per-(segment, width) maximum and chi-square threshold--> (Algorithm 4, Eq. 9)
+ *   candidates (series, width, start bin, power, sigma).
+ *
+ * Conventions used by every entry point:
+ *  - Pointers prefixed d_ are DEVICE pointers owned by the caller; h_ are host
+ *    pointers owned by the caller.  The plan owns its own scratch (threshold
+ *    table, block statistics, per-(segment, width) slots, candidate buffer).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *    asynchronous on that stream unless stated otherwise.
+ *  - Every function returns PULSCAN_OK (0) or a negative PULSCAN_ERR_* code;
+ *    pulscan_last_error() then returns a message for the calling thread.
+ *  - Width w means a boxcar of w bins, w = 1..z_max (the paper's z + 1).
+ *  - A series of n real samples has M = n/2 + 1 Fourier bins.  It is cut into
+ *    n_seg = max(1, M / segment_len) segments of segment_len bins; the last
+ *    segment absorbs the remainder.  The segment is both the normalisation
+ *    block (§2.2.3) and the search chunk of Algorithm 4.
+ *  - A window is valid only if it lies inside the spectrum: k + w <= M.
+ *  - Noise power is Exp(1) after the 1/2 in P = (a^2 + b^2)/2, so a width-w
+ *    sum S has 2S ~ chi^2(2w) (Eq. 9); p = Q(w, S), Bonferroni-corrected by
+ *    n_trials (default M * z_max per series), sigma = Phi^{-1}(1 - p).
+ */
+#ifndef PULSCAN_H
+#define PULSCAN_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PULSCAN_API __attribute__((visibility("default")))
+#else
+#define PULSCAN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pulscan_stream; /* same type as cudaStream_t */
+typedef struct pulscan_plan_s *pulscan_plan;
+
+#define PULSCAN_OK 0
+#define PULSCAN_ERR_INVALID_ARG (-1) /* bad argument; nothing was launched      */
+#define PULSCAN_ERR_CUDA (-2)        /* a CUDA/cuFFT call failed                */
+#define PULSCAN_ERR_NOMEM (-3)       /* device or host allocation failed        */
+#define PULSCAN_ERR_CAPACITY (-4)    /* output larger than the given capacity   */
+#define PULSCAN_ERR_TIMEOUT (-5)     /* a bounded device wait gave up           */
+#define PULSCAN_ERR_UNSUPPORTED (-6) /* valid request this build cannot serve   */
+
+/* One candidate: the maximum boxcar power of one (series, segment, width) that
+ * passes the sigma threshold (Algorithm 4 keeps one per chunk and width).
+ * `bin` is the window's first bin k within its series (the centre is
+ * k + (width - 1)/2); `power` is S_w[k] in FP32; `sigma` is the
+ * Bonferroni-corrected Gaussian-equivalent significance (§2.2.3).  24 bytes. */
+typedef struct {
+  uint32_t series;
+  uint32_t width;
+  uint64_t bin;
+  float power;
+  float sigma;
+} pulscan_cand;
+
+/* Sizes of the caller-owned buffers of a plan.  All counts are elements. */
+typedef struct {
+  int64_t n_series;       /* series in the plan                                   */
+  int64_t x_floats;       /* time-domain buffer: float[x_floats]                  */
+  int64_t spec_floats;    /* spectrum buffer: interleaved (re, im) float pairs    */
+  int64_t power_floats;   /* power buffer: float[power_floats]                    */
+  int64_t total_segments; /* segments over all series (rows of maxima / stats)    */
+  int32_t z_max;
+  int32_t segment_len;
+  double threshold_sigma;
+  int64_t max_candidates; /* capacity of the plan's device candidate buffer       */
+} pulscan_plan_info;
+
+/* Create a plan for one series of n real samples.
+ * Validation (PULSCAN_ERR_INVALID_ARG, nothing allocated): n >= 2 and even;
+ * z_max >= 1; z_max <= segment_len <= M = n/2 + 1 (a window's halo then comes
+ * from at most one neighbouring segment); threshold_sigma finite and >= 0.
+ * The Bonferroni trial count is M * z_max (reading of §2.2.3: every bin times
+ * every searched width).  Allocates device scratch on the current device. */
+PULSCAN_API int pulscan_plan_create(pulscan_plan *out, int64_t n, int32_t z_max, int32_t segment_len,
+                        double threshold_sigma);
+
+/* Create a plan for a batch of series of uneven lengths (DM trials / beams),
+ * searched by the same kernels in one pass.  lengths[i] follows the rules of
+ * pulscan_plan_create for every i; each series gets its own trial count
+ * M_i * z_max.  The buffers hold the series at the offsets returned by
+ * pulscan_plan_offsets (series are grouped by length so that each length
+ * class is one batched FFT). */
+PULSCAN_API int pulscan_plan_create_batch(pulscan_plan *out, const int64_t *h_lengths, int32_t n_series,
+                              int32_t z_max, int32_t segment_len, double threshold_sigma);
+
+/* Destroy a plan and free its scratch (after the plan's last stream work). */
+PULSCAN_API void pulscan_plan_destroy(pulscan_plan plan);
+
+/* Buffer sizes (see pulscan_plan_info). */
+PULSCAN_API int pulscan_plan_get_info(pulscan_plan plan, pulscan_plan_info *h_info);
+
+/* Per-series offsets, each a host array of n_series + 1 int64 written by the
+ * call (NULL to skip): h_x_off in floats of the time buffer, h_spec_off in
+ * complex bins of the spectrum buffer (float pairs), h_power_off in floats of
+ * the power buffer, h_seg_off in segments.  Entry i+1 - entry i is series
+ * i's extent (spectrum/power extents include alignment padding). */
+PULSCAN_API int pulscan_plan_offsets(pulscan_plan plan, int64_t *h_x_off, int64_t *h_spec_off,
+                         int64_t *h_power_off, int64_t *h_seg_off);
+
+/* Override the Bonferroni trial count of every series (n_trials >= 1; 1 turns
+ * the correction off) and recompute the threshold table. Host-synchronous. */
+PULSCAN_API int pulscan_plan_set_trials(pulscan_plan plan, double n_trials);
+
+/* Copy the FP32 power threshold T_w of series `series` (w = 1..z_max) to
+ * h_thresh[0..z_max-1]: the smallest float S with sigma(S) >= threshold_sigma.
+ * Host-synchronous. */
+PULSCAN_API int pulscan_plan_thresholds(pulscan_plan plan, int32_t series, float *h_thresh);
+
+/* R2C FFT of every series (cuFFT, unnormalised, e^{-2 pi i k n/N}): d_x
+ * float[x_floats] -> d_spec float[spec_floats] as (re, im) pairs. */
+PULSCAN_API int pulscan_rfft(pulscan_plan plan, const float *d_x, float *d_spec, pulscan_stream stream);
+
+/* Normalised power (§2.2.3, Eq. 8): per segment and per component, median and
+ * MAD (exact order statistics; even counts average the two middle ones; DC
+ * bin taken as 0), a = (Re - med)/(kappa MAD), kappa = 1/Phi^{-1}(3/4),
+ * P = (a^2 + b^2)/2.  d_spec float[spec_floats] -> d_power float[power_floats].
+ * d_stats (nullable) receives float[4 * total_segments]: per segment
+ * (med_re, mad_re, med_im, mad_im).  A segment with MAD = 0 gets P = 0. */
+PULSCAN_API int pulscan_power_normalise(pulscan_plan plan, const float *d_spec, float *d_power, float *d_stats,
+                            pulscan_stream stream);
+
+/* Boxcar bank + threshold search (§2.2.5, Algorithm 4): for every segment s
+ * and width w, the maximum of S_w[k] = sum_{j<w} P[k+j] over the segment's
+ * valid start bins (lowest k on ties) becomes a candidate when it is >= T_w.
+ * Candidates land in the plan's device buffer; read them with
+ * pulscan_candidates.  d_power is read only. */
+PULSCAN_API int pulscan_boxcar_search(pulscan_plan plan, const float *d_power, pulscan_stream stream);
+
+/* Copy the candidates of the last pulscan_boxcar_search to h_out, ordered by
+ * (series, segment, width).  Synchronises `stream`.  *n_out = the true count;
+ * if it exceeds cap (or the plan's buffer), the first cap records are written
+ * and PULSCAN_ERR_CAPACITY is returned.  PULSCAN_ERR_TIMEOUT if a device-side
+ * bounded wait gave up during the search. */
+PULSCAN_API int pulscan_candidates(pulscan_plan plan, pulscan_cand *h_out, int64_t cap, int64_t *n_out,
+                       pulscan_stream stream);
+
+/* All per-(segment, width) maxima, thresholded or not (Algorithm 4 without
+ * the threshold): d_max float[total_segments * z_max] (row = segment, column
+ * = w - 1) and d_argmax uint64[...] (start bin within the series).  Entries
+ * with no valid window get NaN and UINT64_MAX. */
+PULSCAN_API int pulscan_segment_maxima(pulscan_plan plan, const float *d_power, float *d_max, uint64_t *d_argmax,
+                           pulscan_stream stream);
+
+/* Whole path (FFT, normalise, search) for a plan: the first call with a given
+ * (d_x, d_spec, d_power, stream) captures the kernels into a CUDA graph when
+ * use_graph != 0, later calls replay it. */
+PULSCAN_API int pulscan_search(pulscan_plan plan, const float *d_x, float *d_spec, float *d_power, int use_graph,
+                   pulscan_stream stream);
+
+/* Per-kernel timing with CUDA events on the launch stream: enable (on != 0)
+ * or disable recording; pulscan_plan_timings then writes the milliseconds of
+ * the most recent launch of [rfft, normalise, boxcar search kernel,
+ * candidate finalise, segment-maxima kernel] (-1 where not run) to
+ * h_ms[0..min(n,5)-1].  Synchronises the events. */
+PULSCAN_API int pulscan_plan_enable_timing(pulscan_plan plan, int on);
+PULSCAN_API int pulscan_plan_timings(pulscan_plan plan, float *h_ms, int32_t n);
+
+/* Message of the last error on this thread ("" if none). */
+PULSCAN_API const char *pulscan_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+PULSCAN_API int pulscan_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PULSCAN_H */

@@ -1,0 +1,215 @@
+"""GB300 boxcar (unmatched-filter) search of Pulscan (arXiv 2406.15186).
+
+Thin ctypes binding over ``libpulscan.so`` and its C ABI (``include/pulscan.h``).
+The binding only marshals arguments: every step of the search runs in the
+library's CUDA kernels (and cuFFT for the transform).  PyTorch is used, when
+given, for device memory and streams only.  There is no CPU fallback: if the
+library has not been built, ``load()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Plan", "PulscanError", "load", "lib_path", "CAND_DTYPE"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+CAND_DTYPE = np.dtype([("series", "<u4"), ("width", "<u4"), ("bin", "<u8"), ("power", "<f4"), ("sigma", "<f4")])
+assert CAND_DTYPE.itemsize == 24
+
+
+class PulscanError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pulscan error {code}: {msg}")
+        self.code = code
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_series", ctypes.c_int64), ("x_floats", ctypes.c_int64), ("spec_floats", ctypes.c_int64),
+                ("power_floats", ctypes.c_int64), ("total_segments", ctypes.c_int64), ("z_max", ctypes.c_int32),
+                ("segment_len", ctypes.c_int32), ("threshold_sigma", ctypes.c_double),
+                ("max_candidates", ctypes.c_int64)]
+
+
+def lib_path():
+    return os.path.join(_HERE, "libpulscan.so")
+
+
+# name -> (restype, argtypes); mirrors include/pulscan.h
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_SIGS = {
+    "pulscan_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double]),
+    "pulscan_plan_create_batch": (ctypes.c_int, [ctypes.POINTER(_P), _I64P, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.c_double]),
+    "pulscan_plan_destroy": (None, [_P]),
+    "pulscan_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(_Info)]),
+    "pulscan_plan_offsets": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, _I64P]),
+    "pulscan_plan_set_trials": (ctypes.c_int, [_P, ctypes.c_double]),
+    "pulscan_plan_thresholds": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
+    "pulscan_rfft": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pulscan_power_normalise": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "pulscan_boxcar_search": (ctypes.c_int, [_P, _P, _P]),
+    "pulscan_candidates": (ctypes.c_int, [_P, _P, ctypes.c_int64, _I64P, _P]),
+    "pulscan_segment_maxima": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "pulscan_search": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
+    "pulscan_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pulscan_plan_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
+    "pulscan_last_error": (ctypes.c_char_p, []),
+    "pulscan_version": (ctypes.c_int, []),
+}
+
+
+def load():
+    """Load libpulscan.so (built by ``paper_2406_15186_gb300.build``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2406_15186_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise PulscanError(rc, _LIB.pulscan_last_error().decode())
+
+
+def _ptr(a):
+    """Device/host address of a torch tensor, a numpy array or a raw int."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A search plan: one series (``n``) or a batch (``lengths``)."""
+
+    def __init__(self, n=None, z_max=256, segment_len=1024, threshold_sigma=6.0, lengths=None):
+        lib = load()
+        h = _P()
+        if lengths is None:
+            _check(lib.pulscan_plan_create(ctypes.byref(h), int(n), int(z_max), int(segment_len),
+                                           float(threshold_sigma)))
+        else:
+            arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
+            _check(lib.pulscan_plan_create_batch(ctypes.byref(h), arr, len(lengths), int(z_max),
+                                                 int(segment_len), float(threshold_sigma)))
+        self._h = h
+        info = _Info()
+        _check(lib.pulscan_plan_get_info(h, ctypes.byref(info)))
+        self.n_series = info.n_series
+        self.x_floats = info.x_floats
+        self.spec_floats = info.spec_floats
+        self.power_floats = info.power_floats
+        self.total_segments = info.total_segments
+        self.z_max = info.z_max
+        self.segment_len = info.segment_len
+        self.threshold_sigma = info.threshold_sigma
+        self.max_candidates = info.max_candidates
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pulscan_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- layout
+    def offsets(self):
+        """(x_off, spec_off, power_off, seg_off): int64 arrays of n_series + 1."""
+        n = self.n_series + 1
+        outs = [np.zeros(n, dtype=np.int64) for _ in range(4)]
+        _check(load().pulscan_plan_offsets(self._h, *[o.ctypes.data_as(_I64P) for o in outs]))
+        return tuple(outs)
+
+    def thresholds(self, series=0):
+        out = np.zeros(self.z_max, dtype=np.float32)
+        _check(load().pulscan_plan_thresholds(self._h, int(series),
+                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def set_trials(self, n_trials):
+        _check(load().pulscan_plan_set_trials(self._h, float(n_trials)))
+
+    # -- the path
+    def rfft(self, d_x, d_spec, stream=None):
+        _check(load().pulscan_rfft(self._h, _ptr(d_x), _ptr(d_spec), _stream(stream)))
+
+    def power_normalise(self, d_spec, d_power, d_stats=None, stream=None):
+        _check(load().pulscan_power_normalise(self._h, _ptr(d_spec), _ptr(d_power), _ptr(d_stats),
+                                              _stream(stream)))
+
+    def boxcar_search(self, d_power, stream=None):
+        _check(load().pulscan_boxcar_search(self._h, _ptr(d_power), _stream(stream)))
+
+    def candidates(self, cap=None, stream=None, allow_overflow=False):
+        """Candidates of the last search as a numpy structured array (CAND_DTYPE)."""
+        cap = self.max_candidates if cap is None else int(cap)
+        out = np.zeros(cap, dtype=CAND_DTYPE)
+        n = ctypes.c_int64(0)
+        rc = load().pulscan_candidates(self._h, out.ctypes.data, cap, ctypes.byref(n), _stream(stream))
+        if rc == -4 and allow_overflow:
+            return out[:cap], n.value
+        _check(rc)
+        return out[: n.value]
+
+    def segment_maxima(self, d_power, d_max, d_argmax, stream=None):
+        _check(load().pulscan_segment_maxima(self._h, _ptr(d_power), _ptr(d_max), _ptr(d_argmax),
+                                             _stream(stream)))
+
+    def search(self, d_x, d_spec, d_power, use_graph=False, stream=None):
+        _check(load().pulscan_search(self._h, _ptr(d_x), _ptr(d_spec), _ptr(d_power), int(bool(use_graph)),
+                                     _stream(stream)))
+
+    # -- timing
+    def enable_timing(self, on=True):
+        _check(load().pulscan_plan_enable_timing(self._h, int(bool(on))))
+
+    def timings(self):
+        """ms of the last [rfft, normalise, search kernel, finalise, segment maxima] (-1: not run)."""
+        out = (ctypes.c_float * 5)()
+        _check(load().pulscan_plan_timings(self._h, out, 5))
+        return list(out)
+
+    # -- convenience: device buffers sized for this plan (torch)
+    def buffers(self, device="cuda"):
+        import torch
+        x = torch.zeros(self.x_floats, dtype=torch.float32, device=device)
+        spec = torch.zeros(self.spec_floats, dtype=torch.float32, device=device)
+        power = torch.zeros(self.power_floats, dtype=torch.float32, device=device)
+        return x, spec, power

@@ -1,0 +1,130 @@
+// Internal definitions shared by the library's translation units: the plan,
+// error reporting, and thin inline-PTX wrappers for mbarrier and TMA bulk
+// copies (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pulscan.h"
+
+namespace ps {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define PS_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e__ = (call);                           \
+    if (e__ != cudaSuccess) return ps::cuda_fail(e__, #call); \
+  } while (0)
+
+// device error flags (bit set by kernels, read by pulscan_candidates)
+enum : uint32_t { kErrTimeout = 1u, kErrTouchOverflow = 2u };
+
+// ---------------------------------------------------------------- tiling
+// Boxcar search: each lane owns kR consecutive start bins; a warp owns
+// 32 * kR bins; a CTA of kWarps warps owns one tile of kTileBins bins.
+constexpr int kR = 33;                   // bins per lane (odd: conflict-free smem)
+constexpr int kWarps = 4;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kTileBins = 32 * kR * kWarps;  // 4224
+constexpr int kSub = 11;                 // early sub-block edge (kR = 3 * kSub)
+constexpr int kEarlyBlocks = 4;          // widths <= 132 use the finer bound
+
+// Normalisation kernel
+constexpr int kNormThreads = 512;
+constexpr int kHistBins = 2048;
+
+// ---------------------------------------------------------------- plan
+struct Series {
+  int64_t n;          // samples
+  int64_t m;          // bins = n/2 + 1
+  int64_t n_seg;      // segments
+  int64_t x_off;      // floats
+  int64_t spec_off;   // complex bins
+  int64_t p_off;      // floats (16-byte aligned)
+  int64_t seg_off;    // first global segment
+  int64_t tile_off;   // first global search tile
+  uint32_t user_index;
+};
+
+// device-side view of one series (what the kernels need)
+struct SeriesDev {
+  int64_t m;
+  int64_t n_seg;
+  int64_t p_off;
+  int64_t spec_off;
+  int64_t seg_off;
+  int64_t tile_off;
+  uint32_t user_index;
+  uint32_t pad_;
+};
+
+struct FftClass {
+  int64_t n;
+  int count;
+  int64_t x_off;      // first series of the class
+  int64_t spec_off;
+  int64_t spec_stride;  // complex bins between series of the class
+  cufftHandle handle;
+};
+
+struct GraphCache {
+  const void *x = nullptr, *spec = nullptr, *power = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace ps
+
+struct pulscan_plan_s {
+  int32_t z_max = 0;
+  int32_t seg_len = 0;
+  double sigma_thr = 0.0;
+  std::vector<ps::Series> series;
+  std::vector<ps::FftClass> fft;
+  std::vector<double> n_trials;     // per series (layout order)
+  std::vector<int> layout_of_user;  // user series index -> layout index
+  std::vector<float> h_thresh;      // n_series * z_max, layout order
+  int64_t x_floats = 0, spec_bins = 0, p_floats = 0, total_seg = 0, total_tiles = 0;
+  int64_t max_cands = 0;
+  int64_t touched_cap = 0;
+  // device scratch
+  ps::SeriesDev *d_series = nullptr;
+  int64_t *d_tile_off = nullptr;   // n_series + 1, for tile -> series search
+  int64_t *d_seg_off = nullptr;    // n_series + 1, for segment -> series search
+  float *d_thresh = nullptr;       // n_series * z_max
+  float *d_thresh_bound = nullptr; // same, scaled down slightly for bound checks
+  double *d_ln_trials = nullptr;   // ln(n_trials) per series
+  float *d_stats = nullptr;        // 4 * total_seg
+  unsigned long long *d_slots = nullptr;  // total_seg * z_max keys, 0 at rest
+  uint32_t *d_touched = nullptr;   // touched slot list
+  uint32_t *d_counters = nullptr;  // [0] touched, [1] candidates, [2] error flags, [3] spare
+  pulscan_cand *d_cands = nullptr;
+  // timing
+  bool timing = false;
+  cudaEvent_t ev[10] = {};
+  bool ran[5] = {};
+  ps::GraphCache graph;
+};
+
+namespace ps {
+// launchers (defined in the kernel translation units)
+int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats,
+                     cudaStream_t s);
+int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s);
+int launch_finalize(pulscan_plan p, cudaStream_t s);
+int launch_segmax(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax,
+                  cudaStream_t s);
+void record(pulscan_plan p, int idx, cudaStream_t s);  // timing event helper
+int search_smem_bytes(int W, int *buf_len_out);
+int prepare_bank(pulscan_plan p);       // one-time kernel attributes (before any capture)
+int prepare_normalise(pulscan_plan p);
+}  // namespace ps

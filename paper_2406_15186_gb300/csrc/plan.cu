@@ -1,0 +1,486 @@
+// Host runtime of the C ABI: plan creation (layout, threshold tables, cuFFT
+// plans, device scratch), argument checking, the whole-path CUDA graph, timing
+// events and candidate read-back.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "common.cuh"
+#include "signif.cuh"
+
+namespace ps {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+  set_error(msg);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? PULSCAN_ERR_NOMEM : PULSCAN_ERR_CUDA;
+}
+
+static int cuda_ok_or(cudaError_t e) { return e == cudaSuccess ? PULSCAN_OK : cuda_fail(e, "plan setup"); }
+
+static int cufft_fail(cufftResult r, const char *what) {
+  set_error(std::string(what) + ": cuFFT error " + std::to_string(static_cast<int>(r)));
+  return r == CUFFT_ALLOC_FAILED ? PULSCAN_ERR_NOMEM : PULSCAN_ERR_CUDA;
+}
+
+void record(pulscan_plan p, int idx, cudaStream_t s) {
+  if (p->timing) {
+    cudaEventRecord(p->ev[idx], s);
+    p->ran[idx / 2] = true;
+  }
+}
+
+// ln Phi_c(s) on the host: erfc while it is representable, else the
+// asymptotic (Mills-ratio) series phi(s)/s (1 - 1/s^2 + 3/s^4 - 15/s^6 + 105/s^8).
+static double log_sf_normal(double s) {
+  if (s < 30.0) return std::log(0.5 * std::erfc(s / std::sqrt(2.0)));
+  const double s2 = s * s;
+  const double series = 1.0 - 1.0 / s2 + 3.0 / (s2 * s2) - 15.0 / (s2 * s2 * s2) + 105.0 / (s2 * s2 * s2 * s2);
+  return -0.5 * s2 - std::log(s) - 0.5 * std::log(2.0 * M_PI) + std::log(series);
+}
+
+// Smallest float T with ln Q(w, T) <= y (bisection on the FP64 ln Q).
+static float threshold_for(int w, double y) {
+  if (y >= 0.0) return 0.0f;
+  double lo = 0.0, hi = static_cast<double>(w) + 1.0;
+  while (log_q_gamma(w, hi) > y) hi *= 2.0;
+  for (int it = 0; it < 300 && hi - lo > 1e-13 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (log_q_gamma(w, mid) > y) lo = mid; else hi = mid;
+  }
+  float f = static_cast<float>(hi);
+  if (static_cast<double>(f) < hi) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+static void compute_thresholds(pulscan_plan p) {
+  const int W = p->z_max;
+  const size_t ns = p->series.size();
+  p->h_thresh.assign(ns * W, 0.0f);
+  std::map<double, std::vector<float>> cache;
+  const double lsf = log_sf_normal(p->sigma_thr);
+  for (size_t i = 0; i < ns; ++i) {
+    const double nt = p->n_trials[i];
+    auto it = cache.find(nt);
+    if (it == cache.end()) {
+      std::vector<float> t(W);
+      const double y = lsf - std::log(nt);
+      for (int w = 1; w <= W; ++w) t[w - 1] = threshold_for(w, y);
+      it = cache.emplace(nt, std::move(t)).first;
+    }
+    std::copy(it->second.begin(), it->second.end(), p->h_thresh.begin() + i * W);
+  }
+}
+
+// Threshold tables to the device: exact T_w, and for the block bounds the
+// running minimum over widths >= w scaled by (1 - 2^-10), a margin that covers
+// FP32 rounding of the bound and of the running sums.
+static int upload_thresholds(pulscan_plan p) {
+  const int W = p->z_max;
+  const size_t ns = p->series.size();
+  std::vector<float> tb(ns * W);
+  std::vector<double> lt(ns);
+  for (size_t i = 0; i < ns; ++i) {
+    float run = INFINITY;
+    for (int w = W; w >= 1; --w) {
+      run = std::min(run, p->h_thresh[i * W + w - 1]);
+      tb[i * W + w - 1] = run * (1.0f - 1.0f / 1024.0f);
+    }
+    lt[i] = std::log(p->n_trials[i]);
+  }
+  PS_CUDA(cudaMemcpy(p->d_thresh, p->h_thresh.data(), ns * W * sizeof(float), cudaMemcpyHostToDevice));
+  PS_CUDA(cudaMemcpy(p->d_thresh_bound, tb.data(), ns * W * sizeof(float), cudaMemcpyHostToDevice));
+  PS_CUDA(cudaMemcpy(p->d_ln_trials, lt.data(), ns * sizeof(double), cudaMemcpyHostToDevice));
+  return PULSCAN_OK;
+}
+
+static void free_plan(pulscan_plan p) {
+  if (!p) return;
+  for (auto &f : p->fft)
+    if (f.handle) cufftDestroy(f.handle);
+  void *ptrs[] = {p->d_series, p->d_tile_off, p->d_seg_off, p->d_thresh, p->d_thresh_bound, p->d_ln_trials,
+                  p->d_stats,  p->d_slots,    p->d_touched, p->d_counters, p->d_cands};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  for (auto &e : p->ev)
+    if (e) cudaEventDestroy(e);
+  if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
+  delete p;
+}
+
+template <class T>
+static int dalloc(T **out, size_t count) {
+  *out = nullptr;
+  if (count == 0) count = 1;
+  PS_CUDA(cudaMalloc(reinterpret_cast<void **>(out), count * sizeof(T)));
+  return PULSCAN_OK;
+}
+
+static int check_shape(int64_t n, int32_t z_max, int32_t seg_len, double sigma) {
+  if (n < 2 || (n & 1)) return fail(PULSCAN_ERR_INVALID_ARG, "series length must be even and >= 2");
+  if (n > (int64_t(1) << 33)) return fail(PULSCAN_ERR_UNSUPPORTED, "series longer than 2^33 samples");
+  const int64_t m = n / 2 + 1;
+  if (z_max < 1) return fail(PULSCAN_ERR_INVALID_ARG, "z_max must be >= 1");
+  if (seg_len < z_max) return fail(PULSCAN_ERR_INVALID_ARG, "segment_len must be >= z_max");
+  if (seg_len > m) return fail(PULSCAN_ERR_INVALID_ARG, "segment_len must be <= n/2 + 1");
+  if (!std::isfinite(sigma) || sigma < 0.0)
+    return fail(PULSCAN_ERR_INVALID_ARG, "threshold_sigma must be finite and >= 0");
+  return PULSCAN_OK;
+}
+
+static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_series, int32_t z_max,
+                      int32_t seg_len, double sigma) {
+  if (!out) return fail(PULSCAN_ERR_INVALID_ARG, "null plan pointer");
+  *out = nullptr;
+  if (n_series < 1 || !lengths) return fail(PULSCAN_ERR_INVALID_ARG, "need at least one series");
+  for (int32_t i = 0; i < n_series; ++i) {
+    const int rc = check_shape(lengths[i], z_max, seg_len, sigma);
+    if (rc) return rc;
+  }
+  pulscan_plan p = new (std::nothrow) pulscan_plan_s();
+  if (!p) return fail(PULSCAN_ERR_NOMEM, "host allocation failed");
+  p->z_max = z_max;
+  p->seg_len = seg_len;
+  p->sigma_thr = sigma;
+  // layout: series grouped by length (stable in the caller's order) so every
+  // length class is one strided batched FFT
+  std::vector<int> order(n_series);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lengths[a] < lengths[b]; });
+  p->layout_of_user.assign(n_series, 0);
+  int64_t x = 0, sp = 0, pw = 0, sg = 0, tl = 0;
+  for (int li = 0; li < n_series; ++li) {
+    const int ui = order[li];
+    Series s{};
+    s.n = lengths[ui];
+    s.m = s.n / 2 + 1;
+    s.n_seg = std::max<int64_t>(1, s.m / seg_len);
+    s.x_off = x;
+    s.spec_off = sp;
+    s.p_off = pw;
+    s.seg_off = sg;
+    s.tile_off = tl;
+    s.user_index = static_cast<uint32_t>(ui);
+    p->series.push_back(s);
+    p->layout_of_user[ui] = li;
+    x += s.n;
+    const int64_t mpad = (s.m + 31) / 32 * 32;
+    sp += (li + 1 < n_series) ? mpad : s.m;
+    pw += (li + 1 < n_series) ? mpad : s.m;
+    sg += s.n_seg;
+    tl += (s.m + kTileBins - 1) / kTileBins;
+  }
+  p->x_floats = x;
+  p->spec_bins = sp;
+  p->p_floats = pw;
+  p->total_seg = sg;
+  p->total_tiles = tl;
+  const int64_t total_slots = sg * static_cast<int64_t>(z_max);
+  if (total_slots >= (int64_t(1) << 32)) {
+    free_plan(p);
+    return fail(PULSCAN_ERR_UNSUPPORTED, "segments x z_max exceeds 2^32 slots");
+  }
+  p->max_cands = std::min<int64_t>(total_slots, int64_t(1) << 24);
+  p->touched_cap = p->max_cands;
+  for (auto &s : p->series) p->n_trials.push_back(static_cast<double>(s.m) * z_max);
+  compute_thresholds(p);
+
+  int rc = PULSCAN_OK;
+  auto ok = [&](int r) {
+    if (r && !rc) rc = r;
+    return rc == PULSCAN_OK;
+  };
+  const size_t ns = p->series.size();
+  if (ok(dalloc(&p->d_series, ns)) && ok(dalloc(&p->d_tile_off, ns + 1)) && ok(dalloc(&p->d_seg_off, ns + 1)) &&
+      ok(dalloc(&p->d_thresh, ns * z_max)) && ok(dalloc(&p->d_thresh_bound, ns * z_max)) &&
+      ok(dalloc(&p->d_ln_trials, ns)) && ok(dalloc(&p->d_stats, 4 * sg)) &&
+      ok(dalloc(&p->d_slots, total_slots)) && ok(dalloc(&p->d_touched, p->touched_cap)) &&
+      ok(dalloc(&p->d_counters, 4)) && ok(dalloc(&p->d_cands, p->max_cands))) {
+    std::vector<SeriesDev> sd(ns);
+    std::vector<int64_t> to(ns + 1), so(ns + 1);
+    for (size_t i = 0; i < ns; ++i) {
+      const Series &s = p->series[i];
+      sd[i] = SeriesDev{s.m, s.n_seg, s.p_off, s.spec_off, s.seg_off, s.tile_off, s.user_index, 0u};
+      to[i] = s.tile_off;
+      so[i] = s.seg_off;
+    }
+    to[ns] = tl;
+    so[ns] = sg;
+    ok(cuda_ok_or(cudaMemcpy(p->d_series, sd.data(), ns * sizeof(SeriesDev), cudaMemcpyHostToDevice)));
+    ok(cuda_ok_or(cudaMemcpy(p->d_tile_off, to.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)));
+    ok(cuda_ok_or(cudaMemcpy(p->d_seg_off, so.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)));
+    ok(cuda_ok_or(cudaMemset(p->d_slots, 0, total_slots * sizeof(unsigned long long))));
+    ok(cuda_ok_or(cudaMemset(p->d_counters, 0, 4 * sizeof(uint32_t))));
+    ok(upload_thresholds(p));
+    ok(prepare_bank(p));
+    ok(prepare_normalise(p));
+  }
+  // cuFFT: one strided batched plan per length class
+  for (size_t i = 0; rc == PULSCAN_OK && i < ns;) {
+    size_t j = i;
+    while (j < ns && p->series[j].n == p->series[i].n) ++j;
+    FftClass f{};
+    f.n = p->series[i].n;
+    f.count = static_cast<int>(j - i);
+    f.x_off = p->series[i].x_off;
+    f.spec_off = p->series[i].spec_off;
+    f.spec_stride = (p->series[i].m + 31) / 32 * 32;
+    long long nn = f.n, inembed = f.n, onembed = f.spec_stride;
+    size_t work = 0;
+    cufftResult r = cufftCreate(&f.handle);
+    if (r == CUFFT_SUCCESS)
+      r = cufftMakePlanMany64(f.handle, 1, &nn, &inembed, 1, f.n, &onembed, 1, f.spec_stride, CUFFT_R2C,
+                              f.count, &work);
+    if (r != CUFFT_SUCCESS) {
+      rc = cufft_fail(r, "cufftMakePlanMany64");
+      if (f.handle) cufftDestroy(f.handle);
+      break;
+    }
+    p->fft.push_back(f);
+    i = j;
+  }
+  if (rc != PULSCAN_OK) {
+    free_plan(p);
+    return rc;
+  }
+  *out = p;
+  return PULSCAN_OK;
+}
+
+static bool aligned16(const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0u; }
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" {
+
+int pulscan_version(void) { return 10000; }
+
+const char *pulscan_last_error(void) { return g_last_error.c_str(); }
+
+int pulscan_plan_create(pulscan_plan *out, int64_t n, int32_t z_max, int32_t segment_len,
+                        double threshold_sigma) {
+  return build_plan(out, &n, 1, z_max, segment_len, threshold_sigma);
+}
+
+int pulscan_plan_create_batch(pulscan_plan *out, const int64_t *h_lengths, int32_t n_series, int32_t z_max,
+                              int32_t segment_len, double threshold_sigma) {
+  return build_plan(out, h_lengths, n_series, z_max, segment_len, threshold_sigma);
+}
+
+void pulscan_plan_destroy(pulscan_plan plan) { free_plan(plan); }
+
+int pulscan_plan_get_info(pulscan_plan p, pulscan_plan_info *info) {
+  if (!p || !info) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  info->n_series = static_cast<int64_t>(p->series.size());
+  info->x_floats = p->x_floats;
+  info->spec_floats = 2 * p->spec_bins;
+  info->power_floats = p->p_floats;
+  info->total_segments = p->total_seg;
+  info->z_max = p->z_max;
+  info->segment_len = p->seg_len;
+  info->threshold_sigma = p->sigma_thr;
+  info->max_candidates = p->max_cands;
+  return PULSCAN_OK;
+}
+
+int pulscan_plan_offsets(pulscan_plan p, int64_t *x_off, int64_t *spec_off, int64_t *power_off,
+                         int64_t *seg_off) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  const size_t ns = p->series.size();
+  // offsets are reported in the caller's series order; entry ns is the total
+  for (size_t u = 0; u < ns; ++u) {
+    const Series &s = p->series[p->layout_of_user[u]];
+    if (x_off) x_off[u] = s.x_off;
+    if (spec_off) spec_off[u] = s.spec_off;
+    if (power_off) power_off[u] = s.p_off;
+    if (seg_off) seg_off[u] = s.seg_off;
+  }
+  if (x_off) x_off[ns] = p->x_floats;
+  if (spec_off) spec_off[ns] = p->spec_bins;
+  if (power_off) power_off[ns] = p->p_floats;
+  if (seg_off) seg_off[ns] = p->total_seg;
+  return PULSCAN_OK;
+}
+
+int pulscan_plan_set_trials(pulscan_plan p, double n_trials) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  if (!(n_trials >= 1.0) || !std::isfinite(n_trials)) return fail(PULSCAN_ERR_INVALID_ARG, "n_trials must be >= 1");
+  for (auto &t : p->n_trials) t = n_trials;
+  compute_thresholds(p);
+  return upload_thresholds(p);
+}
+
+int pulscan_plan_thresholds(pulscan_plan p, int32_t series, float *h_thresh) {
+  if (!p || !h_thresh) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  if (series < 0 || series >= static_cast<int32_t>(p->series.size()))
+    return fail(PULSCAN_ERR_INVALID_ARG, "series index out of range");
+  const int li = p->layout_of_user[series];
+  std::memcpy(h_thresh, p->h_thresh.data() + static_cast<size_t>(li) * p->z_max, p->z_max * sizeof(float));
+  return PULSCAN_OK;
+}
+
+int pulscan_rfft(pulscan_plan p, const float *d_x, float *d_spec, pulscan_stream stream) {
+  if (!p || !d_x || !d_spec) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(d_x) || !aligned16(d_spec)) return fail(PULSCAN_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  record(p, 0, s);
+  for (auto &f : p->fft) {
+    cufftResult r = cufftSetStream(f.handle, s);
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecR2C(f.handle, const_cast<cufftReal *>(d_x + f.x_off),
+                       reinterpret_cast<cufftComplex *>(d_spec) + f.spec_off);
+    if (r != CUFFT_SUCCESS) return cufft_fail(r, "cufftExecR2C");
+  }
+  record(p, 1, s);
+  return PULSCAN_OK;
+}
+
+int pulscan_power_normalise(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats,
+                            pulscan_stream stream) {
+  if (!p || !d_spec || !d_power) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(d_spec) || !aligned16(d_power)) return fail(PULSCAN_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  if (d_stats && !aligned16(d_stats)) return fail(PULSCAN_ERR_INVALID_ARG, "stats buffer must be 16-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  record(p, 2, s);
+  const int rc = launch_normalise(p, d_spec, d_power, d_stats, s);
+  record(p, 3, s);
+  return rc;
+}
+
+static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s) {
+  PS_CUDA(cudaMemsetAsync(p->d_counters, 0, 4 * sizeof(uint32_t), s));
+  record(p, 4, s);
+  int rc = launch_search(p, d_power, s);
+  if (rc) return rc;
+  record(p, 5, s);
+  record(p, 6, s);
+  rc = launch_finalize(p, s);
+  record(p, 7, s);
+  return rc;
+}
+
+int pulscan_boxcar_search(pulscan_plan p, const float *d_power, pulscan_stream stream) {
+  if (!p || !d_power) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(d_power)) return fail(PULSCAN_ERR_INVALID_ARG, "power buffer must be 16-byte aligned");
+  return search_impl(p, d_power, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int pulscan_candidates(pulscan_plan p, pulscan_cand *h_out, int64_t cap, int64_t *n_out, pulscan_stream stream) {
+  if (!p || !n_out || cap < 0 || (cap > 0 && !h_out)) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t ctr[4];
+  PS_CUDA(cudaMemcpyAsync(ctr, p->d_counters, sizeof(ctr), cudaMemcpyDeviceToHost, s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  const int64_t count = ctr[1];
+  *n_out = count;
+  const int64_t have = std::min<int64_t>(count, p->max_cands);
+  std::vector<pulscan_cand> tmp(static_cast<size_t>(have));
+  if (have > 0) {
+    PS_CUDA(cudaMemcpyAsync(tmp.data(), p->d_cands, have * sizeof(pulscan_cand), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaStreamSynchronize(s));
+  }
+  // order by (series, segment, width)
+  auto seg_of = [&](const pulscan_cand &c) {
+    const Series &se = p->series[p->layout_of_user[c.series]];
+    return std::min<int64_t>(static_cast<int64_t>(c.bin) / p->seg_len, se.n_seg - 1);
+  };
+  std::sort(tmp.begin(), tmp.end(), [&](const pulscan_cand &a, const pulscan_cand &b) {
+    if (a.series != b.series) return a.series < b.series;
+    const int64_t sa = seg_of(a), sb = seg_of(b);
+    if (sa != sb) return sa < sb;
+    return a.width < b.width;
+  });
+  const int64_t ncopy = std::min<int64_t>(have, cap);
+  if (ncopy > 0) std::memcpy(h_out, tmp.data(), ncopy * sizeof(pulscan_cand));
+  if (ctr[2] & kErrTimeout) return fail(PULSCAN_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (count > cap || count > p->max_cands)
+    return fail(PULSCAN_ERR_CAPACITY, "more candidates than the output capacity");
+  return PULSCAN_OK;
+}
+
+int pulscan_segment_maxima(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax,
+                           pulscan_stream stream) {
+  if (!p || !d_power || !d_max || !d_argmax) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(d_power)) return fail(PULSCAN_ERR_INVALID_ARG, "power buffer must be 16-byte aligned");
+  return launch_segmax(p, d_power, d_max, d_argmax, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_power, int use_graph,
+                   pulscan_stream stream) {
+  if (!p || !d_x || !d_spec || !d_power) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!use_graph) {
+    int rc = pulscan_rfft(p, d_x, d_spec, stream);
+    if (!rc) rc = pulscan_power_normalise(p, d_spec, d_power, nullptr, stream);
+    if (!rc) rc = pulscan_boxcar_search(p, d_power, stream);
+    return rc;
+  }
+  GraphCache &g = p->graph;
+  if (!(g.exec && g.x == d_x && g.spec == d_spec && g.power == d_power && g.stream == s)) {
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    const bool timing = p->timing;
+    p->timing = false;
+    PS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = pulscan_rfft(p, d_x, d_spec, stream);
+    if (!rc) rc = pulscan_power_normalise(p, d_spec, d_power, nullptr, stream);
+    if (!rc) rc = pulscan_boxcar_search(p, d_power, stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    p->timing = timing;
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate");
+    g.x = d_x;
+    g.spec = d_spec;
+    g.power = d_power;
+    g.stream = s;
+  }
+  PS_CUDA(cudaGraphLaunch(g.exec, s));
+  return PULSCAN_OK;
+}
+
+int pulscan_plan_enable_timing(pulscan_plan p, int on) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  if (on) {
+    for (auto &e : p->ev)
+      if (!e) PS_CUDA(cudaEventCreate(&e));
+  }
+  p->timing = on != 0;
+  for (bool &r : p->ran) r = false;
+  return PULSCAN_OK;
+}
+
+int pulscan_plan_timings(pulscan_plan p, float *h_ms, int32_t n) {
+  if (!p || !h_ms || n < 0) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
+  for (int i = 0; i < std::min(n, 5); ++i) {
+    h_ms[i] = -1.0f;
+    if (!p->ran[i] || !p->ev[2 * i]) continue;
+    PS_CUDA(cudaEventSynchronize(p->ev[2 * i + 1]));
+    float ms = 0.0f;
+    PS_CUDA(cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]));
+    h_ms[i] = ms;
+  }
+  return PULSCAN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Chi-square significance used by the plan (threshold table, host) and by
+// the candidate finaliser (device), in FP64.
+//
+// Paper §2.2.3, Eq. 9: a width-w boxcar of normalised power is a sum of w
+// chi^2(2) variables.  With P = (a^2 + b^2)/2 a width-w sum S has 2S ~
+// chi^2(2w), so p = Q(w, S), the regularised upper incomplete gamma.  It is
+// Bonferroni-corrected for the trial count and converted to a one-sided
+// Gaussian-equivalent sigma.
+//
+// ln Q(a, x) follows the published method of Press et al., Numerical Recipes
+// (3rd ed., §6.2): the power series for P(a, x) when x < a + 1, and Legendre's
+// continued fraction for Q(a, x), evaluated by the modified Lentz method,
+// otherwise; both in log form so deep tails stay finite.  sigma is the root of
+// ln Phi_c(sigma) = ln p, found by Newton's method on
+// ln Phi_c(s) = ln(erfcx(s / sqrt 2) / 2) - s^2 / 2 (derivative
+// -sqrt(2/pi) / erfcx(s / sqrt 2)); ln Phi_c is concave, so after the first
+// step the iterates approach the root monotonically from above.
+#pragma once
+#include <math.h>
+
+namespace ps {
+
+__host__ __device__ inline double log_q_gamma(double a, double x) {
+  if (!(x > 0.0)) return 0.0;
+  const double lpre = -x + a * log(x) - lgamma(a);  // ln(x^a e^-x / Gamma(a))
+  if (x < a + 1.0) {
+    // P(a, x) = x^a e^-x / Gamma(a) * sum_{n>=0} x^n / (a (a+1) ... (a+n))
+    double ap = a, del = 1.0 / a, sum = del;
+    for (int n = 0; n < 200000; ++n) {
+      ap += 1.0;
+      del *= x / ap;
+      sum += del;
+      if (fabs(del) < fabs(sum) * 1e-17) break;
+    }
+    const double lp = lpre + log(sum);
+    return log1p(-exp(lp));
+  }
+  // Q(a, x) = x^a e^-x / Gamma(a) * 1 / (x + 1 - a - 1 (1 - a) / (x + 3 - a - ...))
+  const double tiny = 1e-300;
+  double b = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / b, h = d;
+  for (int i = 1; i < 200000; ++i) {
+    const double an = -i * (i - a);
+    b += 2.0;
+    d = an * d + b;
+    if (fabs(d) < tiny) d = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    d = 1.0 / d;
+    const double del = d * c;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return lpre + log(h);
+}
+
+#ifdef __CUDACC__
+// sigma with ln Phi_c(sigma) = lp, lp <= ln(1/2) (device: uses erfcx).
+__device__ inline double sigma_from_log_p(double lp) {
+  const double t = -2.0 * lp;
+  double s = (t > 2.0) ? sqrt(fmax(t - log(t) - 1.8378770664093453, 0.0)) : 0.0;  // ln(2 pi)
+  for (int it = 0; it < 60; ++it) {
+    const double e = erfcx(s * 0.70710678118654752);
+    const double f = log(0.5 * e) - 0.5 * s * s - lp;
+    const double step = f * e * 1.2533141373155003;  // sqrt(pi / 2)
+    s += step;
+    if (fabs(step) <= 1e-15 * fmax(1.0, fabs(s))) break;
+  }
+  return s;
+}
+#endif
+
+}  // namespace ps

@@ -1,0 +1,159 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Stage A: normalisation of the GPU spectrum.  Stage B: all (segment, width)
+maxima of the GPU power.  Candidates: thresholded search against the oracle's
+decisions.  Stage C: end-to-end from the raw series with the oracle's own FFT.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fft as offt
+from oracle import pipeline as opipe
+from oracle import significance as osig
+from paper_2406_15186_gb300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2406_15186_gb300 as p
+    from paper_2406_15186_gb300 import build
+    build.build()
+    p.load()
+    return p
+
+
+# (n, z_max, segment_len, sigma): several tiles, ragged tails, odd segment
+# lengths (unaligned TMA sources fall back to plain loads), widths that are
+# not multiples of 33, widths < 33, segment_len < 66 (lane bins span three
+# segments), a single segment, a non-power-of-two length
+SHAPES = [
+    (1 << 16, 64, 1024, 6.0),
+    (1 << 16, 100, 777, 4.0),
+    (1 << 14, 5, 16, 3.0),
+    (1 << 13, 40, 48, 3.0),
+    (1 << 12, 33, 2049, 3.0),
+    (3 * (1 << 12) + 10, 130, 1000, 3.0),
+    (1 << 17, 300, 4096, 5.0),
+]
+
+
+def _series(n, seed=11):
+    x = synth.noise(n, seed)
+    tones = [dict(amp=0.2, r0=0.31 * n / 2, z=min(40.0, n / 400), w=0.0, phi0=0.3),
+             dict(amp=0.1, r0=0.77 * n / 2, z=3.0, w=0.0, phi0=1.1)]
+    return synth.inject(x, tones)
+
+
+@pytest.mark.parametrize("n,w_max,seg_len,sigma", SHAPES)
+def test_stage_a_b_and_candidates(pkg, n, w_max, seg_len, sigma):
+    x = _series(n)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    out = parity.run_gpu(plan, x, stats=True)
+    m = n // 2 + 1
+    spec = parity.spectrum_complex(out["spec"], 0, m)
+    parity.check_normalise(spec, out["power"][:m], out["stats"], seg_len)
+    p64 = out["power"][:m].astype(np.float64)
+    mx_ref, am_ref = parity.check_maxima(p64, out["mx"], out["am"], w_max, seg_len)
+    parity.check_candidates(out["cands"], p64, mx_ref, am_ref, w_max, seg_len, sigma,
+                            parity.n_trials_of(m, w_max))
+
+
+@pytest.mark.parametrize("sigma", [0.0, 2.0])
+def test_low_thresholds_exercise_many_candidates(pkg, sigma):
+    n, w_max, seg_len = 1 << 16, 70, 512
+    x = _series(n, seed=5)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    plan.set_trials(1.0)
+    out = parity.run_gpu(plan, x)
+    m = n // 2 + 1
+    p64 = out["power"][:m].astype(np.float64)
+    mx_ref, am_ref = parity.check_maxima(p64, out["mx"], out["am"], w_max, seg_len)
+    k = parity.check_candidates(out["cands"], p64, mx_ref, am_ref, w_max, seg_len, sigma, 1.0)
+    assert k > 100
+
+
+def test_thresholds_match_oracle(pkg):
+    n, w_max, seg_len = 1 << 20, 256, 1024
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=6.0)
+    t = plan.thresholds()
+    nt = parity.n_trials_of(n // 2 + 1, w_max)
+    for w in (1, 2, 7, 33, 100, 255, 256):
+        ref = osig.threshold_power(w, 6.0, nt)
+        assert t[w - 1] >= ref * (1 - 1e-7) and t[w - 1] <= ref * (1 + 2 ** -22), (w, t[w - 1], ref)
+    assert np.all(np.diff(t) > 0)
+    # width 1: exp(-T) = Phi_c(6) / n_trials
+    assert t[0] == pytest.approx(math.log(nt / 9.865876450376946e-10), rel=1e-6)
+
+
+def test_full_single_2p20_end_to_end(pkg):
+    """Stage C on the full 2^20-sample workload: oracle from the raw series."""
+    cfg = synth.WORKLOADS["single_2p20"]
+    n, w_max, seg_len, sigma = cfg["n"], cfg["z_max"], cfg["segment_len"], cfg["sigma"]
+    x, tones = synth.single_series("single_2p20")
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    out = parity.run_gpu(plan, x, stats=True)
+    m = n // 2 + 1
+    # FFT stage: relative L2 error of the FP32 cuFFT spectrum vs the FP64 radix-2 oracle
+    ref_spec = offt.rfft(x.astype(np.float64))
+    gspec = parity.spectrum_complex(out["spec"], 0, m)
+    rel = np.linalg.norm(gspec - ref_spec) / np.linalg.norm(ref_spec)
+    assert rel <= 1e-6 * math.log2(n), rel
+    # stages A and B on the GPU's own intermediates
+    parity.check_normalise(gspec, out["power"][:m], out["stats"], seg_len)
+    p64 = out["power"][:m].astype(np.float64)
+    parity.check_maxima(p64, out["mx"], out["am"], w_max, seg_len)
+    # stage C: the oracle's full FP64 path from x
+    from oracle import boxcar as obox
+    from oracle import normalise as onorm
+    p_ref, _, _ = onorm.normalise_power(ref_spec, seg_len)
+    mx_ref, am_ref = obox.segment_maxima(p_ref, w_max, seg_len)
+    parity.check_candidates(out["cands"], p_ref, mx_ref, am_ref, w_max, seg_len, sigma,
+                            parity.n_trials_of(m, w_max))
+    best = out["cands"][np.argmax(out["cands"]["sigma"])]
+    assert tones[0]["r0"] - w_max <= best["bin"] <= tones[0]["r0"] + tones[0]["z"]
+    ref_c = opipe.candidates_from_maxima(mx_ref, am_ref, w_max, parity.n_trials_of(m, w_max), sigma)
+    assert abs(len(ref_c) - len(out["cands"])) <= 2
+
+
+def test_graph_replay_matches_eager(pkg):
+    n, w_max, seg_len = 1 << 16, 64, 1024
+    x = _series(n, seed=3)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=3.0)
+    eager = parity.run_gpu(plan, x, maxima=False)
+    graph = parity.run_gpu(plan, x, maxima=False, use_graph=True)
+    assert np.array_equal(eager["power"], graph["power"])
+    a = np.sort(eager["cands"], order=["series", "bin", "width"])
+    b = np.sort(graph["cands"], order=["series", "bin", "width"])
+    assert np.array_equal(a, b)
+
+
+def test_batch_uneven_lengths(pkg):
+    lengths = [1 << 13, 1 << 15, 1 << 12, 1 << 14, 1 << 13, 6000]
+    w_max, seg_len, sigma = 48, 256, 3.0
+    xs = [_series(n, seed=100 + i) for i, n in enumerate(lengths)]
+    plan = pkg.Plan(lengths=lengths, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    xo, so, po, go = plan.offsets()
+    x_all = np.zeros(plan.x_floats, dtype=np.float32)
+    for i, x in enumerate(xs):
+        x_all[xo[i]: xo[i] + len(x)] = x
+    out = parity.run_gpu(plan, x_all, stats=True)
+    for i, n in enumerate(lengths):
+        m = n // 2 + 1
+        spec = parity.spectrum_complex(out["spec"], so[i], m)
+        p = out["power"][po[i]: po[i] + m]
+        st = out["stats"][go[i]: go[i] + max(1, m // seg_len)]
+        parity.check_normalise(spec, p, st, seg_len)
+        p64 = p.astype(np.float64)
+        rows = slice(go[i], go[i] + max(1, m // seg_len))
+        mx_ref, am_ref = parity.check_maxima(p64, out["mx"][rows], out["am"][rows], w_max, seg_len)
+        parity.check_candidates(out["cands"], p64, mx_ref, am_ref, w_max, seg_len, sigma,
+                                parity.n_trials_of(m, w_max), series=i)

@@ -1,0 +1,335 @@
+"""Benchmark of the GB300 boxcar search (one JSON line on stdout, rank 0).
+
+Workload: the SPOTLIGHT-scale single series -- N = 2^23 float32 samples of
+Gaussian noise with 8 injected drifting tones, boxcar widths 1..1024, segments
+of 4096 bins, threshold 6 sigma (synthetic stand-in for the paper's `.fft`
+inputs).  One step = the whole path: R2C FFT (cuFFT), per-segment median/MAD
+normalisation, the boxcar bank over every width at every bin, and the
+per-(segment, width) maximum / threshold / significance.  The metric is
+boxcar bins x widths per second, M * W / step time, summed over ranks.
+
+--impl reference times the FP64 CPU oracle instead (the repository's own
+reference implementation of the method), on a bounded sample of the same
+workload scaled to the same unit.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "single_2p23"
+METRIC = "boxcar bins x widths per second"
+UNIT = "G bin-widths/s"
+L2_FLUSH_BYTES = 512 << 20      # > 129 MB of L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def profile_traffic(kernel_src):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the kernel source."""
+    path = os.path.join(ROOT, "profiles", "boxcar_search_single_2p23.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    want = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    src_hash = traffic = None
+    for ln in text.splitlines():
+        if ln.startswith("kernel_source_sha256_16:"):
+            src_hash = ln.split(":", 1)[1].strip()
+        if ln.startswith("dram_bytes_per_launch:"):
+            traffic = float(ln.split(":", 1)[1].strip())
+    return traffic if src_hash == want else None
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_fft(x):
+    """The oracle's FFT of the whole series, with its time (s)."""
+    from oracle import fft as offt
+    t0 = time.perf_counter()
+    spec = offt.rfft(x.astype(np.float64))
+    return spec, time.perf_counter() - t0
+
+
+def oracle_sample(spec, t_fft, cfg, n_seg_sample):
+    """Time the FP64 oracle on a bounded sample; returns (G bin-widths/s, seconds, description).
+
+    The FFT is timed once on the whole series (t_fft); normalisation and the
+    boxcar stage are linear in segments, so they are timed on the first
+    n_seg_sample segments and scaled to the whole series.
+    """
+    from oracle import boxcar as obox
+    from oracle import normalise as onorm
+    from oracle import pipeline as opipe
+    n, w_max, seg_len, sigma = cfg["n"], cfg["z_max"], cfg["segment_len"], cfg["sigma"]
+    m = n // 2 + 1
+    n_seg = m // seg_len
+    t1 = time.perf_counter()
+    sub = n_seg_sample * seg_len + w_max
+    p, _, _ = onorm.normalise_power(spec[:sub], seg_len)
+    mx, am = obox.segment_maxima(p, w_max, seg_len, seg_range=(0, n_seg_sample))
+    opipe.candidates_from_maxima(mx[:n_seg_sample], am[:n_seg_sample], w_max, opipe.n_trials_default(m, w_max),
+                                 sigma)
+    t3 = time.perf_counter()
+    frac = n_seg_sample / n_seg
+    t_full = t_fft + (t3 - t1) / frac
+    desc = (f"oracle FFT of the full 2^{n.bit_length() - 1}-sample series ({t_fft:.1f} s, timed once) + "
+            f"normalise/boxcar/search of {n_seg_sample}/{n_seg} segments, scaled linearly to all segments")
+    return m * w_max / t_full / 1e9, (t3 - t1), desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2406_15186_gb300 import synth
+    cfg = synth.WORKLOADS[WORKLOAD]
+    x, _ = synth.single_series(WORKLOAD)
+    m = cfg["n"] // 2 + 1
+    sample = 16                 # segments per step (1/64 of the series)
+    spec, t_fft = oracle_fft(x)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, _, desc = oracle_sample(spec, t_fft, cfg, sample)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    ms = m * cfg["z_max"] / (value * 1e9) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: N=2^23, z_max=1024, segment_len=4096, sigma=6",
+                       "sample": desc, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2406_15186_gb300 as pkg
+    from paper_2406_15186_gb300 import build, synth
+
+    build.build()
+    pkg.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    cfg = synth.WORKLOADS[WORKLOAD]
+    n, w_max, seg_len, sigma = cfg["n"], cfg["z_max"], cfg["segment_len"], cfg["sigma"]
+    m = n // 2 + 1
+    x, _ = synth.single_series(WORKLOAD)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        d_x, d_spec, d_power = plan.buffers(dev)
+        d_x.copy_(torch.from_numpy(x))
+    torch.cuda.synchronize()
+    plan.enable_timing(True)
+
+    def step():
+        plan.rfft(d_x, d_spec, stream=stream)
+        plan.power_normalise(d_spec, d_power, stream=stream)
+        plan.boxcar_search(d_power, stream=stream)
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        step()
+    n_cands = len(plan.candidates(stream=stream))
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    k_search, k_norm, k_fft, k_def, k_fin = [], [], [], [], []
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # L2 flushed between timed steps (outside the events)
+            ev[i][0].record(stream)
+        step()
+        with torch.cuda.stream(stream):
+            ev[i][1].record(stream)
+        t = plan.timings()                      # kernel events of this step (same stream)
+        k_fft.append(t[0])
+        k_norm.append(t[1])
+        k_search.append(t[2])
+        k_def.append(t[3])
+        k_fin.append(t[4])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * m * w_max / (ms * 1e-3) / 1e9
+
+    # end to end through the host-buffer entry point (H2D of the series, D2H of candidates)
+    plan.enable_timing(False)
+    x_pin = torch.from_numpy(x).pin_memory()
+    plan.search_host(x_pin, use_graph=True, stream=stream)
+    e2e_ms = []
+    nc = 0
+    for _ in range(max(3, args.steps // 2)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = plan.search_host(x_pin, use_graph=True, stream=stream)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        nc = len(c)
+    e2e_ms_mean = statistics.mean(e2e_ms)
+    if dist:
+        tt = torch.tensor([e2e_ms_mean], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms_mean = float(tt.item())
+
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    p_add = props.multi_processor_count * 128 * sm_max * 1e6          # FP32 adds/s
+    t_search = statistics.mean(k_search) * 1e-3
+    adds = m * (w_max - 1)
+    achieved = adds / t_search / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": p_add / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / (p_add / 1e12),
+                "traffic": profile_traffic(os.path.join(ROOT, "paper_2406_15186_gb300", "csrc", "boxcar.cu")),
+                "kernel": "boxcar_kernel<search>",
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
+                               f"({peak_kind} sm_max_mhz)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: N=2^23 samples (M=4194305 bins), 8 drifting tones, "
+                                   f"z_max=1024, segment_len=4096, sigma=6",
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "kernels_ms": {"rfft_cufft": statistics.mean(k_fft), "normalise": statistics.mean(k_norm),
+                           "boxcar_search": statistics.mean(k_search), "deferred_blocks": statistics.mean(k_def),
+                           "finalise": statistics.mean(k_fin)},
+            "candidates": n_cands,
+            "roofline": roofline,
+            "e2e": {"value": world * m * w_max / (e2e_ms_mean * 1e-3) / 1e9, "unit": UNIT,
+                    "ms_per_step": e2e_ms_mean, "h2d_bytes_per_step": 4 * n,
+                    "d2h_bytes_per_step": 16 + 24 * nc},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        spec, t_fft = oracle_fft(x)
+        v, secs, desc = oracle_sample(spec, t_fft, cfg, 64)
+        secs += t_fft
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                "seconds": secs}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

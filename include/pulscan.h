@@ -162,13 +162,31 @@ PULSCAN_API int pulscan_segment_maxima(pulscan_plan plan, const float *d_power, 
 PULSCAN_API int pulscan_search(pulscan_plan plan, const float *d_x, float *d_spec, float *d_power, int use_graph,
                    pulscan_stream stream);
 
+/* Whole path from HOST memory: copies h_x (float[x_floats], pinned or
+ * pageable) into device buffers owned by the plan (allocated on the first
+ * call), runs pulscan_search on them and returns the candidates exactly as
+ * pulscan_candidates does.  Synchronises `stream`. */
+PULSCAN_API int pulscan_search_host(pulscan_plan plan, const float *h_x, pulscan_cand *h_out, int64_t cap,
+                                    int64_t *n_out, int use_graph, pulscan_stream stream);
+
 /* Per-kernel timing with CUDA events on the launch stream: enable (on != 0)
  * or disable recording; pulscan_plan_timings then writes the milliseconds of
  * the most recent launch of [rfft, normalise, boxcar search kernel,
- * candidate finalise, segment-maxima kernel] (-1 where not run) to
- * h_ms[0..min(n,5)-1].  Synchronises the events. */
+ * deferred-block kernel, candidate finalise, segment-maxima kernel] (-1
+ * where not run) to h_ms[0..min(n,6)-1].  Synchronises the events. */
 PULSCAN_API int pulscan_plan_enable_timing(pulscan_plan plan, int on);
 PULSCAN_API int pulscan_plan_timings(pulscan_plan plan, float *h_ms, int32_t n);
+
+/* Counters of the last pulscan_boxcar_search (host-synchronous):
+ * h_out[0..min(n,4)-1] = [blocks deferred to the deferred-block kernel,
+ * deferred-block capacity, candidates found, candidate capacity].  A search
+ * whose deferred blocks exceed the capacity runs the excess blocks exactly
+ * inside the main kernel instead (same results, slower). */
+PULSCAN_API int pulscan_plan_counters(pulscan_plan plan, int64_t *h_out, int32_t n);
+
+/* Limit the deferred-block list to cap items (0 = every flagged block is
+ * run exactly by its own warp); cap is clipped to the allocated capacity. */
+PULSCAN_API int pulscan_plan_set_defer_capacity(pulscan_plan plan, int64_t cap);
 
 /* Message of the last error on this thread ("" if none). */
 PULSCAN_API const char *pulscan_last_error(void);

@@ -56,7 +56,10 @@ _SIGS = {
     "pulscan_candidates": (ctypes.c_int, [_P, _P, ctypes.c_int64, _I64P, _P]),
     "pulscan_segment_maxima": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pulscan_search": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
+    "pulscan_search_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _I64P, ctypes.c_int, _P]),
     "pulscan_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pulscan_plan_counters": (ctypes.c_int, [_P, _I64P, ctypes.c_int32]),
+    "pulscan_plan_set_defer_capacity": (ctypes.c_int, [_P, ctypes.c_int64]),
     "pulscan_plan_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "pulscan_last_error": (ctypes.c_char_p, []),
     "pulscan_version": (ctypes.c_int, []),
@@ -179,14 +182,19 @@ class Plan:
 
     def candidates(self, cap=None, stream=None, allow_overflow=False):
         """Candidates of the last search as a numpy structured array (CAND_DTYPE)."""
-        cap = self.max_candidates if cap is None else int(cap)
-        out = np.zeros(cap, dtype=CAND_DTYPE)
+        lib = load()
         n = ctypes.c_int64(0)
-        rc = load().pulscan_candidates(self._h, out.ctypes.data, cap, ctypes.byref(n), _stream(stream))
-        if rc == -4 and allow_overflow:
-            return out[:cap], n.value
-        _check(rc)
-        return out[: n.value]
+        size = 4096 if cap is None else int(cap)
+        while True:
+            out = np.empty(size, dtype=CAND_DTYPE)
+            rc = lib.pulscan_candidates(self._h, out.ctypes.data, size, ctypes.byref(n), _stream(stream))
+            if rc == -4 and cap is None and size < n.value <= self.max_candidates:
+                size = n.value          # grow to the true count and read again
+                continue
+            if rc == -4 and allow_overflow:
+                return out[:size], n.value
+            _check(rc)
+            return out[: n.value]
 
     def segment_maxima(self, d_power, d_max, d_argmax, stream=None):
         _check(load().pulscan_segment_maxima(self._h, _ptr(d_power), _ptr(d_max), _ptr(d_argmax),
@@ -196,15 +204,36 @@ class Plan:
         _check(load().pulscan_search(self._h, _ptr(d_x), _ptr(d_spec), _ptr(d_power), int(bool(use_graph)),
                                      _stream(stream)))
 
+    def search_host(self, h_x, use_graph=True, cap=4096, stream=None):
+        """Whole path from host memory (numpy array or pinned CPU tensor); returns candidates."""
+        lib = load()
+        n = ctypes.c_int64(0)
+        out = np.empty(int(cap), dtype=CAND_DTYPE)
+        rc = lib.pulscan_search_host(self._h, _ptr(h_x), out.ctypes.data, int(cap), ctypes.byref(n),
+                                     int(bool(use_graph)), _stream(stream))
+        if rc == -4 and n.value <= self.max_candidates:
+            return self.candidates(stream=stream)
+        _check(rc)
+        return out[: n.value]
+
     # -- timing
     def enable_timing(self, on=True):
         _check(load().pulscan_plan_enable_timing(self._h, int(bool(on))))
 
     def timings(self):
-        """ms of the last [rfft, normalise, search kernel, finalise, segment maxima] (-1: not run)."""
-        out = (ctypes.c_float * 5)()
-        _check(load().pulscan_plan_timings(self._h, out, 5))
+        """ms of the last [rfft, normalise, boxcar kernel, deferred blocks, finalise, segment maxima] (-1: not run)."""
+        out = (ctypes.c_float * 6)()
+        _check(load().pulscan_plan_timings(self._h, out, 6))
         return list(out)
+
+    def counters(self):
+        """[deferred blocks, deferred capacity, candidates, candidate capacity] of the last search."""
+        out = np.zeros(4, dtype=np.int64)
+        _check(load().pulscan_plan_counters(self._h, out.ctypes.data_as(_I64P), 4))
+        return [int(v) for v in out]
+
+    def set_defer_capacity(self, cap):
+        _check(load().pulscan_plan_set_defer_capacity(self._h, int(cap)))
 
     # -- convenience: device buffers sized for this plan (torch)
     def buffers(self, device="cuda"):

@@ -1,9 +1,9 @@
 // Boxcar filter bank + per-(segment, width) maximum (paper §2.2.5 and
 // Algorithm 4), GB300 design.
 //
-// Work decomposition: a CTA of kWarps warps owns a tile of kTileBins
-// consecutive start bins of one series; lane l of warp v owns the kR = 33
-// start bins k0 .. k0+32, k0 = tile + 33 (32 v + l).  The tile plus its halo
+// Work decomposition: a CTA of 1, 2 or 4 warps owns a tile of 1056 bins per
+// warp (consecutive start bins of one series); lane l of warp v owns the
+// kR = 33 start bins k0 .. k0+32, k0 = tile + 33 (32 v + l).  The tile plus its halo
 // of z_max bins is staged into shared memory by one TMA bulk copy.  Each lane
 // keeps its 33 running sums s_i = S_w[k0+i] in registers and walks w = 1..W:
 // step w adds P[k0+i+w-1] to s_i (one FP32 add per (bin, width), the
@@ -51,9 +51,7 @@ struct LaneCtx {
   int64_t seg_base;    // global index of the series' first segment
   int W;
   unsigned long long *slots;
-  uint32_t *touched;
-  uint32_t touched_cap;
-  uint32_t *counters;
+  uint32_t *dirty;
 };
 
 __device__ __forceinline__ unsigned long long slot_key(float v, uint32_t bin) {
@@ -61,69 +59,76 @@ __device__ __forceinline__ unsigned long long slot_key(float v, uint32_t bin) {
          static_cast<unsigned long long>(0xffffffffu - bin);
 }
 
-// Merge one (segment, width) maximum into its slot; in search mode record the
-// slot the first time it is touched so the finaliser can visit (and clear)
-// only touched slots.
+// Merge one (segment, width) maximum into its slot.  Both updates are
+// fire-and-forget reductions (no value returned, so the warp does not wait
+// for the round trip): the 64-bit max on the slot, and in search mode one bit
+// in the dirty bitmap that tells the finaliser which slots to visit.
 template <bool kSearch>
-__device__ __noinline__ void emit_slot(unsigned long long *slots, uint32_t *touched, uint32_t cap,
-                                       uint32_t *counters, uint64_t idx, unsigned long long key) {
-  const unsigned long long old = atomicMax(slots + idx, key);
-  if (kSearch && old == 0ull) {
-    const uint32_t t = atomicAdd(counters + 0, 1u);
-    if (t < cap) touched[t] = static_cast<uint32_t>(idx);
-  }
+__device__ __forceinline__ void emit_slot(unsigned long long *slots, uint32_t *dirty, uint64_t idx,
+                                          unsigned long long key) {
+  atomicMax(slots + idx, key);
+  if (kSearch) atomicOr(dirty + (idx >> 5), 1u << (idx & 31u));
 }
 
-// Segmented warp max-reduction of this step's per-lane bests and merge into
-// the slots.  Each lane offers at most two parts: bins [0, ib) in segment
-// seg_a and bins [ib, 33) in segment seg_a + 1 (v < 0: no entry).  The warp
-// reduces the parts that fall into its first two segments; any part beyond
-// (only possible when segment_len < 66) is merged lane by lane.
+// Lowest lane-bin index i in [ia, ib) with s_i == v (kR if none).
+__device__ __forceinline__ int first_equal(const float (&s)[kR], float v, int ia, int ib) {
+  int idx = kR;
+#pragma unroll
+  for (int i = kR - 1; i >= 0; --i) idx = (s[i] == v && i >= ia && i < ib) ? i : idx;
+  return idx;
+}
+
+// One exact step's merge.  Each lane offers the maximum of its valid bins in
+// segment seg_a (bins [0, ib)) and, for the one lane that straddles a
+// segment boundary, in seg_a + 1 (bins [ib, lim)); v < 0 means no valid bin.
+// For each of the warp's first two segments the warp reduces the maximum,
+// drops it if it is below T (search mode), finds the lowest bin holding it,
+// and lane 0 merges it into the (segment, width) slot.  Parts in a third
+// segment (segment_len < 1056 only) are merged lane by lane.
 template <bool kSearch>
-__device__ __forceinline__ void merge_step(const LaneCtx &c, int w, float vA, int iA, float vB, int iB) {
+__device__ __forceinline__ void merge_step(const float (&s)[kR], const LaneCtx &c, int w, float T, float vA,
+                                           float vB, int lim) {
   const int64_t s_first = __shfl_sync(kFull, c.seg_a, 0);
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
     const int64_t X = s_first + t;
-    float v = -1.0f;
-    int i = -1;
-    if (c.seg_a == X) {
-      v = vA;
-      i = iA;
-    } else if (c.seg_a + 1 == X) {
-      v = vB;
-      i = iB;
-    }
-    const bool has = (i >= 0);
-    const unsigned any = __ballot_sync(kFull, has);
-    if (any == 0u) continue;
-    const uint32_t bits = has ? __float_as_uint(v) : 0u;
+    const bool isA = (c.seg_a == X);
+    const bool isB = (c.seg_a + 1 == X);
+    const float v = isA ? vA : (isB ? vB : -1.0f);
+    const uint32_t bits = (v >= 0.0f) ? __float_as_uint(v) : 0u;
+    const unsigned has = __ballot_sync(kFull, v >= 0.0f);
+    if (has == 0u) continue;
     const uint32_t bmax = __reduce_max_sync(kFull, bits);
-    const uint32_t bin = (has && bits == bmax) ? static_cast<uint32_t>(c.k0 + i) : 0xffffffffu;
-    const uint32_t bmin = __reduce_min_sync(kFull, bin);
-    if ((threadIdx.x & 31) == 0) {
-      const uint64_t idx = static_cast<uint64_t>(X) * c.W + (w - 1);
-      emit_slot<kSearch>(c.slots, c.touched, c.touched_cap, c.counters, idx,
-                         slot_key(__uint_as_float(bmax), bmin));
+    const float vmax = __uint_as_float(bmax);
+    if (kSearch && !(vmax >= T)) continue;
+    uint32_t bin = 0xffffffffu;
+    if (v >= 0.0f && bits == bmax) {
+      const int i = isA ? first_equal(s, vmax, 0, min(c.ib, lim)) : first_equal(s, vmax, c.ib, lim);
+      bin = static_cast<uint32_t>(c.k0 + i);
     }
+    const uint32_t bmin = __reduce_min_sync(kFull, bin);
+    if ((threadIdx.x & 31) == 0)
+      emit_slot<kSearch>(c.slots, c.dirty, static_cast<uint64_t>(X) * c.W + (w - 1), slot_key(vmax, bmin));
   }
   // parts outside the warp's first two segments
-  if (iA >= 0 && c.seg_a > s_first + 1) {
-    emit_slot<kSearch>(c.slots, c.touched, c.touched_cap, c.counters,
-                       static_cast<uint64_t>(c.seg_a) * c.W + (w - 1),
-                       slot_key(vA, static_cast<uint32_t>(c.k0 + iA)));
+  if (vA >= 0.0f && c.seg_a > s_first + 1 && (!kSearch || vA >= T)) {
+    const int i = first_equal(s, vA, 0, min(c.ib, lim));
+    emit_slot<kSearch>(c.slots, c.dirty, static_cast<uint64_t>(c.seg_a) * c.W + (w - 1),
+                       slot_key(vA, static_cast<uint32_t>(c.k0 + i)));
   }
-  if (iB >= 0 && c.seg_a + 1 > s_first + 1) {
-    emit_slot<kSearch>(c.slots, c.touched, c.touched_cap, c.counters,
-                       static_cast<uint64_t>(c.seg_a + 1) * c.W + (w - 1),
-                       slot_key(vB, static_cast<uint32_t>(c.k0 + iB)));
+  if (vB >= 0.0f && c.seg_a + 1 > s_first + 1 && (!kSearch || vB >= T)) {
+    const int i = first_equal(s, vB, c.ib, lim);
+    emit_slot<kSearch>(c.slots, c.dirty, static_cast<uint64_t>(c.seg_a + 1) * c.W + (w - 1),
+                       slot_key(vB, static_cast<uint32_t>(c.k0 + i)));
   }
 }
 
-// Exact mode: steps w = wf + cb .. wf + ce - 1 with every sum compared.  The
-// sums stay in registers (static index i); the window is read straight from
-// shared memory (33 loads per step: this path is rare in search mode).
-// kSearch: emit maxima of bins with s_i >= T_w; otherwise emit every maximum.
+// Exact mode: steps w = wf + cb .. wf + ce - 1 with every window inspected.
+// The sums stay in registers (static index i); the window is read straight
+// from shared memory (33 loads per step).  Branch-free per bin: the lane's
+// maxima over its valid bins are max-reductions with selects, and the bin
+// index is searched only by the lane(s) holding the warp maximum.
+// kSearch: only maxima >= T_w are merged; otherwise every maximum is.
 template <bool kSearch>
 __device__ __forceinline__ void exact_steps(float (&s)[kR], const float *__restrict__ lane_buf, int wf,
                                             int cb, int ce, const float *__restrict__ thr,
@@ -131,6 +136,7 @@ __device__ __forceinline__ void exact_steps(float (&s)[kR], const float *__restr
   // segment_len < 66 lets a lane's 33 bins reach a third segment: then every
   // bin is merged on its own (only tiny test shapes take this branch)
   const bool small_seg = c.seg_len < 2 * kR;
+  const bool any_split = __any_sync(kFull, c.ib < kR);
   for (int cc = cb; cc < ce; ++cc) {
     const int w = wf + cc;
     const float *pw = lane_buf + (w - 1);
@@ -144,28 +150,24 @@ __device__ __forceinline__ void exact_steps(float (&s)[kR], const float *__restr
 #pragma unroll
       for (int i = 0; i < kR; ++i) {
         if (i < lim && (!kSearch || s[i] >= T)) {
-          const int64_t sg = c.seg_base + min((c.k0 + i) / c.seg_len, c.seg_last - c.seg_base);
-          emit_slot<kSearch>(c.slots, c.touched, c.touched_cap, c.counters,
-                             static_cast<uint64_t>(sg) * c.W + (w - 1),
+          const int64_t sg = c.seg_base + min64((c.k0 + i) / c.seg_len, c.seg_last - c.seg_base);
+          emit_slot<kSearch>(c.slots, c.dirty, static_cast<uint64_t>(sg) * c.W + (w - 1),
                              slot_key(s[i], static_cast<uint32_t>(c.k0 + i)));
         }
       }
       continue;
     }
+    const int la = min(c.ib, lim);   // part A: bins [0, la)
     float vA = -1.0f, vB = -1.0f;
-    int iA = -1, iB = -1;
 #pragma unroll
-    for (int i = 0; i < kR; ++i) {
-      if (i < lim && (!kSearch || s[i] >= T)) {
-        if (i < c.ib) {
-          if (s[i] > vA) { vA = s[i]; iA = i; }
-        } else {
-          if (s[i] > vB) { vB = s[i]; iB = i; }
-        }
-      }
+    for (int i = 0; i < kR; ++i) vA = fmaxf(vA, (i < la) ? s[i] : -1.0f);
+    if (any_split) {
+#pragma unroll
+      for (int i = 0; i < kR; ++i) vB = fmaxf(vB, (i >= c.ib && i < lim) ? s[i] : -1.0f);
     }
-    if (!__any_sync(kFull, (iA >= 0) || (iB >= 0))) continue;
-    merge_step<kSearch>(c, w, vA, iA, vB, iB);
+    // nothing to merge if no valid bin reaches T anywhere in the warp
+    if (kSearch && !__any_sync(kFull, vA >= T || vB >= T)) continue;
+    merge_step<kSearch>(s, c, w, T, vA, vB, lim);
   }
 }
 
@@ -189,12 +191,82 @@ __device__ __forceinline__ void reload_ring(float (&b)[kR], const float *__restr
   for (int j = 0; j < kR - 1; ++j) b[(CE + j) % kR] = pb[CE + j];
 }
 
+// Bound test of one 11-width sub-block of an early block: three groups of
+// 11 bins, each bounded by s_{11 j} plus a pre-summed window of 22 bins.
+__device__ __forceinline__ bool early_bound(const float (&s)[kR], const float *__restrict__ q11, int qb, float tb) {
+  return (s[0] + q11[qb] + q11[qb + 1] >= tb) || (s[kSub] + q11[qb + 1] + q11[qb + 2] >= tb) ||
+         (s[2 * kSub] + q11[qb + 2] + q11[qb + 3] >= tb);
+}
+
+// Lane context for lane `lane` of warp `warp` of the tile starting at bin t0.
+__device__ __forceinline__ LaneCtx lane_ctx(const SeriesDev &S, int64_t t0, int tile_bins, int warp, int lane,
+                                            int W, int seg_len, unsigned long long *slots, uint32_t *dirty) {
+  LaneCtx c;
+  c.k0 = t0 + warp * (32 * kR) + lane * kR;
+  c.m = S.m;
+  const int64_t tile_end = min64(t0 + static_cast<int64_t>(tile_bins), S.m);
+  c.lim_tile = static_cast<int>(max64(min64(tile_end - c.k0, kR), -1));
+  c.seg_len = seg_len;
+  c.seg_base = S.seg_off;
+  c.seg_last = S.seg_off + S.n_seg - 1;
+  const int64_t sa_local = min64(c.k0 / seg_len, S.n_seg - 1);
+  c.seg_a = S.seg_off + sa_local;
+  c.ib = (sa_local < S.n_seg - 1) ? static_cast<int>(min64((sa_local + 1) * seg_len - c.k0, kR)) : kR;
+  c.W = W;
+  c.slots = slots;
+  c.dirty = dirty;
+  return c;
+}
+
+__device__ __forceinline__ int series_of_tile(const int64_t *__restrict__ tile_off, int n_series, int64_t tile) {
+  int lo = 0, hi = n_series - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_off[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Deferred block: (tile, warp, block, first step) packed in 64 bits.
+__device__ __forceinline__ unsigned long long pack_item(int64_t tile, int warp, int bi, int cx) {
+  return static_cast<unsigned long long>(tile) | (static_cast<unsigned long long>(warp) << 40) |
+         (static_cast<unsigned long long>(bi) << 42) | (static_cast<unsigned long long>(cx) << 56);
+}
+
+// Defer the rest of block bi (steps cx..) of this warp: append a work item
+// and snapshot the 33 running sums (coalesced, [item][bin][lane]).  Returns
+// false when the list is full; the caller then runs the block exactly inline.
+__device__ __forceinline__ bool defer_block(const float (&s)[kR], unsigned long long *__restrict__ items,
+                                            float *__restrict__ snaps, uint32_t *__restrict__ counters,
+                                            uint32_t cap, int64_t tile, int warp, int bi, int cx) {
+  const int lane = threadIdx.x & 31;
+  uint32_t idx = 0;
+  if (lane == 0) idx = atomicAdd(counters + 0, 1u);
+  idx = __shfl_sync(kFull, idx, 0);
+  if (idx >= cap) return false;
+  if (lane == 0) items[idx] = pack_item(tile, warp, bi, cx);
+  float *sp = snaps + static_cast<size_t>(idx) * (kR * 32) + lane;
+#pragma unroll
+  for (int i = 0; i < kR; ++i) sp[i * 32] = s[i];
+  return true;
+}
+
+// Plain steps w = wa..wb-1 (no ring, no compares): the partial last block.
+__device__ __forceinline__ void tail_steps(float (&s)[kR], const float *__restrict__ lane_buf, int wa, int wb) {
+  for (int w = wa; w < wb; ++w) {
+    const float *pw = lane_buf + (w - 1);
+#pragma unroll
+    for (int i = 0; i < kR; ++i) s[i] += pw[i];
+  }
+}
+
 template <bool kSearch>
-__global__ void __launch_bounds__(kThreads) boxcar_kernel(
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
     int n_series, int W, int seg_len, const float *__restrict__ thr_all, const float *__restrict__ thrb_all,
-    unsigned long long *__restrict__ slots, uint32_t *__restrict__ touched, uint32_t touched_cap,
-    uint32_t *__restrict__ counters, int buf_len) {
+    unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty, uint32_t *__restrict__ counters,
+    unsigned long long *__restrict__ items, float *__restrict__ snaps, uint32_t item_cap, int tile_bins,
+    int buf_len) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
@@ -202,16 +274,12 @@ __global__ void __launch_bounds__(kThreads) boxcar_kernel(
   const int nq11 = buf_len / kSub;      // 11-bin block sums
   float *q33 = buf + buf_len;
   float *q11 = q33 + nq33 + 1;
+  const int nthreads = blockDim.x;
 
-  // tile -> series (largest i with tile_off[i] <= tile)
   const int64_t tile = blockIdx.x;
-  int lo = 0, hi = n_series - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tile_off[mid] <= tile) lo = mid; else hi = mid - 1;
-  }
-  const SeriesDev S = series[lo];
-  const int64_t t0 = (tile - S.tile_off) * static_cast<int64_t>(kTileBins);
+  const int si = series_of_tile(tile_off, n_series, tile);
+  const SeriesDev S = series[si];
+  const int64_t t0 = (tile - S.tile_off) * static_cast<int64_t>(tile_bins);
   const float *src = power + S.p_off + t0;
   const int64_t avail64 = S.m - t0;
   const int avail = static_cast<int>(min64(avail64, static_cast<int64_t>(buf_len)));
@@ -224,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) boxcar_kernel(
     mbar_arrive_expect_tx(bar, static_cast<uint32_t>(n_tma) * 4u);
     tma_load_1d(buf, src, static_cast<uint32_t>(n_tma) * 4u, bar);
   }
-  for (int i = n_tma + threadIdx.x; i < buf_len; i += kThreads) buf[i] = (i < avail) ? src[i] : 0.0f;
+  for (int i = n_tma + threadIdx.x; i < buf_len; i += nthreads) buf[i] = (i < avail) ? src[i] : 0.0f;
   if (n_tma > 0) {
     if (!mbar_wait_bounded(bar, 0, 2000000000ull)) {
       if (threadIdx.x == 0) atomicOr(counters + 2, kErrTimeout);
@@ -235,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) boxcar_kernel(
 
   // block sums for the bounds: q11[j] = sum of 11 bins from 11 j,
   // q33[j] = sum of 33 bins from 33 j
-  for (int j = threadIdx.x; j < nq11; j += kThreads) {
+  for (int j = threadIdx.x; j < nq11; j += nthreads) {
     const float *p = buf + kSub * j;
     float a = 0.0f;
 #pragma unroll
@@ -243,29 +311,14 @@ __global__ void __launch_bounds__(kThreads) boxcar_kernel(
     q11[j] = a;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < nq33; j += kThreads) q33[j] = q11[3 * j] + q11[3 * j + 1] + q11[3 * j + 2];
+  for (int j = threadIdx.x; j < nq33; j += nthreads) q33[j] = q11[3 * j] + q11[3 * j + 1] + q11[3 * j + 2];
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int x0 = warp * (32 * kR) + lane * kR;   // buffer-relative first bin
-  LaneCtx c;
-  c.k0 = t0 + x0;
-  c.m = S.m;
-  const int64_t tile_end = min(t0 + static_cast<int64_t>(kTileBins), S.m);
-  c.lim_tile = static_cast<int>(max64(min64(tile_end - c.k0, kR), -1));
-  c.seg_len = seg_len;
-  c.seg_base = S.seg_off;
-  c.seg_last = S.seg_off + S.n_seg - 1;
-  const int64_t sa_local = min(c.k0 / seg_len, S.n_seg - 1);
-  c.seg_a = S.seg_off + sa_local;
-  c.ib = (sa_local < S.n_seg - 1) ? static_cast<int>(min64((sa_local + 1) * seg_len - c.k0, kR)) : kR;
-  c.W = W;
-  c.slots = slots;
-  c.touched = touched;
-  c.touched_cap = touched_cap;
-  c.counters = counters;
-  const float *thr = thr_all + static_cast<int64_t>(lo) * W;
-  const float *thrb = thrb_all + static_cast<int64_t>(lo) * W;
+  const LaneCtx c = lane_ctx(S, t0, tile_bins, warp, lane, W, seg_len, slots, dirty);
+  const float *thr = thr_all + static_cast<int64_t>(si) * W;
+  const float *thrb = thrb_all + static_cast<int64_t>(si) * W;
 
   float s[kR], b[kR];
 #pragma unroll
@@ -281,45 +334,194 @@ __global__ void __launch_bounds__(kThreads) boxcar_kernel(
   for (int j = 0; j < kR - 1; ++j) b[j] = lane_buf[j];
   b[kR - 1] = 0.0f;
 
+  // One 33-step body serves every block.  A block first tests its bound
+  // (per 11 x 11 sub-block for the early widths, per 33 x 33 block after);
+  // early blocks test again before steps 11 and 22.  When a bound reaches the
+  // threshold the rest of the block is deferred (snapshot + work item for the
+  // deferred kernel) and the warp carries on with plain adds; only when the
+  // work list is full does the warp inspect the block itself (exact mode).
   const int nb = (W + kR - 1) / kR;
+  const int qb0 = x0 / kSub;
+  const int qc0 = x0 / kR;
   for (int bi = 0; bi < nb; ++bi) {
     const float *pb = lane_buf + bi * kR;
     const int wf = bi * kR + 1;
     const int nsteps = min(kR, W - bi * kR);
-    if (bi < kEarlyBlocks) {
-      // three sub-blocks of 11 widths, bound per 11 bins
+    const bool early = bi < kEarlyBlocks;
+    bool deferred = false;
+    {
+      const bool hit = early ? early_bound(s, q11, qb0 + 3 * bi, thrb[wf - 1])
+                             : (s[0] + q33[qc0 + bi] + q33[qc0 + bi + 1] >= thrb[wf - 1]);
+      if (__any_sync(kFull, hit)) {
+        if (!defer_block(s, items, snaps, counters, item_cap, tile, warp, bi, 0)) {
+          exact_steps<true>(s, lane_buf, wf, 0, nsteps, thr, c);
+          reload_ring<kR>(b, pb);
+          continue;
+        }
+        deferred = true;
+      }
+    }
+    if (nsteps < kSub) {
+      tail_steps(s, lane_buf, wf, wf + nsteps);
+      continue;
+    }
+    fast_steps<0, kSub>(s, b, pb);
+    if (early && !deferred && nsteps > kSub &&
+        __any_sync(kFull, early_bound(s, q11, qb0 + 3 * bi + 1, thrb[wf + kSub - 1]))) {
+      if (!defer_block(s, items, snaps, counters, item_cap, tile, warp, bi, kSub)) {
+        exact_steps<true>(s, lane_buf, wf, kSub, nsteps, thr, c);
+        reload_ring<kR>(b, pb);
+        continue;
+      }
+      deferred = true;
+    }
+    if (nsteps < 2 * kSub) {
+      tail_steps(s, lane_buf, wf + kSub, wf + nsteps);
+      continue;
+    }
+    fast_steps<kSub, kSub>(s, b, pb);
+    if (early && !deferred && nsteps > 2 * kSub &&
+        __any_sync(kFull, early_bound(s, q11, qb0 + 3 * bi + 2, thrb[wf + 2 * kSub - 1]))) {
+      if (!defer_block(s, items, snaps, counters, item_cap, tile, warp, bi, 2 * kSub)) {
+        exact_steps<true>(s, lane_buf, wf, 2 * kSub, nsteps, thr, c);
+        reload_ring<kR>(b, pb);
+        continue;
+      }
+    }
+    if (nsteps < kR) {
+      tail_steps(s, lane_buf, wf + 2 * kSub, wf + nsteps);
+      continue;
+    }
+    fast_steps<2 * kSub, kSub>(s, b, pb);
+  }
+}
+
+// Lane's best window among its bins [ia, ib) (power bits << 32 | ~bin), or 0.
+__device__ __forceinline__ unsigned long long lane_best(const float (&s)[kR], int64_t k0, int ia, int ib) {
+  float v[kR];
 #pragma unroll
-      for (int sub = 0; sub < 3; ++sub) {
-        const int cb = sub * kSub;
-        if (cb >= nsteps) break;
-        const int ce = min(cb + kSub, nsteps);
-        const int qj = (x0 + bi * kR + cb) / kSub;
-        const float tb = thrb[wf + cb - 1];
-        const bool hit = (s[0] + q11[qj] + q11[qj + 1] >= tb) ||
-                         (s[kSub] + q11[qj + 1] + q11[qj + 2] >= tb) ||
-                         (s[2 * kSub] + q11[qj + 2] + q11[qj + 3] >= tb);
-        const bool exact = __any_sync(kFull, hit) || (ce - cb < kSub);
-        if (exact) {
-          exact_steps<true>(s, lane_buf, wf, cb, ce, thr, c);
-          if (sub == 0) reload_ring<kSub>(b, pb);
-          else if (sub == 1) reload_ring<2 * kSub>(b, pb);
-          else reload_ring<3 * kSub>(b, pb);
-        } else {
-          if (sub == 0) fast_steps<0, kSub>(s, b, pb);
-          else if (sub == 1) fast_steps<kSub, kSub>(s, b, pb);
-          else fast_steps<2 * kSub, kSub>(s, b, pb);
+  for (int i = 0; i < kR; ++i) v[i] = (i >= ia && i < ib) ? s[i] : -1.0f;
+  // max over 33 values as a tree (short dependency chains)
+  float m16[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) m16[i] = fmaxf(v[2 * i], v[2 * i + 1]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) m16[i] = fmaxf(m16[2 * i], m16[2 * i + 1]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) m16[i] = fmaxf(m16[2 * i], m16[2 * i + 1]);
+  const float m = fmaxf(fmaxf(fmaxf(m16[0], m16[1]), fmaxf(m16[2], m16[3])), v[kR - 1]);
+  if (!(m >= 0.0f)) return 0ull;
+  uint32_t eq = 0u;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) eq |= (v[i] == m) ? (1u << i) : 0u;
+  const int first = eq ? (__ffs(static_cast<int>(eq)) - 1) : (kR - 1);
+  return slot_key(m, static_cast<uint32_t>(k0 + first));
+}
+
+// Deferred blocks, one warp per work item.  The warp reloads its 33 x 32
+// running sums from the snapshot and stages the block's window of P (32 x 33
+// bins plus the 66-bin reach of one block) into shared memory.  Phase 1 runs
+// the remaining steps of the block: per step each lane records the key of its
+// best window per segment part in shared memory (no warp-wide operation in
+// the step loop).  Phase 2 gives each lane one width: it merges the 32 lanes'
+// keys segment by segment and sends every maximum that reaches T_w to its
+// slot.  Items are independent, so the warps of the whole GPU share them
+// instead of one warp walking every width of a busy region.
+constexpr int kRegion = 32 * kR + 2 * kR;
+constexpr int kDeferWarps = 2;
+
+__global__ void __launch_bounds__(32 * kDeferWarps) deferred_kernel(
+    const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
+    int n_series, int W, int seg_len, const float *__restrict__ thr_all, unsigned long long *__restrict__ slots,
+    uint32_t *__restrict__ dirty, const uint32_t *__restrict__ counters,
+    const unsigned long long *__restrict__ items, const float *__restrict__ snaps, uint32_t item_cap,
+    int tile_bins) {
+  __shared__ float region_all[kDeferWarps][kRegion];
+  // keys[part][lane][step]: lane-major so both phases are bank-conflict free
+  __shared__ unsigned long long keys_all[kDeferWarps][2][32][kR];
+  __shared__ long long segs_all[kDeferWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *region = region_all[warp];
+  const uint32_t n_items = min(counters[0], item_cap);
+  const uint32_t stride = gridDim.x * kDeferWarps;
+  for (uint32_t it = blockIdx.x * kDeferWarps + warp; it < n_items; it += stride) {
+    const unsigned long long item = items[it];
+    const int64_t tile = static_cast<int64_t>(item & 0xffffffffffull);
+    const int wv = static_cast<int>((item >> 40) & 3ull);
+    const int bi = static_cast<int>((item >> 42) & 0x3fffull);
+    const int cx = static_cast<int>((item >> 56) & 0xffull);
+    const int si = series_of_tile(tile_off, n_series, tile);
+    const SeriesDev S = series[si];
+    const int64_t t0 = (tile - S.tile_off) * static_cast<int64_t>(tile_bins);
+    const int64_t r0 = t0 + wv * (32 * kR) + bi * kR + cx;   // first bin of the staged window
+    const float *src = power + S.p_off;
+    __syncwarp();
+    for (int j = lane; j < kRegion; j += 32) region[j] = (r0 + j < S.m) ? src[r0 + j] : 0.0f;
+    __syncwarp();
+    const LaneCtx c = lane_ctx(S, t0, tile_bins, wv, lane, W, seg_len, slots, dirty);
+    float s[kR];
+    const float *sp = snaps + static_cast<size_t>(it) * (kR * 32) + lane;
+#pragma unroll
+    for (int i = 0; i < kR; ++i) s[i] = sp[i * 32];
+    // lane_buf[w - 1 + i] must address bin k0 + w - 1 + i of the window
+    const float *lane_buf = region + lane * kR - (bi * kR + cx);
+    const int nsteps = min(kR, W - bi * kR);
+    const int wf = bi * kR + 1;
+    const float *thr = thr_all + static_cast<int64_t>(si) * W;
+    if (seg_len < 2 * kR) {
+      // lane bins may span three segments: merge per step (test shapes only)
+      exact_steps<true>(s, lane_buf, wf, cx, nsteps, thr, c);
+      continue;
+    }
+    const bool any_split = __any_sync(kFull, c.ib < kR);
+    unsigned long long(*keys)[32][kR] = keys_all[warp];
+    long long *segs = segs_all[warp];
+    segs[lane] = c.seg_a;
+    for (int cc = cx; cc < nsteps; ++cc) {
+      const int w = wf + cc;
+      const float *pw = lane_buf + (w - 1);
+#pragma unroll
+      for (int i = 0; i < kR; ++i) s[i] += pw[i];
+      const int64_t lim64 = c.m - w + 1 - c.k0;
+      const int lim = static_cast<int>(min64(static_cast<int64_t>(c.lim_tile), max64(lim64, 0)));
+      keys[0][lane][cc] = lane_best(s, c.k0, 0, min(c.ib, lim));
+      keys[1][lane][cc] = any_split ? lane_best(s, c.k0, c.ib, lim) : 0ull;
+    }
+    __syncwarp();
+    // phase 2: lane -> width.  The lanes' segments are non-decreasing along
+    // (lane, part A, part B), so a running maximum is flushed whenever the
+    // segment changes.
+    for (int cc = cx + lane; cc < nsteps; cc += 32) {
+      const int w = wf + cc;
+      const float T = thr[w - 1];
+      int64_t cur = -1;
+      unsigned long long best = 0ull;
+      auto flush = [&]() {
+        if (best != 0ull && __uint_as_float(static_cast<uint32_t>(best >> 32)) >= T)
+          emit_slot<true>(slots, dirty, static_cast<uint64_t>(cur) * W + (w - 1), best);
+      };
+      for (int l = 0; l < 32; ++l) {
+        const int64_t sa = segs[l];
+        const unsigned long long ka = keys[0][l][cc];
+        if (sa != cur) {
+          flush();
+          cur = sa;
+          best = 0ull;
+        }
+        best = max(best, ka);
+        if (any_split) {
+          const unsigned long long kb = keys[1][l][cc];
+          if (kb != 0ull) {
+            if (sa + 1 != cur) {
+              flush();
+              cur = sa + 1;
+              best = 0ull;
+            }
+            best = max(best, kb);
+          }
         }
       }
-    } else {
-      const int qj = (x0 + bi * kR) / kR;
-      const bool hit = s[0] + q33[qj] + q33[qj + 1] >= thrb[wf - 1];
-      const bool exact = __any_sync(kFull, hit) || (nsteps < kR);
-      if (exact) {
-        exact_steps<true>(s, lane_buf, wf, 0, nsteps, thr, c);
-        reload_ring<kR>(b, pb);
-      } else {
-        fast_steps<0, kR>(s, b, pb);
-      }
+      flush();
     }
   }
 }
@@ -343,39 +545,53 @@ __global__ void unpack_kernel(unsigned long long *__restrict__ slots, int64_t n,
 
 }  // namespace
 
-int search_smem_bytes(int W, int *buf_len_out) {
+int search_tile_bins(int warps) { return 32 * kR * warps; }
+
+int search_smem_bytes(int W, int warps, int *buf_len_out) {
   const int nb = (W + kR - 1) / kR;
-  int buf_len = kTileBins + nb * kR + 3 * kR;
+  int buf_len = search_tile_bins(warps) + nb * kR + 3 * kR;
   buf_len = (buf_len + 3) & ~3;
   const int nq33 = buf_len / kR, nq11 = buf_len / kSub;
   if (buf_len_out) *buf_len_out = buf_len;
   return 128 + 4 * (buf_len + nq33 + 1 + nq11 + 1);
 }
 
-static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaStream_t s) {
-  int buf_len = 0;
-  const int smem = search_smem_bytes(p->z_max, &buf_len);
-  if (p->total_tiles > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many search tiles");
-  if (search) {
-    boxcar_kernel<true><<<static_cast<unsigned>(p->total_tiles), kThreads, smem, s>>>(
-        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
-        p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_touched, static_cast<uint32_t>(p->touched_cap),
-        p->d_counters, buf_len);
-  } else {
-    boxcar_kernel<false><<<static_cast<unsigned>(p->total_tiles), kThreads, smem, s>>>(
-        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
-        p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_touched, static_cast<uint32_t>(p->touched_cap),
-        p->d_counters, buf_len);
-  }
-  PS_CUDA(cudaGetLastError());
-  return PULSCAN_OK;
-}
-
 int prepare_bank(pulscan_plan p) {
-  const int smem = search_smem_bytes(p->z_max, nullptr);
+  const int smem = search_smem_bytes(p->z_max, p->search_warps, nullptr);
   if (smem > 220 * 1024) return fail(PULSCAN_ERR_UNSUPPORTED, "z_max too large for the shared-memory tile");
   PS_CUDA(cudaFuncSetAttribute(boxcar_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   PS_CUDA(cudaFuncSetAttribute(boxcar_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  return PULSCAN_OK;
+}
+
+static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaStream_t s) {
+  int buf_len = 0;
+  const int smem = search_smem_bytes(p->z_max, p->search_warps, &buf_len);
+  if (p->total_tiles > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many search tiles");
+  const dim3 grid(static_cast<unsigned>(p->total_tiles));
+  const dim3 block(32 * p->search_warps);
+  const int tile_bins = search_tile_bins(p->search_warps);
+  const uint32_t cap = static_cast<uint32_t>(p->item_cap);
+  if (search) {
+    boxcar_kernel<true><<<grid, block, smem, s>>>(
+        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+        p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
+        tile_bins, buf_len);
+    PS_CUDA(cudaGetLastError());
+    record(p, 5, s);
+    record(p, 6, s);
+    deferred_kernel<<<p->defer_grid, 32 * kDeferWarps, 0, s>>>(
+        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+        p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
+    PS_CUDA(cudaGetLastError());
+    record(p, 7, s);
+  } else {
+    boxcar_kernel<false><<<grid, block, smem, s>>>(
+        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+        p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, 0u,
+        tile_bins, buf_len);
+  }
+  PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }
 
@@ -386,10 +602,10 @@ int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s) {
 int launch_segmax(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax, cudaStream_t s) {
   const int64_t n = p->total_seg * static_cast<int64_t>(p->z_max);
   PS_CUDA(cudaMemsetAsync(p->d_slots, 0, static_cast<size_t>(n) * sizeof(unsigned long long), s));
-  record(p, 8, s);
+  record(p, 10, s);
   int rc = launch_bank(p, d_power, false, s);
   if (rc) return rc;
-  record(p, 9, s);
+  record(p, 11, s);
   unpack_kernel<<<1024, 256, 0, s>>>(p->d_slots, n, d_max, d_argmax);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;

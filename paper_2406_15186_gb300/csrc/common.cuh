@@ -26,15 +26,14 @@ int cuda_fail(cudaError_t e, const char *what);
   } while (0)
 
 // device error flags (bit set by kernels, read by pulscan_candidates)
-enum : uint32_t { kErrTimeout = 1u, kErrTouchOverflow = 2u };
+enum : uint32_t { kErrTimeout = 1u };
 
 // ---------------------------------------------------------------- tiling
 // Boxcar search: each lane owns kR consecutive start bins; a warp owns
-// 32 * kR bins; a CTA of kWarps warps owns one tile of kTileBins bins.
+// 32 * kR bins; a CTA of 1..4 warps owns one tile of 32 * kR * warps bins.
 constexpr int kR = 33;                   // bins per lane (odd: conflict-free smem)
-constexpr int kWarps = 4;
-constexpr int kThreads = 32 * kWarps;
-constexpr int kTileBins = 32 * kR * kWarps;  // 4224
+constexpr int kMaxThreads = 128;         // at most 4 warps (tiles of 1056..4224 bins)
+constexpr int kMinBlocks = 4;            // resident CTAs per SM the register budget targets
 constexpr int kSub = 11;                 // early sub-block edge (kR = 3 * kSub)
 constexpr int kEarlyBlocks = 4;          // widths <= 132 use the finer bound
 
@@ -78,7 +77,7 @@ struct FftClass {
 
 struct GraphCache {
   const void *x = nullptr, *spec = nullptr, *power = nullptr;
-  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;   // plan-owned stream the graph is captured on
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -95,7 +94,7 @@ struct pulscan_plan_s {
   std::vector<float> h_thresh;      // n_series * z_max, layout order
   int64_t x_floats = 0, spec_bins = 0, p_floats = 0, total_seg = 0, total_tiles = 0;
   int64_t max_cands = 0;
-  int64_t touched_cap = 0;
+  int search_warps = 4;            // warps per boxcar CTA (tile = 1056 * warps bins)
   // device scratch
   ps::SeriesDev *d_series = nullptr;
   int64_t *d_tile_off = nullptr;   // n_series + 1, for tile -> series search
@@ -105,13 +104,20 @@ struct pulscan_plan_s {
   double *d_ln_trials = nullptr;   // ln(n_trials) per series
   float *d_stats = nullptr;        // 4 * total_seg
   unsigned long long *d_slots = nullptr;  // total_seg * z_max keys, 0 at rest
-  uint32_t *d_touched = nullptr;   // touched slot list
-  uint32_t *d_counters = nullptr;  // [0] touched, [1] candidates, [2] error flags, [3] spare
+  uint32_t *d_dirty = nullptr;     // one bit per slot touched by the search, 0 at rest
+  uint32_t *d_counters = nullptr;  // [0] deferred items, [1] candidates, [2] error flags, [3] spare
+  unsigned long long *d_items = nullptr;  // deferred boxcar blocks
+  float *d_snaps = nullptr;        // their running-sum snapshots (33 x 32 floats each)
+  int64_t item_cap = 0;           // deferred items in use (<= alloc_item_cap)
+  int64_t alloc_item_cap = 0;
+  int defer_grid = 1;
   pulscan_cand *d_cands = nullptr;
+  // device buffers owned by the plan for pulscan_search_host
+  float *own_x = nullptr, *own_spec = nullptr, *own_power = nullptr;
   // timing
   bool timing = false;
-  cudaEvent_t ev[10] = {};
-  bool ran[5] = {};
+  cudaEvent_t ev[12] = {};
+  bool ran[6] = {};
   ps::GraphCache graph;
 };
 
@@ -124,7 +130,8 @@ int launch_finalize(pulscan_plan p, cudaStream_t s);
 int launch_segmax(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax,
                   cudaStream_t s);
 void record(pulscan_plan p, int idx, cudaStream_t s);  // timing event helper
-int search_smem_bytes(int W, int *buf_len_out);
+int search_smem_bytes(int W, int warps, int *buf_len_out);
+int search_tile_bins(int warps);
 int prepare_bank(pulscan_plan p);       // one-time kernel attributes (before any capture)
 int prepare_normalise(pulscan_plan p);
 }  // namespace ps

@@ -3,12 +3,15 @@
 // end of Algorithm 4).
 //
 // The search kernel leaves, for every (segment, width) whose maximum reached
-// T_w, a 64-bit key (power bits << 32 | ~bin) in its slot and the slot's index
-// in a "touched" list.  This kernel visits the touched slots (or, if the list
-// overflowed, every slot), converts each to a record, computes
+// T_w, a 64-bit key (power bits << 32 | ~bin) in its slot and sets the slot's
+// bit in a dirty bitmap.  This kernel scans the bitmap (one word per warp,
+// one slot per lane, grid-stride), visits the slots whose bits are set, converts each to a
+// record, computes
 // ln p = ln Q(w, S) + ln n_trials (Bonferroni, capped at 0) and the
 // Gaussian-equivalent sigma in FP64, appends the record, and clears the slot
-// so the slot array is zero again for the next search.
+// and the bitmap word so both are zero again for the next search.
+#include <algorithm>
+
 #include "common.cuh"
 #include "signif.cuh"
 
@@ -16,18 +19,28 @@ namespace ps {
 
 namespace {
 
-__global__ void finalize_kernel(unsigned long long *__restrict__ slots, const uint32_t *__restrict__ touched,
-                                uint32_t touched_cap, uint32_t *__restrict__ counters, int64_t total_slots,
-                                int W, const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
+__global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty,
+                                int64_t n_words, uint32_t *__restrict__ counters, int W,
+                                const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
                                 int n_series, const double *__restrict__ ln_trials,
                                 pulscan_cand *__restrict__ cands, uint32_t max_cands) {
-  const uint32_t nt = counters[0];
-  const bool full = nt > touched_cap;
-  const int64_t n = full ? total_slots : static_cast<int64_t>(nt);
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const uint64_t idx = full ? static_cast<uint64_t>(i) : static_cast<uint64_t>(touched[i]);
-    const unsigned long long key = slots[idx];
+  // one warp per bitmap word, one lane per bit: the FP64 significance of
+  // neighbouring (segment, width) slots is evaluated in parallel
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); j < n_words;
+       j += warps) {
+    const uint32_t bits = dirty[j];
+    if (bits == 0u) continue;
+    if (lane == 0) dirty[j] = 0u;
+    const bool mine = (bits >> lane) & 1u;
+    const uint64_t idx = static_cast<uint64_t>(j) * 32u + static_cast<uint64_t>(lane);
+    const unsigned long long key = mine ? slots[idx] : 0ull;
+    // one output reservation per warp (the word's set bits), not per record
+    const unsigned act = __ballot_sync(0xffffffffu, key != 0ull);
+    uint32_t base = 0;
+    if (lane == 0 && act) base = atomicAdd(counters + 1, static_cast<uint32_t>(__popc(act)));
+    base = __shfl_sync(0xffffffffu, base, 0);
     if (key == 0ull) continue;
     slots[idx] = 0ull;
     const int64_t gseg = static_cast<int64_t>(idx / static_cast<uint64_t>(W));
@@ -41,7 +54,7 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ slots, const ui
     const uint32_t bin = 0xffffffffu - static_cast<uint32_t>(key & 0xffffffffull);
     const double lp = fmin(0.0, log_q_gamma(static_cast<double>(w), static_cast<double>(pw)) + ln_trials[lo]);
     const double sg = sigma_from_log_p(lp);
-    const uint32_t o = atomicAdd(counters + 1, 1u);
+    const uint32_t o = base + static_cast<uint32_t>(__popc(act & ((1u << lane) - 1u)));
     if (o < max_cands) {
       pulscan_cand c;
       c.series = series[lo].user_index;
@@ -57,11 +70,11 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ slots, const ui
 }  // namespace
 
 int launch_finalize(pulscan_plan p, cudaStream_t s) {
-  const int64_t total = p->total_seg * static_cast<int64_t>(p->z_max);
-  finalize_kernel<<<304, 256, 0, s>>>(p->d_slots, p->d_touched, static_cast<uint32_t>(p->touched_cap),
-                                       p->d_counters, total, p->z_max, p->d_series, p->d_seg_off,
-                                       static_cast<int>(p->series.size()), p->d_ln_trials, p->d_cands,
-                                       static_cast<uint32_t>(p->max_cands));
+  const int64_t words = (p->total_seg * static_cast<int64_t>(p->z_max) + 31) / 32;
+  const int grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>((words + 7) / 8, 1), 2432));
+  finalize_kernel<<<grid, 256, 0, s>>>(p->d_slots, p->d_dirty, words, p->d_counters, p->z_max, p->d_series,
+                                       p->d_seg_off, static_cast<int>(p->series.size()), p->d_ln_trials,
+                                       p->d_cands, static_cast<uint32_t>(p->max_cands));
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }

@@ -109,12 +109,14 @@ static void free_plan(pulscan_plan p) {
   for (auto &f : p->fft)
     if (f.handle) cufftDestroy(f.handle);
   void *ptrs[] = {p->d_series, p->d_tile_off, p->d_seg_off, p->d_thresh, p->d_thresh_bound, p->d_ln_trials,
-                  p->d_stats,  p->d_slots,    p->d_touched, p->d_counters, p->d_cands};
+                  p->d_stats,  p->d_slots,    p->d_dirty,   p->d_counters, p->d_cands,     p->own_x,
+                  p->own_spec, p->own_power, p->d_items, p->d_snaps};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (auto &e : p->ev)
     if (e) cudaEventDestroy(e);
   if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
+  if (p->graph.capture) cudaStreamDestroy(p->graph.capture);
   delete p;
 }
 
@@ -158,6 +160,19 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lengths[a] < lengths[b]; });
   p->layout_of_user.assign(n_series, 0);
+  // warps per boxcar CTA: the widest tile that still gives >= 4 CTAs per SM
+  int n_sm = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  p->search_warps = 1;
+  for (int wp = 4; wp >= 1; wp >>= 1) {
+    int64_t tiles = 0;
+    for (int32_t i = 0; i < n_series; ++i) tiles += (lengths[i] / 2 + 1 + search_tile_bins(wp) - 1) / search_tile_bins(wp);
+    if (tiles >= 4LL * n_sm) {
+      p->search_warps = wp;
+      break;
+    }
+  }
+  const int64_t tile_bins = search_tile_bins(p->search_warps);
   int64_t x = 0, sp = 0, pw = 0, sg = 0, tl = 0;
   for (int li = 0; li < n_series; ++li) {
     const int ui = order[li];
@@ -178,7 +193,7 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
     sp += (li + 1 < n_series) ? mpad : s.m;
     pw += (li + 1 < n_series) ? mpad : s.m;
     sg += s.n_seg;
-    tl += (s.m + kTileBins - 1) / kTileBins;
+    tl += (s.m + tile_bins - 1) / tile_bins;
   }
   p->x_floats = x;
   p->spec_bins = sp;
@@ -191,7 +206,15 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
     return fail(PULSCAN_ERR_UNSUPPORTED, "segments x z_max exceeds 2^32 slots");
   }
   p->max_cands = std::min<int64_t>(total_slots, int64_t(1) << 24);
-  p->touched_cap = p->max_cands;
+  const int64_t dirty_words = (total_slots + 31) / 32;
+  // deferred-block list: at most one item per (warp, block); the capacity
+  // scales with the warps and is capped (an overflowing block is then run
+  // exactly by its own warp)
+  const int64_t total_warps = tl * p->search_warps;
+  const int64_t nb = (z_max + kR - 1) / kR;
+  p->item_cap = std::min<int64_t>(total_warps * nb, std::min<int64_t>(std::max<int64_t>(total_warps, 8192), 65536));
+  p->alloc_item_cap = p->item_cap;
+  p->defer_grid = 8 * n_sm;   // 2-warp CTAs: 16 warps per SM for deferred blocks
   for (auto &s : p->series) p->n_trials.push_back(static_cast<double>(s.m) * z_max);
   compute_thresholds(p);
 
@@ -204,8 +227,9 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
   if (ok(dalloc(&p->d_series, ns)) && ok(dalloc(&p->d_tile_off, ns + 1)) && ok(dalloc(&p->d_seg_off, ns + 1)) &&
       ok(dalloc(&p->d_thresh, ns * z_max)) && ok(dalloc(&p->d_thresh_bound, ns * z_max)) &&
       ok(dalloc(&p->d_ln_trials, ns)) && ok(dalloc(&p->d_stats, 4 * sg)) &&
-      ok(dalloc(&p->d_slots, total_slots)) && ok(dalloc(&p->d_touched, p->touched_cap)) &&
-      ok(dalloc(&p->d_counters, 4)) && ok(dalloc(&p->d_cands, p->max_cands))) {
+      ok(dalloc(&p->d_slots, total_slots)) && ok(dalloc(&p->d_dirty, dirty_words)) &&
+      ok(dalloc(&p->d_counters, 4)) && ok(dalloc(&p->d_cands, p->max_cands)) &&
+      ok(dalloc(&p->d_items, p->item_cap)) && ok(dalloc(&p->d_snaps, p->item_cap * kR * 32))) {
     std::vector<SeriesDev> sd(ns);
     std::vector<int64_t> to(ns + 1), so(ns + 1);
     for (size_t i = 0; i < ns; ++i) {
@@ -220,6 +244,7 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
     ok(cuda_ok_or(cudaMemcpy(p->d_tile_off, to.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(cuda_ok_or(cudaMemcpy(p->d_seg_off, so.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(cuda_ok_or(cudaMemset(p->d_slots, 0, total_slots * sizeof(unsigned long long))));
+    ok(cuda_ok_or(cudaMemset(p->d_dirty, 0, dirty_words * sizeof(uint32_t))));
     ok(cuda_ok_or(cudaMemset(p->d_counters, 0, 4 * sizeof(uint32_t))));
     ok(upload_thresholds(p));
     ok(prepare_bank(p));
@@ -362,12 +387,11 @@ int pulscan_power_normalise(pulscan_plan p, const float *d_spec, float *d_power,
 static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s) {
   PS_CUDA(cudaMemsetAsync(p->d_counters, 0, 4 * sizeof(uint32_t), s));
   record(p, 4, s);
-  int rc = launch_search(p, d_power, s);
+  int rc = launch_search(p, d_power, s);   // records 5, 6, 7 around the deferred kernel
   if (rc) return rc;
-  record(p, 5, s);
-  record(p, 6, s);
+  record(p, 8, s);
   rc = launch_finalize(p, s);
-  record(p, 7, s);
+  record(p, 9, s);
   return rc;
 }
 
@@ -427,20 +451,24 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
     if (!rc) rc = pulscan_boxcar_search(p, d_power, stream);
     return rc;
   }
+  // The work is captured once on a plan-owned stream (the legacy default
+  // stream cannot be captured) and the graph is launched on the caller's.
   GraphCache &g = p->graph;
-  if (!(g.exec && g.x == d_x && g.spec == d_spec && g.power == d_power && g.stream == s)) {
+  if (!(g.exec && g.x == d_x && g.spec == d_spec && g.power == d_power)) {
     if (g.exec) {
       cudaGraphExecDestroy(g.exec);
       g.exec = nullptr;
     }
+    if (!g.capture) PS_CUDA(cudaStreamCreateWithFlags(&g.capture, cudaStreamNonBlocking));
     const bool timing = p->timing;
     p->timing = false;
-    PS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    int rc = pulscan_rfft(p, d_x, d_spec, stream);
-    if (!rc) rc = pulscan_power_normalise(p, d_spec, d_power, nullptr, stream);
-    if (!rc) rc = pulscan_boxcar_search(p, d_power, stream);
+    const pulscan_stream cs = reinterpret_cast<pulscan_stream>(g.capture);
+    PS_CUDA(cudaStreamBeginCapture(g.capture, cudaStreamCaptureModeThreadLocal));
+    int rc = pulscan_rfft(p, d_x, d_spec, cs);
+    if (!rc) rc = pulscan_power_normalise(p, d_spec, d_power, nullptr, cs);
+    if (!rc) rc = pulscan_boxcar_search(p, d_power, cs);
     cudaGraph_t graph = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    const cudaError_t ec = cudaStreamEndCapture(g.capture, &graph);
     p->timing = timing;
     if (rc) {
       if (graph) cudaGraphDestroy(graph);
@@ -453,9 +481,42 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
     g.x = d_x;
     g.spec = d_spec;
     g.power = d_power;
-    g.stream = s;
   }
   PS_CUDA(cudaGraphLaunch(g.exec, s));
+  return PULSCAN_OK;
+}
+
+int pulscan_search_host(pulscan_plan p, const float *h_x, pulscan_cand *h_out, int64_t cap, int64_t *n_out,
+                        int use_graph, pulscan_stream stream) {
+  if (!p || !h_x || !n_out) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  if (!p->own_x) {
+    int rc = dalloc(&p->own_x, p->x_floats);
+    if (!rc) rc = dalloc(&p->own_spec, 2 * p->spec_bins);
+    if (!rc) rc = dalloc(&p->own_power, p->p_floats);
+    if (rc) return rc;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  PS_CUDA(cudaMemcpyAsync(p->own_x, h_x, p->x_floats * sizeof(float), cudaMemcpyHostToDevice, s));
+  const int rc = pulscan_search(p, p->own_x, p->own_spec, p->own_power, use_graph, stream);
+  if (rc) return rc;
+  return pulscan_candidates(p, h_out, cap, n_out, stream);
+}
+
+int pulscan_plan_counters(pulscan_plan p, int64_t *h_out, int32_t n) {
+  if (!p || !h_out || n < 0) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
+  uint32_t ctr[4];
+  PS_CUDA(cudaMemcpy(ctr, p->d_counters, sizeof(ctr), cudaMemcpyDeviceToHost));
+  const int64_t vals[4] = {ctr[0], p->item_cap, ctr[1], p->max_cands};
+  for (int i = 0; i < std::min(n, 4); ++i) h_out[i] = vals[i];
+  return PULSCAN_OK;
+}
+
+int pulscan_plan_set_defer_capacity(pulscan_plan p, int64_t cap) {
+  if (!p || cap < 0) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
+  const int64_t nb = (p->z_max + kR - 1) / kR;
+  const int64_t limit = p->alloc_item_cap;
+  p->item_cap = std::min<int64_t>(cap, limit);
+  (void)nb;
   return PULSCAN_OK;
 }
 
@@ -472,7 +533,7 @@ int pulscan_plan_enable_timing(pulscan_plan p, int on) {
 
 int pulscan_plan_timings(pulscan_plan p, float *h_ms, int32_t n) {
   if (!p || !h_ms || n < 0) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
-  for (int i = 0; i < std::min(n, 5); ++i) {
+  for (int i = 0; i < std::min(n, 6); ++i) {
     h_ms[i] = -1.0f;
     if (!p->ran[i] || !p->ev[2 * i]) continue;
     PS_CUDA(cudaEventSynchronize(p->ev[2 * i + 1]));

@@ -48,7 +48,7 @@ __host__ __device__ inline double log_q_gamma(double a, double x) {
     d = 1.0 / d;
     const double del = d * c;
     h *= del;
-    if (fabs(del - 1.0) < 1e-16) break;
+    if (fabs(del - 1.0) < 4e-16) break;   // two ulps of 1: FP64 convergence
   }
   return lpre + log(h);
 }
@@ -58,12 +58,17 @@ __host__ __device__ inline double log_q_gamma(double a, double x) {
 __device__ inline double sigma_from_log_p(double lp) {
   const double t = -2.0 * lp;
   double s = (t > 2.0) ? sqrt(fmax(t - log(t) - 1.8378770664093453, 0.0)) : 0.0;  // ln(2 pi)
-  for (int it = 0; it < 60; ++it) {
+  // stop at a relative step of 1e-12 (the result is stored in FP32), or once
+  // the steps stop shrinking: then they are FP64 rounding noise of ln Phi_c
+  double prev = INFINITY;
+  for (int it = 0; it < 40; ++it) {
     const double e = erfcx(s * 0.70710678118654752);
     const double f = log(0.5 * e) - 0.5 * s * s - lp;
     const double step = f * e * 1.2533141373155003;  // sqrt(pi / 2)
+    if (it >= 3 && !(fabs(step) < prev)) break;
     s += step;
-    if (fabs(step) <= 1e-15 * fmax(1.0, fabs(s))) break;
+    prev = fabs(step);
+    if (prev <= 1e-12 * fmax(1.0, fabs(s))) break;
   }
   return s;
 }

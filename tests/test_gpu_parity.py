@@ -157,3 +157,18 @@ def test_batch_uneven_lengths(pkg):
         mx_ref, am_ref = parity.check_maxima(p64, out["mx"][rows], out["am"][rows], w_max, seg_len)
         parity.check_candidates(out["cands"], p64, mx_ref, am_ref, w_max, seg_len, sigma,
                                 parity.n_trials_of(m, w_max), series=i)
+
+
+def test_deferred_overflow_falls_back_to_inline_exact(pkg):
+    """With no room for deferred blocks every flagged block is inspected by its own warp."""
+    n, w_max, seg_len, sigma = 1 << 16, 100, 1024, 3.0
+    x = _series(n, seed=9)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    a = parity.run_gpu(plan, x, maxima=False)
+    deferred = plan.counters()[0]
+    plan.set_defer_capacity(0)
+    b = parity.run_gpu(plan, x, maxima=False)
+    assert deferred > 0 and plan.counters()[0] >= deferred
+    ka = np.sort(a["cands"], order=["series", "bin", "width"])
+    kb = np.sort(b["cands"], order=["series", "bin", "width"])
+    assert np.array_equal(ka, kb)

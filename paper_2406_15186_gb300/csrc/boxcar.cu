@@ -293,11 +293,12 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
     tma_load_1d(buf, src, static_cast<uint32_t>(n_tma) * 4u, bar);
   }
   for (int i = n_tma + threadIdx.x; i < buf_len; i += nthreads) buf[i] = (i < avail) ? src[i] : 0.0f;
-  if (n_tma > 0) {
-    if (!mbar_wait_bounded(bar, 0, 2000000000ull)) {
-      if (threadIdx.x == 0) atomicOr(counters + 2, kErrTimeout);
-      return;   // nothing else is in flight: the only copy is this one
-    }
+  // one thread waits on the copy (bounded); the others sleep in the barrier
+  if (threadIdx.x == 0) q33[0] = (n_tma == 0 || mbar_wait_bounded(bar, 0, 2000000000ull)) ? 1.0f : 0.0f;
+  __syncthreads();
+  if (q33[0] == 0.0f) {
+    if (threadIdx.x == 0) atomicOr(counters + 2, kErrTimeout);
+    return;   // nothing else is in flight: the only copy is this one
   }
   __syncthreads();
 

@@ -38,7 +38,7 @@ constexpr int kSub = 11;                 // early sub-block edge (kR = 3 * kSub)
 constexpr int kEarlyBlocks = 4;          // widths <= 132 use the finer bound
 
 // Normalisation kernel
-constexpr int kNormThreads = 512;
+constexpr int kNormThreads = 256;
 constexpr int kHistBins = 2048;
 
 // ---------------------------------------------------------------- plan
@@ -102,6 +102,7 @@ struct pulscan_plan_s {
   float *d_thresh = nullptr;       // n_series * z_max
   float *d_thresh_bound = nullptr; // same, scaled down slightly for bound checks
   double *d_ln_trials = nullptr;   // ln(n_trials) per series
+  float *d_gtab = nullptr;         // g(w) = w ln w - w - ln Gamma(w), w = 1..z_max
   float *d_stats = nullptr;        // 4 * total_seg
   unsigned long long *d_slots = nullptr;  // total_seg * z_max keys, 0 at rest
   uint32_t *d_dirty = nullptr;     // one bit per slot touched by the search, 0 at rest

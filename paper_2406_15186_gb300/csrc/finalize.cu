@@ -8,7 +8,8 @@
 // one slot per lane, grid-stride), visits the slots whose bits are set, converts each to a
 // record, computes
 // ln p = ln Q(w, S) + ln n_trials (Bonferroni, capped at 0) and the
-// Gaussian-equivalent sigma in FP64, appends the record, and clears the slot
+// Gaussian-equivalent sigma (FP32, cancellation-free form, see signif.cuh),
+// appends the record, and clears the slot
 // and the bitmap word so both are zero again for the next search.
 #include <algorithm>
 
@@ -23,6 +24,7 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t
                                 int64_t n_words, uint32_t *__restrict__ counters, int W,
                                 const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
                                 int n_series, const double *__restrict__ ln_trials,
+                                const float *__restrict__ gtab,
                                 pulscan_cand *__restrict__ cands, uint32_t max_cands) {
   // one warp per bitmap word, one lane per bit: the FP64 significance of
   // neighbouring (segment, width) slots is evaluated in parallel
@@ -52,8 +54,9 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t
     }
     const float pw = __uint_as_float(static_cast<uint32_t>(key >> 32));
     const uint32_t bin = 0xffffffffu - static_cast<uint32_t>(key & 0xffffffffull);
-    const double lp = fmin(0.0, log_q_gamma(static_cast<double>(w), static_cast<double>(pw)) + ln_trials[lo]);
-    const double sg = sigma_from_log_p(lp);
+    const float lp = fminf(0.0f, log_q_f32(static_cast<float>(w), pw, gtab[w - 1]) +
+                                     static_cast<float>(ln_trials[lo]));
+    const float sg = sigma_from_log_p_f32(lp);
     const uint32_t o = base + static_cast<uint32_t>(__popc(act & ((1u << lane) - 1u)));
     if (o < max_cands) {
       pulscan_cand c;
@@ -61,7 +64,7 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t
       c.width = static_cast<uint32_t>(w);
       c.bin = bin;
       c.power = pw;
-      c.sigma = static_cast<float>(sg);
+      c.sigma = sg;
       cands[o] = c;
     }
   }
@@ -74,7 +77,7 @@ int launch_finalize(pulscan_plan p, cudaStream_t s) {
   const int grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>((words + 7) / 8, 1), 2432));
   finalize_kernel<<<grid, 256, 0, s>>>(p->d_slots, p->d_dirty, words, p->d_counters, p->z_max, p->d_series,
                                        p->d_seg_off, static_cast<int>(p->series.size()), p->d_ln_trials,
-                                       p->d_cands, static_cast<uint32_t>(p->max_cands));
+                                       p->d_gtab, p->d_cands, static_cast<uint32_t>(p->max_cands));
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }

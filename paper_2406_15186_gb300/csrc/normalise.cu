@@ -1,15 +1,24 @@
 // Per-segment median/MAD normalisation and power (paper §2.2.3, Eq. 8).
 //
-// One CTA per segment (normalisation block).  The block's complex bins are
-// staged into shared memory by one TMA bulk copy (or read from global memory
-// when the block is too large for shared memory).  The real and imaginary
-// parts are normalised separately, as Eq. 8 prescribes, with EXACT order
-// statistics: a radix select on order-preserving 32-bit keys of the FP32
-// values (digits of 11, 11 and 10 bits, one shared-memory histogram per
-// component, both components in the same pass) finds the rank-j element; an
-// even count takes the mean of ranks n/2-1 and n/2, the second found from the
-// first's multiplicity or by one min-reduction.  The MAD is the same select on
-// |x - median|.  Then a = (x - med) / (kappa MAD), kappa = 1/Phi^{-1}(3/4),
+// One CTA of 256 threads per segment (normalisation block).  The block's
+// complex bins are staged into shared memory by one TMA bulk copy (or read
+// from global memory when the block is too large for shared memory).  The
+// real and imaginary parts are normalised separately, as Eq. 8 prescribes,
+// with EXACT order statistics found by a value-bucket select that serves both
+// components at once:
+//   * bucket b(x) = floor((x - lo) * scale) over the block's [lo, hi] is
+//     non-decreasing in x (each step is a monotone rounding), so the rank-r
+//     element lies in the bucket where the cumulative count passes r;
+//   * one histogram pass (2048 buckets per component), one block-wide scan,
+//     one gather pass of the target bucket(s) -- a handful of values for
+//     noise -- and one warp per component ranks them;
+//   * if a target bucket is crowded (a block dominated by a strong tone) the
+//     select refines it level by level: the bucket's [min, max] becomes the
+//     next range and only its elements are bucketed again; a range with
+//     min == max means every remaining candidate is equal.
+// An even count takes the mean of ranks n/2-1 and n/2.  The MAD is the same
+// select on |x - median|, whose range [0, max deviation] follows from the
+// median pass.  Then a = (x - med) / (kappa MAD), kappa = 1/Phi^{-1}(3/4),
 // and P = (a^2 + b^2)/2, written coalesced.  The DC bin of a series is taken
 // as 0 + 0i.  A segment whose MAD is 0 gets P = 0.
 //
@@ -26,125 +35,287 @@ namespace ps {
 namespace {
 
 constexpr double kKappa = 1.482602218505602;  // 1 / Phi^{-1}(3/4)
-constexpr int kMaxSmemBins = 24576;            // float2 elements staged in shared memory
-
-__device__ __forceinline__ uint32_t fkey(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float kfloat(uint32_t k) {
-  const uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
-  return __uint_as_float(u);
-}
+constexpr int kMaxSmemBins = 16384 + 4096;     // float2 elements staged in shared memory
+constexpr int kStoreBins = 8192;               // blocks up to this size keep their bucket indices
+constexpr int kBuckets = kHistBins;            // value buckets per level
+constexpr int kPerThread = kBuckets / (kNormThreads / 2);   // buckets per scanning thread
+constexpr int kCap = 256;                      // values ranked directly
+constexpr int kMaxLevels = 8;
+constexpr int kWarpsN = kNormThreads / 32;
 
 struct SelShared {
-  uint32_t hist[2][kHistBins];
-  uint32_t wsum[2][8];
-  uint32_t prefix[2];
-  uint32_t rem[2];
-  uint32_t cnt[2];
-  uint32_t minkey[2];
-  float med[2];
-  float mad[2];
+  uint32_t hist[2][kBuckets];
+  uint32_t wsum[2][kWarpsN / 2];
+  float red[kWarpsN][4];
+  float lo[kMaxLevels][2], scale[kMaxLevels][2];
+  uint32_t b1[kMaxLevels][2], b2[kMaxLevels][2];
+  uint32_t rank[2], below[2], cnt[2], list_n[2];
+  float list[2][kCap];
+  float res[2][2];
+  float mm[4];     // block min0, min1, max0, max1
+  int done[2];
+  uint32_t flag;
 };
 
-// Block-wide: component c = threadIdx / 256 scans its 2048-bin histogram
-// (8 bins per thread) and locates the digit holding rank rem[c].
-__device__ __forceinline__ void find_digit(SelShared &sh, int shift) {
-  const int c = threadIdx.x >> 8;
-  const int t = threadIdx.x & 255;
-  const uint32_t *h = sh.hist[c] + 8 * t;
+__device__ __forceinline__ uint32_t bucket_of(float x, float lo, float scale) {
+  const float t = (x - lo) * scale;
+  return min(static_cast<uint32_t>(fmaxf(t, 0.0f)), static_cast<uint32_t>(kBuckets - 1));
+}
+
+__device__ __forceinline__ float bucket_scale(float lo, float hi) {
+  // shrink a hair so that hi stays in the last bucket
+  return (hi > lo) ? static_cast<float>(kBuckets) / (hi - lo) * (1.0f - 1.0f / 4096.0f) : 0.0f;
+}
+
+// Block min/max of both components over the values cand(e, v0, c0, v1, c1)
+// flags as candidates; result in sh.mm.
+template <class Cand>
+__device__ __forceinline__ void block_minmax(SelShared &sh, Cand cand, int n) {
+  float a0 = INFINITY, a1 = INFINITY, z0 = -INFINITY, z1 = -INFINITY;
+  for (int e = threadIdx.x; e < n; e += kNormThreads) {
+    float v0, v1;
+    bool c0, c1;
+    cand(e, v0, c0, v1, c1);
+    if (c0) { a0 = fminf(a0, v0); z0 = fmaxf(z0, v0); }
+    if (c1) { a1 = fminf(a1, v1); z1 = fmaxf(z1, v1); }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 = fminf(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+    a1 = fminf(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+    z0 = fmaxf(z0, __shfl_xor_sync(0xffffffffu, z0, o));
+    z1 = fmaxf(z1, __shfl_xor_sync(0xffffffffu, z1, o));
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh.red[wid][0] = a0;
+    sh.red[wid][1] = a1;
+    sh.red[wid][2] = z0;
+    sh.red[wid][3] = z1;
+  }
+  __syncthreads();
+  if (wid == 0 && lane < 4) {
+    // lane k reduces column k over the warps
+    float r = (lane < 2) ? INFINITY : -INFINITY;
+    for (int w = 0; w < kWarpsN; ++w) r = (lane < 2) ? fminf(r, sh.red[w][lane]) : fmaxf(r, sh.red[w][lane]);
+    sh.mm[lane] = r;
+  }
+  __syncthreads();
+}
+
+// Block-wide scan of both histograms: threads [0, 128) scan component 0,
+// [128, 256) component 1, kPerThread consecutive buckets each (summed in a
+// skewed order to spread banks).  Writes the buckets holding ranks r and
+// r + pair, the count below the first and the cumulative count through the
+// second.
+__device__ __forceinline__ void scan_find(SelShared &sh, int level, bool pair) {
+  const int c = threadIdx.x / (kNormThreads / 2);
+  const int t = threadIdx.x % (kNormThreads / 2);
+  const uint32_t *h = sh.hist[c] + kPerThread * t;
   uint32_t local = 0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) local += h[j];
-  // inclusive scan of `local` over the 256 threads of this component
+  for (int j = 0; j < kPerThread; ++j) local += h[(j + t) & (kPerThread - 1)];
   const int lane = t & 31, wid = t >> 5;
-  uint32_t v = local;
+  uint32_t incl = local;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += u;
+    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
   }
-  if (lane == 31) sh.wsum[c][wid] = v;
+  if (lane == 31) sh.wsum[c][wid] = incl;
   __syncthreads();
   uint32_t base = 0;
   for (int j = 0; j < wid; ++j) base += sh.wsum[c][j];
-  const uint32_t excl = base + v - local;
-  const uint32_t r = sh.rem[c];
-  __syncthreads();   // everyone has read rem before it is updated
-  if (r >= excl && r < excl + local) {
+  const uint32_t excl = base + incl - local;
+  const uint32_t r1 = sh.rank[c];
+  const uint32_t r2 = r1 + (pair ? 1u : 0u);
+  if (!sh.done[c] && ((r1 >= excl && r1 < excl + local) || (r2 >= excl && r2 < excl + local))) {
     uint32_t acc = excl;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (r < acc + h[j]) {
-        sh.prefix[c] |= static_cast<uint32_t>(8 * t + j) << shift;
-        sh.rem[c] = r - acc;
-        sh.cnt[c] = h[j];
-        break;
+    for (int j = 0; j < kPerThread; ++j) {
+      const uint32_t nxt = acc + h[j];
+      if (r1 >= acc && r1 < nxt) {
+        sh.b1[level][c] = kPerThread * t + j;
+        sh.below[c] = acc;
       }
-      acc += h[j];
+      if (r2 >= acc && r2 < nxt) {
+        sh.b2[level][c] = kPerThread * t + j;
+        sh.cnt[c] = nxt;
+      }
+      acc = nxt;
     }
   }
+  __syncthreads();
 }
 
-// Keys of the rank-`rank` and rank-`rank+1` (if `pair`) elements of both
-// components; get(e) returns the element's (re-key, im-key).
-template <class Get>
-__device__ __forceinline__ void select2(SelShared &sh, Get get, int n, uint32_t rank, bool pair,
-                                        uint32_t (&k_lo)[2], uint32_t (&k_hi)[2]) {
-  if (threadIdx.x < 2) {
-    sh.prefix[threadIdx.x] = 0u;
-    sh.rem[threadIdx.x] = rank;
-    sh.cnt[threadIdx.x] = 0u;
-    sh.minkey[threadIdx.x] = 0xffffffffu;
-  }
-  uint32_t mask = 0u;
-  const int shifts[3] = {21, 10, 0};
-  const uint32_t dmasks[3] = {0x7ffu, 0x7ffu, 0x3ffu};
-#pragma unroll
-  for (int pass = 0; pass < 3; ++pass) {
-    for (int j = threadIdx.x; j < 2 * kHistBins; j += kNormThreads) (&sh.hist[0][0])[j] = 0u;
-    __syncthreads();
-    const uint32_t p0 = sh.prefix[0], p1 = sh.prefix[1];
-    const int sh_ = shifts[pass];
-    const uint32_t dm = dmasks[pass];
-    for (int e = threadIdx.x; e < n; e += kNormThreads) {
-      const uint2 k = get(e);
-      if ((k.x & mask) == p0) atomicAdd(&sh.hist[0][(k.x >> sh_) & dm], 1u);
-      if ((k.y & mask) == p1) atomicAdd(&sh.hist[1][(k.y >> sh_) & dm], 1u);
+// One warp per component ranks its gathered list (ties by list position)
+// and stores the values of ranks `want` and `want + 1`.
+__device__ __forceinline__ void rank_lists(SelShared &sh, const bool (&active)[2], bool pair) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 2 && active[warp]) {
+    const int c = warp;
+    const uint32_t m = sh.list_n[c];
+    const uint32_t want = sh.rank[c] - sh.below[c];
+    for (uint32_t i = lane; i < m; i += 32) {
+      const float v = sh.list[c][i];
+      uint32_t rk = 0;
+      for (uint32_t f = 0; f < m; ++f) {
+        const float u = sh.list[c][f];
+        rk += (u < v || (u == v && f < i)) ? 1u : 0u;
+      }
+      if (rk == want) sh.res[c][0] = v;
+      if (pair && rk == want + 1) sh.res[c][1] = v;
     }
-    __syncthreads();
-    find_digit(sh, sh_);
-    __syncthreads();
-    mask |= dm << sh_;
   }
-  k_lo[0] = sh.prefix[0];
-  k_lo[1] = sh.prefix[1];
-  if (!pair) {
-    __syncthreads();   // all reads of sh done before the next select resets it
-    return;
-  }
-  // rank+1: the same key if it repeats, else the smallest larger key
-  const bool need0 = sh.rem[0] + 1 >= sh.cnt[0];
-  const bool need1 = sh.rem[1] + 1 >= sh.cnt[1];
-  if (need0 || need1) {
-    uint32_t m0 = 0xffffffffu, m1 = 0xffffffffu;
-    for (int e = threadIdx.x; e < n; e += kNormThreads) {
-      const uint2 k = get(e);
-      if (k.x > k_lo[0]) m0 = min(m0, k.x);
-      if (k.y > k_lo[1]) m1 = min(m1, k.y);
-    }
-    m0 = __reduce_min_sync(0xffffffffu, m0);
-    m1 = __reduce_min_sync(0xffffffffu, m1);
-    if ((threadIdx.x & 31) == 0) {
-      atomicMin(&sh.minkey[0], m0);
-      atomicMin(&sh.minkey[1], m1);
-    }
-    __syncthreads();
-  }
-  k_hi[0] = need0 ? sh.minkey[0] : k_lo[0];
-  k_hi[1] = need1 ? sh.minkey[1] : k_lo[1];
   __syncthreads();
+}
+
+// Multi-level select (the general path): get(e, v0, v1) gives element e's
+// two component values; level 0 starts from the whole block.
+template <class Get>
+__device__ void select_levels(SelShared &sh, Get get, int n, uint32_t rank, bool pair, float (&out_lo)[2],
+                              float (&out_hi)[2]) {
+  if (threadIdx.x < 2) {
+    sh.rank[threadIdx.x] = rank;
+    sh.done[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  auto cand = [&](int e, float &v0, bool &c0, float &v1, bool &c1, int levels) {
+    get(e, v0, v1);
+    c0 = !sh.done[0];
+    c1 = !sh.done[1];
+    for (int L = 0; L < levels; ++L) {
+      if (c0) {
+        const uint32_t b = bucket_of(v0, sh.lo[L][0], sh.scale[L][0]);
+        c0 = b >= sh.b1[L][0] && b <= sh.b2[L][0];
+      }
+      if (c1) {
+        const uint32_t b = bucket_of(v1, sh.lo[L][1], sh.scale[L][1]);
+        c1 = b >= sh.b1[L][1] && b <= sh.b2[L][1];
+      }
+    }
+  };
+  for (int level = 0; level < kMaxLevels; ++level) {
+    block_minmax(sh, [&](int e, float &v0, bool &c0, float &v1, bool &c1) { cand(e, v0, c0, v1, c1, level); }, n);
+    if (threadIdx.x < 2) {
+      const int c = threadIdx.x;
+      sh.list_n[c] = 0u;
+      if (!sh.done[c]) {
+        const float mn = sh.mm[c], mx = sh.mm[2 + c];
+        if (!(mx > mn)) {
+          sh.res[c][0] = mn;   // every remaining candidate has this value
+          sh.res[c][1] = mn;
+          sh.done[c] = 1;
+        } else {
+          sh.lo[level][c] = mn;
+          sh.scale[level][c] = bucket_scale(mn, mx);
+        }
+      }
+    }
+    for (int j = threadIdx.x; j < 2 * kBuckets; j += kNormThreads) (&sh.hist[0][0])[j] = 0u;
+    __syncthreads();
+    if (sh.done[0] && sh.done[1]) break;
+    for (int e = threadIdx.x; e < n; e += kNormThreads) {
+      float v0, v1;
+      bool c0, c1;
+      cand(e, v0, c0, v1, c1, level);
+      if (c0) atomicAdd(&sh.hist[0][bucket_of(v0, sh.lo[level][0], sh.scale[level][0])], 1u);
+      if (c1) atomicAdd(&sh.hist[1][bucket_of(v1, sh.lo[level][1], sh.scale[level][1])], 1u);
+    }
+    __syncthreads();
+    scan_find(sh, level, pair);
+    bool gather[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) gather[c] = !sh.done[c] && (sh.cnt[c] - sh.below[c] <= static_cast<uint32_t>(kCap));
+    if (gather[0] || gather[1]) {
+      for (int e = threadIdx.x; e < n; e += kNormThreads) {
+        float v0, v1;
+        bool c0, c1;
+        cand(e, v0, c0, v1, c1, level + 1);   // includes this level's [b1, b2]
+        if (c0 && gather[0]) sh.list[0][atomicAdd(&sh.list_n[0], 1u)] = v0;
+        if (c1 && gather[1]) sh.list[1][atomicAdd(&sh.list_n[1], 1u)] = v1;
+      }
+      __syncthreads();
+      rank_lists(sh, gather, pair);
+    }
+    if (threadIdx.x < 2) {
+      const int c = threadIdx.x;
+      if (gather[c]) sh.done[c] = 1;
+      else if (!sh.done[c]) sh.rank[c] -= sh.below[c];   // the next level refines [b1, b2]
+    }
+    __syncthreads();
+    if (sh.done[0] && sh.done[1]) break;
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    out_lo[c] = sh.res[c][0];
+    out_hi[c] = pair ? sh.res[c][1] : sh.res[c][0];
+  }
+  __syncthreads();
+}
+
+// Level-0 select for both components over the known range [lo, hi]:
+// histogram (keeping each element's packed bucket indices in `bkt` when it is
+// given), scan, gather, rank.  Returns false, having decided nothing, when a
+// target bucket holds more than kCap values.
+template <class Get>
+__device__ __forceinline__ bool select_fast(SelShared &sh, Get get, uint32_t *bkt, int n, uint32_t rank, bool pair,
+                                            float lo0, float lo1, float hi0, float hi1, float (&out_lo)[2],
+                                            float (&out_hi)[2]) {
+  const float s0 = bucket_scale(lo0, hi0), s1 = bucket_scale(lo1, hi1);
+  const bool flat0 = !(hi0 > lo0), flat1 = !(hi1 > lo1);
+  for (int j = threadIdx.x; j < 2 * kBuckets; j += kNormThreads) (&sh.hist[0][0])[j] = 0u;
+  if (threadIdx.x < 2) {
+    sh.rank[threadIdx.x] = rank;
+    sh.done[threadIdx.x] = 0;
+    sh.list_n[threadIdx.x] = 0u;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += kNormThreads) {
+    float v0, v1;
+    get(e, v0, v1);
+    const uint32_t q0 = bucket_of(v0, lo0, s0), q1 = bucket_of(v1, lo1, s1);
+    atomicAdd(&sh.hist[0][q0], 1u);
+    atomicAdd(&sh.hist[1][q1], 1u);
+    if (bkt) bkt[e] = q0 | (q1 << 16);
+  }
+  __syncthreads();
+  scan_find(sh, 0, pair);
+  if ((!flat0 && sh.cnt[0] - sh.below[0] > static_cast<uint32_t>(kCap)) ||
+      (!flat1 && sh.cnt[1] - sh.below[1] > static_cast<uint32_t>(kCap))) {
+    __syncthreads();
+    return false;
+  }
+  // a flat component (all values equal) gathers nothing: its answer is lo
+  const uint32_t l0 = flat0 ? 1u : sh.b1[0][0], h0 = flat0 ? 0u : sh.b2[0][0];
+  const uint32_t l1 = flat1 ? 1u : sh.b1[0][1], h1 = flat1 ? 0u : sh.b2[0][1];
+  for (int e = threadIdx.x; e < n; e += kNormThreads) {
+    float v0, v1;
+    uint32_t q0, q1;
+    if (bkt) {
+      const uint32_t q = bkt[e];
+      q0 = q & 0xffffu;
+      q1 = q >> 16;
+    } else {
+      get(e, v0, v1);
+      q0 = bucket_of(v0, lo0, s0);
+      q1 = bucket_of(v1, lo1, s1);
+    }
+    const bool g0 = q0 >= l0 && q0 <= h0, g1 = q1 >= l1 && q1 <= h1;
+    if (g0 || g1) {
+      get(e, v0, v1);
+      if (g0) sh.list[0][atomicAdd(&sh.list_n[0], 1u)] = v0;
+      if (g1) sh.list[1][atomicAdd(&sh.list_n[1], 1u)] = v1;
+    }
+  }
+  __syncthreads();
+  const bool active[2] = {!flat0, !flat1};
+  rank_lists(sh, active, pair);
+  out_lo[0] = flat0 ? lo0 : sh.res[0][0];
+  out_lo[1] = flat1 ? lo1 : sh.res[1][0];
+  out_hi[0] = flat0 ? lo0 : (pair ? sh.res[0][1] : sh.res[0][0]);
+  out_hi[1] = flat1 ? lo1 : (pair ? sh.res[1][1] : sh.res[1][0]);
+  __syncthreads();
+  return true;
 }
 
 __device__ __forceinline__ float mean_of(float a, float b) {
@@ -154,11 +325,13 @@ __device__ __forceinline__ float mean_of(float a, float b) {
 __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
     const float2 *__restrict__ spec, float *__restrict__ power, float4 *__restrict__ stats,
     const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off, int n_series, int seg_len,
-    uint32_t *__restrict__ counters) {
+    uint32_t *__restrict__ counters, int smem_bins) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   SelShared &sh = *reinterpret_cast<SelShared *>(smem_raw + 128);
-  float2 *data = reinterpret_cast<float2 *>(smem_raw + 128 + ((sizeof(SelShared) + 127) & ~size_t(127)));
+  unsigned char *tail = smem_raw + 128 + ((sizeof(SelShared) + 127) & ~size_t(127));
+  float2 *data = reinterpret_cast<float2 *>(tail);
+  uint32_t *bkt_store = reinterpret_cast<uint32_t *>(tail + 8 * static_cast<size_t>(smem_bins));
 
   const int64_t g = blockIdx.x;
   int lo = 0, hi = n_series - 1;
@@ -172,7 +345,9 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
   const int64_t b1 = (sl == S.n_seg - 1) ? S.m : b0 + seg_len;
   const int n = static_cast<int>(b1 - b0);
   const float2 *src = spec + S.spec_off + b0;
-  const bool in_smem = n <= kMaxSmemBins;
+  const bool in_smem = n <= smem_bins;
+  // bucket indices are kept only where the launch reserved room for them
+  uint32_t *bkt = (in_smem && smem_bins <= kStoreBins) ? bkt_store : nullptr;
 
   if (in_smem) {
     // float2 pairs: a 16-byte multiple from a 16-byte aligned source
@@ -184,11 +359,13 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
       tma_load_1d(data, src, static_cast<uint32_t>(n_tma) * 8u, bar);
     }
     for (int e = n_tma + threadIdx.x; e < n; e += kNormThreads) data[e] = src[e];
-    if (n_tma > 0 && !mbar_wait_bounded(bar, 0, 2000000000ull)) {
+    // one thread waits on the copy (bounded); the others sleep in the barrier
+    if (threadIdx.x == 0) sh.flag = (n_tma == 0 || mbar_wait_bounded(bar, 0, 2000000000ull)) ? 1u : 0u;
+    __syncthreads();
+    if (sh.flag == 0u) {
       if (threadIdx.x == 0) atomicOr(counters + 2, kErrTimeout);
       return;
     }
-    __syncthreads();
     if (b0 == 0 && threadIdx.x == 0) data[0] = make_float2(0.0f, 0.0f);   // DC := 0
     __syncthreads();
   }
@@ -202,21 +379,42 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
   const bool even = (n % 2) == 0;
   const uint32_t rank = even ? static_cast<uint32_t>(n / 2 - 1) : static_cast<uint32_t>(n / 2);
 
+  // range of both components
+  block_minmax(sh,
+               [&](int e, float &v0, bool &c0, float &v1, bool &c1) {
+                 const float2 v = val(e);
+                 v0 = v.x;
+                 v1 = v.y;
+                 c0 = c1 = true;
+               },
+               n);
+  const float mn0 = sh.mm[0], mn1 = sh.mm[1], mx0 = sh.mm[2], mx1 = sh.mm[3];
+  __syncthreads();
+
   // medians
-  uint32_t klo[2], khi[2];
-  select2(sh, [&](int e) { const float2 v = val(e); return make_uint2(fkey(v.x), fkey(v.y)); }, n, rank,
-          even, klo, khi);
-  const float med_re = even ? mean_of(kfloat(klo[0]), kfloat(khi[0])) : kfloat(klo[0]);
-  const float med_im = even ? mean_of(kfloat(klo[1]), kfloat(khi[1])) : kfloat(klo[1]);
-  // MADs: the same select on |x - med| (non-negative floats)
-  select2(sh,
-          [&](int e) {
-            const float2 v = val(e);
-            return make_uint2(fkey(fabsf(v.x - med_re)), fkey(fabsf(v.y - med_im)));
-          },
-          n, rank, even, klo, khi);
-  const float mad_re = even ? mean_of(kfloat(klo[0]), kfloat(khi[0])) : kfloat(klo[0]);
-  const float mad_im = even ? mean_of(kfloat(klo[1]), kfloat(khi[1])) : kfloat(klo[1]);
+  auto raw = [&](int e, float &v0, float &v1) {
+    const float2 v = val(e);
+    v0 = v.x;
+    v1 = v.y;
+  };
+  float lo_v[2], hi_v[2];
+  if (!select_fast(sh, raw, bkt, n, rank, even, mn0, mn1, mx0, mx1, lo_v, hi_v))
+    select_levels(sh, raw, n, rank, even, lo_v, hi_v);
+  const float med_re = even ? mean_of(lo_v[0], hi_v[0]) : lo_v[0];
+  const float med_im = even ? mean_of(lo_v[1], hi_v[1]) : lo_v[1];
+
+  // MADs: the same selection on |x - med|, over [0, max deviation]
+  auto dev = [&](int e, float &v0, float &v1) {
+    const float2 v = val(e);
+    v0 = fabsf(v.x - med_re);
+    v1 = fabsf(v.y - med_im);
+  };
+  const float dh0 = fmaxf(fabsf(mx0 - med_re), fabsf(med_re - mn0));
+  const float dh1 = fmaxf(fabsf(mx1 - med_im), fabsf(med_im - mn1));
+  if (!select_fast(sh, dev, bkt, n, rank, even, 0.0f, 0.0f, dh0, dh1, lo_v, hi_v))
+    select_levels(sh, dev, n, rank, even, lo_v, hi_v);
+  const float mad_re = even ? mean_of(lo_v[0], hi_v[0]) : lo_v[0];
+  const float mad_im = even ? mean_of(lo_v[1], hi_v[1]) : lo_v[1];
 
   const bool degenerate = !(mad_re > 0.0f) || !(mad_im > 0.0f);
   const float inv_re = degenerate ? 0.0f : static_cast<float>(1.0 / (kKappa * static_cast<double>(mad_re)));
@@ -231,30 +429,34 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
   if (threadIdx.x == 0 && stats != nullptr) stats[g] = make_float4(med_re, mad_re, med_im, mad_im);
 }
 
-}  // namespace
-
-static int normalise_smem(pulscan_plan p) {
+int normalise_smem(pulscan_plan p, int *bins_out) {
   int64_t max_n = 0;
   for (const auto &se : p->series) {
     const int64_t last = se.m - (se.n_seg - 1) * p->seg_len;
     max_n = std::max<int64_t>(max_n, last);
   }
-  const int data_bins = static_cast<int>(std::min<int64_t>(max_n, kMaxSmemBins));
-  return 128 + static_cast<int>((sizeof(SelShared) + 127) & ~size_t(127)) + 8 * data_bins;
+  const int bins = static_cast<int>(std::min<int64_t>(max_n, kMaxSmemBins));
+  const int store = (bins <= kStoreBins) ? bins : 0;
+  if (bins_out) *bins_out = bins;
+  return 128 + static_cast<int>((sizeof(SelShared) + 127) & ~size_t(127)) + 8 * bins + 4 * store;
 }
 
+}  // namespace
+
 int prepare_normalise(pulscan_plan p) {
-  PS_CUDA(cudaFuncSetAttribute(normalise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, normalise_smem(p)));
+  PS_CUDA(cudaFuncSetAttribute(normalise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               normalise_smem(p, nullptr)));
   return PULSCAN_OK;
 }
 
 int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, cudaStream_t s) {
-  const int smem = normalise_smem(p);
+  int bins = 0;
+  const int smem = normalise_smem(p, &bins);
   if (p->total_seg > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many segments");
   float4 *st = d_stats ? reinterpret_cast<float4 *>(d_stats) : reinterpret_cast<float4 *>(p->d_stats);
   normalise_kernel<<<static_cast<unsigned>(p->total_seg), kNormThreads, smem, s>>>(
       reinterpret_cast<const float2 *>(d_spec), d_power, st, p->d_series, p->d_seg_off,
-      static_cast<int>(p->series.size()), p->seg_len, p->d_counters);
+      static_cast<int>(p->series.size()), p->seg_len, p->d_counters, bins);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }

@@ -110,7 +110,7 @@ static void free_plan(pulscan_plan p) {
     if (f.handle) cufftDestroy(f.handle);
   void *ptrs[] = {p->d_series, p->d_tile_off, p->d_seg_off, p->d_thresh, p->d_thresh_bound, p->d_ln_trials,
                   p->d_stats,  p->d_slots,    p->d_dirty,   p->d_counters, p->d_cands,     p->own_x,
-                  p->own_spec, p->own_power, p->d_items, p->d_snaps};
+                  p->own_spec, p->own_power, p->d_items, p->d_snaps,    p->d_gtab};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (auto &e : p->ev)
@@ -229,7 +229,8 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
       ok(dalloc(&p->d_ln_trials, ns)) && ok(dalloc(&p->d_stats, 4 * sg)) &&
       ok(dalloc(&p->d_slots, total_slots)) && ok(dalloc(&p->d_dirty, dirty_words)) &&
       ok(dalloc(&p->d_counters, 4)) && ok(dalloc(&p->d_cands, p->max_cands)) &&
-      ok(dalloc(&p->d_items, p->item_cap)) && ok(dalloc(&p->d_snaps, p->item_cap * kR * 32))) {
+      ok(dalloc(&p->d_items, p->item_cap)) && ok(dalloc(&p->d_snaps, p->item_cap * kR * 32)) &&
+      ok(dalloc(&p->d_gtab, z_max))) {
     std::vector<SeriesDev> sd(ns);
     std::vector<int64_t> to(ns + 1), so(ns + 1);
     for (size_t i = 0; i < ns; ++i) {
@@ -247,6 +248,9 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
     ok(cuda_ok_or(cudaMemset(p->d_dirty, 0, dirty_words * sizeof(uint32_t))));
     ok(cuda_ok_or(cudaMemset(p->d_counters, 0, 4 * sizeof(uint32_t))));
     ok(upload_thresholds(p));
+    std::vector<float> gt(z_max);
+    for (int w = 1; w <= z_max; ++w) gt[w - 1] = static_cast<float>(g_of(static_cast<double>(w)));
+    ok(cuda_ok_or(cudaMemcpy(p->d_gtab, gt.data(), z_max * sizeof(float), cudaMemcpyHostToDevice)));
     ok(prepare_bank(p));
     ok(prepare_normalise(p));
   }

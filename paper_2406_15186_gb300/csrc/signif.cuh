@@ -1,5 +1,5 @@
-// Chi-square significance used by the plan (threshold table, host) and by
-// the candidate finaliser (device), in FP64.
+// Chi-square significance used by the plan (threshold table, host, FP64) and
+// by the candidate finaliser (device, FP32: GB300's FP64 rate is 1/64 of FP32).
 //
 // Paper §2.2.3, Eq. 9: a width-w boxcar of normalised power is a sum of w
 // chi^2(2) variables.  With P = (a^2 + b^2)/2 a width-w sum S has 2S ~
@@ -53,7 +53,75 @@ __host__ __device__ inline double log_q_gamma(double a, double x) {
   return lpre + log(h);
 }
 
+// g(a) = a ln a - a - ln Gamma(a): with lambda = x / a and delta = lambda - 1,
+//   ln(x^a e^-x / Gamma(a)) = -a (delta - ln(1 + delta)) + g(a)
+// exactly, and both terms are free of cancellation (g(a) is O(ln a)).  The
+// host tabulates g per width in FP64 so the device can work in FP32.
+inline double g_of(double a) { return a * log(a) - a - lgamma(a); }
+
 #ifdef __CUDACC__
+// delta - ln(1 + delta), >= 0; a power series near 0 avoids the cancellation.
+__device__ inline float h_delta_f32(float d) {
+  if (fabsf(d) < 0.25f) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 16; k >= 2; --k) acc = fmaf(acc, d, ((k & 1) ? -1.0f : 1.0f) / static_cast<float>(k));
+    return acc * d * d;
+  }
+  return d - log1pf(d);
+}
+
+// ln Q(a, x) in FP32 from the cancellation-free prefactor above and the same
+// series / continued fraction as log_q_gamma.  Absolute error ~1e-4 at
+// ln Q ~ -500 (relative ~3e-7), far inside what an FP32 sigma resolves.
+__device__ inline float log_q_f32(float a, float x, float g) {
+  if (!(x > 0.0f)) return 0.0f;
+  const float lpre = -a * h_delta_f32((x - a) / a) + g;
+  if (x < a + 1.0f) {
+    float ap = a, del = 1.0f / a, sum = del;
+    for (int n = 0; n < 20000; ++n) {
+      ap += 1.0f;
+      del *= x / ap;
+      sum += del;
+      if (fabsf(del) < fabsf(sum) * 1e-8f) break;
+    }
+    return log1pf(-expf(lpre + logf(sum)));
+  }
+  const float tiny = 1e-30f;
+  float b = x + 1.0f - a, c = 1.0f / tiny, d = 1.0f / b, h = d;
+  for (int i = 1; i < 2000; ++i) {
+    const float an = -static_cast<float>(i) * (static_cast<float>(i) - a);
+    b += 2.0f;
+    d = fmaf(an, d, b);
+    if (fabsf(d) < tiny) d = tiny;
+    c = b + an / c;
+    if (fabsf(c) < tiny) c = tiny;
+    d = 1.0f / d;
+    const float del = d * c;
+    h *= del;
+    if (fabsf(del - 1.0f) < 2.4e-7f) break;
+  }
+  return lpre + logf(h);
+}
+
+// sigma with ln Phi_c(sigma) = lp <= ln(1/2), FP32 Newton on
+// ln Phi_c(s) = ln(erfcx(s / sqrt 2) / 2) - s^2 / 2.
+__device__ inline float sigma_from_log_p_f32(float lp) {
+  const float t = -2.0f * lp;
+  float s = (t > 2.0f) ? sqrtf(fmaxf(t - logf(t) - 1.8378770664f, 0.0f)) : 0.0f;
+  float prev = INFINITY;
+  for (int it = 0; it < 20; ++it) {
+    const float e = erfcxf(s * 0.70710678f);
+    const float f = logf(0.5f * e) - 0.5f * s * s - lp;
+    const float step = f * e * 1.2533141f;
+    if (it >= 3 && !(fabsf(step) < prev)) break;
+    s += step;
+    prev = fabsf(step);
+    if (prev <= 1e-7f * fmaxf(1.0f, fabsf(s))) break;
+  }
+  return s;
+}
+
 // sigma with ln Phi_c(sigma) = lp, lp <= ln(1/2) (device: uses erfcx).
 __device__ inline double sigma_from_log_p(double lp) {
   const double t = -2.0 * lp;

@@ -557,12 +557,14 @@ int search_smem_bytes(int W, int warps, int *buf_len_out) {
   return 128 + 4 * (buf_len + nq33 + 1 + nq11 + 1);
 }
 
+SmemLimit g_lim_search, g_lim_dump;
+
 int prepare_bank(pulscan_plan p) {
   const int smem = search_smem_bytes(p->z_max, p->search_warps, nullptr);
   if (smem > 220 * 1024) return fail(PULSCAN_ERR_UNSUPPORTED, "z_max too large for the shared-memory tile");
-  PS_CUDA(cudaFuncSetAttribute(boxcar_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  PS_CUDA(cudaFuncSetAttribute(boxcar_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  return PULSCAN_OK;
+  int rc = ensure_smem(boxcar_kernel<true>, smem, g_lim_search);
+  if (!rc) rc = ensure_smem(boxcar_kernel<false>, smem, g_lim_dump);
+  return rc;
 }
 
 static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaStream_t s) {
@@ -573,6 +575,9 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
   const dim3 block(32 * p->search_warps);
   const int tile_bins = search_tile_bins(p->search_warps);
   const uint32_t cap = static_cast<uint32_t>(p->item_cap);
+  const int rc = search ? ensure_smem(boxcar_kernel<true>, smem, g_lim_search)
+                        : ensure_smem(boxcar_kernel<false>, smem, g_lim_dump);
+  if (rc) return rc;
   if (search) {
     boxcar_kernel<true><<<grid, block, smem, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
@@ -592,6 +597,28 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
         p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, 0u,
         tile_bins, buf_len);
   }
+  PS_CUDA(cudaGetLastError());
+  return PULSCAN_OK;
+}
+
+// Dump-mode launch with caller-supplied descriptor and scratch pointers
+// (used by the allocation-free entry point; no plan involved).
+int prepare_bank_raw(int W, int warps) {
+  return ensure_smem(boxcar_kernel<false>, search_smem_bytes(W, warps, nullptr), g_lim_dump);
+}
+
+int launch_segmax_raw(const float *d_power, const SeriesDev *d_series, const int64_t *d_tile_off, int64_t tiles,
+                      int warps, int W, int seg_len, unsigned long long *d_slots, uint32_t *d_counters,
+                      int64_t n_slots, float *d_max, uint64_t *d_argmax, cudaStream_t s) {
+  int buf_len = 0;
+  const int smem = search_smem_bytes(W, warps, &buf_len);
+  const int rc = ensure_smem(boxcar_kernel<false>, smem, g_lim_dump);
+  if (rc) return rc;
+  boxcar_kernel<false><<<static_cast<unsigned>(tiles), 32 * warps, smem, s>>>(
+      d_power, d_series, d_tile_off, 1, W, seg_len, nullptr, nullptr, d_slots, nullptr, d_counters, nullptr,
+      nullptr, 0u, search_tile_bins(warps), buf_len);
+  PS_CUDA(cudaGetLastError());
+  unpack_kernel<<<1024, 256, 0, s>>>(d_slots, n_slots, d_max, d_argmax);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }

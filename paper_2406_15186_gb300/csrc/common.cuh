@@ -7,6 +7,7 @@
 #include <cufft.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -24,6 +25,26 @@ int cuda_fail(cudaError_t e, const char *what);
     cudaError_t e__ = (call);                           \
     if (e__ != cudaSuccess) return ps::cuda_fail(e__, #call); \
   } while (0)
+
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on
+// the current device.  The limit is never lowered, so plans of different
+// sizes (and the allocation-free entry point) can share a kernel.
+struct SmemLimit {
+  int set[64] = {};
+  std::mutex m;
+};
+
+template <class K>
+inline int ensure_smem(K kernel, int smem, SmemLimit &lim) {
+  int dev = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(PULSCAN_ERR_UNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lock(lim.m);
+  if (lim.set[dev] >= smem) return PULSCAN_OK;
+  PS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  lim.set[dev] = smem;
+  return PULSCAN_OK;
+}
 
 // device error flags (bit set by kernels, read by pulscan_candidates)
 enum : uint32_t { kErrTimeout = 1u };
@@ -134,5 +155,9 @@ void record(pulscan_plan p, int idx, cudaStream_t s);  // timing event helper
 int search_smem_bytes(int W, int warps, int *buf_len_out);
 int search_tile_bins(int warps);
 int prepare_bank(pulscan_plan p);       // one-time kernel attributes (before any capture)
+int prepare_bank_raw(int W, int warps);
+int launch_segmax_raw(const float *d_power, const SeriesDev *d_series, const int64_t *d_tile_off, int64_t tiles,
+                      int warps, int W, int seg_len, unsigned long long *d_slots, uint32_t *d_counters,
+                      int64_t n_slots, float *d_max, uint64_t *d_argmax, cudaStream_t s);
 int prepare_normalise(pulscan_plan p);
 }  // namespace ps

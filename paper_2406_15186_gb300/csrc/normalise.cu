@@ -443,16 +443,16 @@ int normalise_smem(pulscan_plan p, int *bins_out) {
 
 }  // namespace
 
-int prepare_normalise(pulscan_plan p) {
-  PS_CUDA(cudaFuncSetAttribute(normalise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               normalise_smem(p, nullptr)));
-  return PULSCAN_OK;
-}
+SmemLimit g_lim_norm;
+
+int prepare_normalise(pulscan_plan p) { return ensure_smem(normalise_kernel, normalise_smem(p, nullptr), g_lim_norm); }
 
 int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, cudaStream_t s) {
   int bins = 0;
   const int smem = normalise_smem(p, &bins);
   if (p->total_seg > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many segments");
+  const int rc = ensure_smem(normalise_kernel, smem, g_lim_norm);
+  if (rc) return rc;
   float4 *st = d_stats ? reinterpret_cast<float4 *>(d_stats) : reinterpret_cast<float4 *>(p->d_stats);
   normalise_kernel<<<static_cast<unsigned>(p->total_seg), kNormThreads, smem, s>>>(
       reinterpret_cast<const float2 *>(d_spec), d_power, st, p->d_series, p->d_seg_off,

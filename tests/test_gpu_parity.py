@@ -172,3 +172,17 @@ def test_deferred_overflow_falls_back_to_inline_exact(pkg):
     ka = np.sort(a["cands"], order=["series", "bin", "width"])
     kb = np.sort(b["cands"], order=["series", "bin", "width"])
     assert np.array_equal(ka, kb)
+
+
+def test_plans_of_different_sizes_coexist(pkg):
+    """A smaller plan created later must not break the launches of a larger one."""
+    n = 1 << 15
+    x = _series(n, seed=21)
+    big = pkg.Plan(n=n, z_max=400, segment_len=2048, threshold_sigma=4.0)
+    first = parity.run_gpu(big, x, maxima=False)
+    small = pkg.Plan(n=n, z_max=5, segment_len=16, threshold_sigma=4.0)
+    parity.run_gpu(small, x, maxima=False)
+    again = parity.run_gpu(big, x, maxima=False)
+    a = np.sort(first["cands"], order=["series", "bin", "width"])
+    b = np.sort(again["cands"], order=["series", "bin", "width"])
+    assert np.array_equal(a, b)

@@ -156,6 +156,25 @@ PULSCAN_API int pulscan_candidates(pulscan_plan plan, pulscan_cand *h_out, int64
 PULSCAN_API int pulscan_segment_maxima(pulscan_plan plan, const float *d_power, float *d_max, uint64_t *d_argmax,
                            pulscan_stream stream);
 
+/* pulscan_segment_maxima without allocating: for callers that cannot call
+ * cudaMalloc (a real-time pipeline whose device memory all comes from its
+ * own pool, where an allocation would synchronise the device; a process under
+ * a hard memory cap).  The paper has no counterpart; it is this library's
+ * service to such callers.  One series of n samples (validated as in
+ * pulscan_plan_create, Bonferroni not involved): d_power float[n/2 + 1] (read
+ * only, 16-byte aligned), d_max float[n_seg * z_max] and d_argmax
+ * uint64[n_seg * z_max] with the layout of pulscan_segment_maxima.  Scratch
+ * is one library-owned static device array of 8 MiB (plus a small header)
+ * that each GPU loading the library keeps until exit; the call itself
+ * allocates nothing.  Limits: n_seg * z_max <= 2^20 and z_max <= 4096, else
+ * PULSCAN_ERR_UNSUPPORTED.  The first call on a device sets up (looks up the
+ * array's device address, raises the kernel's shared-memory limit): make it
+ * before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU race; serialise them. */
+PULSCAN_API int pulscan_segment_maxima_noalloc(const float *d_power, int64_t n, int32_t z_max,
+                                               int32_t segment_len, float *d_max, uint64_t *d_argmax,
+                                               pulscan_stream stream);
+
 /* Whole path (FFT, normalise, search) for a plan: the first call with a given
  * (d_x, d_spec, d_power, stream) captures the kernels into a CUDA graph when
  * use_graph != 0, later calls replay it. */

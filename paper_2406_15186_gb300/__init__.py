@@ -55,6 +55,8 @@ _SIGS = {
     "pulscan_boxcar_search": (ctypes.c_int, [_P, _P, _P]),
     "pulscan_candidates": (ctypes.c_int, [_P, _P, ctypes.c_int64, _I64P, _P]),
     "pulscan_segment_maxima": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "pulscan_segment_maxima_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                                      _P]),
     "pulscan_search": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
     "pulscan_search_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _I64P, ctypes.c_int, _P]),
     "pulscan_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),

@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-series batched measurement")
     return ap.parse_args()
 
 
@@ -189,6 +190,58 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
+def run_batched(torch, pkg, synth, dev, stream, steps):
+    """512 uneven DM-trial series: one graph replay vs per-series launches of the same kernels."""
+    cfg = synth.WORKLOADS["batch_512"]
+    w_max, seg_len, sigma = cfg["z_max"], cfg["segment_len"], cfg["sigma"]
+    lengths = synth.batch_lengths(cfg["n_series"], cfg["lengths"])
+    mask = synth.batch_tone_mask(cfg["n_series"])
+    plan = pkg.Plan(lengths=lengths, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    xo, so, po, _ = plan.offsets()
+    with torch.cuda.stream(stream):
+        d_x, d_spec, d_power = plan.buffers(dev)
+        synth.batch_device(d_x, xo, lengths, mask)
+    torch.cuda.synchronize()
+    bins = sum(n // 2 + 1 for n in lengths)
+
+    def timed(fn, reps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    def batched():
+        plan.search(d_x, d_spec, d_power, use_graph=True, stream=stream)
+
+    plans = {n: pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma) for n in sorted(set(lengths))}
+    xp, sp, pp = d_x.data_ptr(), d_spec.data_ptr(), d_power.data_ptr()
+
+    def per_series():
+        for i, n in enumerate(lengths):
+            p = plans[n]
+            p.rfft(xp + 4 * int(xo[i]), sp + 8 * int(so[i]), stream=stream)
+            p.power_normalise(sp + 8 * int(so[i]), pp + 4 * int(po[i]), stream=stream)
+            p.boxcar_search(pp + 4 * int(po[i]), stream=stream)
+
+    batched()
+    per_series()
+    t_b = timed(batched, steps)
+    n_cands = len(plan.candidates(stream=stream))
+    t_s = timed(per_series, max(1, steps // 2))
+    return {"workload": f"batch_512: 512 series, lengths U{{2^20..2^23}} (sum {sum(lengths)} samples, "
+                        f"{bins} bins), 26 with a tone, z_max={w_max}, segment_len={seg_len}, sigma={sigma:g}",
+            "dm_trials_per_s": len(lengths) / (t_b * 1e-3), "ms_per_batch": t_b,
+            "per_series_dm_trials_per_s": len(lengths) / (t_s * 1e-3), "ms_per_series_loop": t_s,
+            "ratio_batched_vs_per_series": t_s / t_b, "bin_widths_per_s": bins * w_max / (t_b * 1e-3) / 1e9,
+            "unit": "G bin-widths/s", "candidates": n_cands, "graph": True,
+            "per_series": "the same kernels launched per series on one stream (no graph), one plan per length",
+            "l2": "inputs (8.2 GB) far larger than L2"}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2406_15186_gb300 as pkg
@@ -310,6 +363,12 @@ def run_ours(args, rank, world, local):
                     "d2h_bytes_per_step": 16 + 24 * nc},
             "gpu_launches": 4 * args.steps,
             "clocks": clocks}
+    if not args.no_batched:
+        plan.close()
+        del d_x, d_spec, d_power
+        torch.cuda.empty_cache()
+        line["batched"] = run_batched(torch, pkg, synth, dev, stream, max(3, args.steps // 4))
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         spec, t_fft = oracle_fft(x)
         v, secs, desc = oracle_sample(spec, t_fft, cfg, 64)

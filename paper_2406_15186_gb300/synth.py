@@ -123,3 +123,45 @@ def binary_params(i, n=1 << 20):
     return dict(r0=float(rng.uniform(1.0e4, 4.0e5)), z=float(rng.uniform(0.0, 300.0)),
                 w=float(rng.uniform(-600.0, 600.0)), phi0=float(rng.uniform(0.0, 2.0 * np.pi)),
                 amp=float(np.exp(rng.uniform(np.log(0.01), np.log(0.1)))))
+
+
+# ---------------------------------------------------------------- on the GPU
+# Large workloads (the DM-trial batch, the big single series, the
+# differentiable batch) are drawn directly on the device: torch's seeded
+# Philox generator for the noise and FP64 chirps, cast to float32.  Tests that
+# compare with the oracle copy the sampled series back to the host, so both
+# sides see the same bytes.
+
+def device_noise(total, seed, device="cuda"):
+    """float32[total] standard normal noise from a seeded device generator."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return torch.randn(int(total), generator=g, device=device, dtype=torch.float32)
+
+
+def device_inject(x, tones):
+    """x += sum of tones in place (FP64 phase on the device, cast to float32)."""
+    import torch
+    n = x.shape[0]
+    u = torch.arange(n, device=x.device, dtype=torch.float64) / float(n)
+    acc = x.to(torch.float64)
+    for t in tones:
+        ph = t["r0"] * u + 0.5 * t["z"] * u * u + (t.get("w", 0.0) / 6.0) * u * u * u
+        acc += t["amp"] * torch.cos(2.0 * np.pi * ph + t.get("phi0", 0.0))
+    x.copy_(acc.to(torch.float32))
+    return x
+
+
+def batch_device(x_all, offsets, lengths, tone_mask, workload_id=3):
+    """Fill x_all (device, float32) with the DM-trial batch at the given offsets."""
+    tones_of = {}
+    for i, n in enumerate(lengths):
+        seg = x_all[int(offsets[i]): int(offsets[i]) + int(n)]
+        seg.copy_(device_noise(n, seed_of(workload_id, i), device=x_all.device))
+        if tone_mask[i]:
+            rng = np.random.default_rng(seed_of(workload_id, i) + 500_000)
+            tones = tone_params(rng, n, 1, 500.0)
+            device_inject(seg, tones)
+            tones_of[i] = tones
+    return tones_of

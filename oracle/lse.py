@@ -32,20 +32,31 @@ def _order_stat_weights(v):
     return wts
 
 
+def _lse(v, tau, axis=-1):
+    """tau * log sum exp(v / tau) along axis, shifted by the maximum."""
+    mv = np.max(v, axis=axis, keepdims=True)
+    return np.squeeze(mv, axis=axis) + tau * np.log(np.sum(np.exp((v - mv) / tau), axis=axis))
+
+
 def forward_power(p, w_max, seg_len, tau):
     """Y[s, w - 1] for normalised power p (FP64)."""
     m = p.shape[0]
     bounds = normalise.block_bounds(m, seg_len)
-    y = np.full((len(bounds), w_max), -np.inf)
+    n_seg = len(bounds)
+    y = np.full((n_seg, w_max), -np.inf)
     for w, s in boxcar.boxcar_widths(p, w_max):
         n_valid = m - w + 1
-        for si, (lo, hi) in enumerate(bounds):
+        # segments 0..f-1: full L-bin segments with every start bin valid
+        f = 0
+        while f < n_seg - 1 and bounds[f][1] <= n_valid:
+            f += 1
+        if f > 0:
+            y[:f, w - 1] = _lse(s[: f * seg_len].reshape(f, seg_len), tau)
+        for si in range(f, n_seg):
+            lo, hi = bounds[si]
             hi = min(hi, n_valid)
-            if lo >= hi:
-                continue
-            v = s[lo:hi] / tau
-            mv = v.max()
-            y[si, w - 1] = tau * (mv + np.log(np.sum(np.exp(v - mv))))
+            if lo < hi:
+                y[si, w - 1] = _lse(s[lo:hi], tau)
     return y
 
 

@@ -188,6 +188,46 @@ PULSCAN_API int pulscan_search(pulscan_plan plan, const float *d_x, float *d_spe
 PULSCAN_API int pulscan_search_host(pulscan_plan plan, const float *h_x, pulscan_cand *h_out, int64_t cap,
                                     int64_t *n_out, int use_graph, pulscan_stream stream);
 
+/* Differentiable extension (a smooth relaxation of Algorithm 4's per-chunk
+ * maximum; the paper has no gradient): for every segment s and width w,
+ *   Y[s, w] = tau * log sum_{k in s, k <= M - w} exp(S_w[k] / tau),
+ * which tends to the segment maximum as tau -> 0.  Runs the R2C FFT and the
+ * normalisation (Eq. 8) itself.  d_x float[x_floats] (read only); d_spec
+ * float[spec_floats], d_power float[power_floats], d_stats
+ * float[4 * total_segments] and d_sel float[8 * total_segments] (the
+ * selected order statistics the adjoint needs) are written and must be kept
+ * for pulscan_lse_backward; d_y float[total_segments * z_max] (row = segment,
+ * column = w - 1).  Terms more than tau ln(2^24 L) below the segment maximum
+ * are skipped: they are below FP32 resolution of the sum.  tau > 0.
+ * Segments must be at most 4224 bins (else PULSCAN_ERR_UNSUPPORTED). */
+PULSCAN_API int pulscan_lse_forward(pulscan_plan plan, const float *d_x, float *d_spec, float *d_power,
+                                    float *d_stats, float *d_sel, float *d_y, float tau, pulscan_stream stream);
+
+/* Adjoint of pulscan_lse_forward: given d_gy = dL/dY (same layout as d_y)
+ * and the forward's d_spec, d_power, d_stats, d_sel, d_y, writes
+ * d_gx = dL/dx float[x_floats].  The chain: softmax weights; the boxcar
+ * scatter dL/dP[j] = sum_w sum_{k=j-w+1..j} dL/dS_w[k]; P = (a^2 + b^2)/2;
+ * the median / MAD normalisation with its almost-everywhere derivatives at
+ * the selected order statistics; the real FFT (DC bin zeroed, so it carries
+ * no gradient), via cuFFT C2R.  Uses plan-owned scratch allocated on first
+ * use (dL/dP, the segment tails, the C2R input); overlapping backward calls
+ * on one plan race. */
+PULSCAN_API int pulscan_lse_backward(pulscan_plan plan, const float *d_spec, const float *d_power,
+                                     const float *d_stats, const float *d_sel, const float *d_y, const float *d_gy,
+                                     float *d_gx, float tau, pulscan_stream stream);
+
+/* Synthetic signal model of the differentiable workload (§2.1, Eq. 1):
+ * d_x = d_noise + amp[i] * d_template for every series i (all
+ * float[x_floats] in the plan's layout; d_amp float[n_series] in the
+ * caller's series order). */
+PULSCAN_API int pulscan_inject(pulscan_plan plan, const float *d_noise, const float *d_template,
+                               const float *d_amp, float *d_x, pulscan_stream stream);
+
+/* dL/dA[i] = sum_n dL/dx[n] template[n] over series i (FP64 accumulation),
+ * d_gamp float[n_series] in the caller's series order. */
+PULSCAN_API int pulscan_amplitude_grad(pulscan_plan plan, const float *d_gx, const float *d_template,
+                                       float *d_gamp, pulscan_stream stream);
+
 /* Per-kernel timing with CUDA events on the launch stream: enable (on != 0)
  * or disable recording; pulscan_plan_timings then writes the milliseconds of
  * the most recent launch of [rfft, normalise, boxcar search kernel,

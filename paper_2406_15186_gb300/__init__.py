@@ -59,6 +59,10 @@ _SIGS = {
                                                       _P]),
     "pulscan_search": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
     "pulscan_search_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _I64P, ctypes.c_int, _P]),
+    "pulscan_lse_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, _P]),
+    "pulscan_lse_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float, _P]),
+    "pulscan_inject": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "pulscan_amplitude_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pulscan_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "pulscan_plan_counters": (ctypes.c_int, [_P, _I64P, ctypes.c_int32]),
     "pulscan_plan_set_defer_capacity": (ctypes.c_int, [_P, ctypes.c_int64]),

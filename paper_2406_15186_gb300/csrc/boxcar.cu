@@ -28,6 +28,7 @@
 //
 // Dump mode (pulscan_segment_maxima) runs every block exactly and merges the
 // maximum of every (segment, width) with no threshold.
+#include "bank.cuh"
 #include "common.cuh"
 #include "ptx.cuh"
 
@@ -37,8 +38,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
-__device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 
 struct LaneCtx {
   int64_t k0;          // series-relative first bin of the lane
@@ -171,26 +170,6 @@ __device__ __forceinline__ void exact_steps(float (&s)[kR], const float *__restr
   }
 }
 
-// Fast mode: steps C0 .. C0+NC-1 of the 33-step ring, adds only.
-template <int C0, int NC>
-__device__ __forceinline__ void fast_steps(float (&s)[kR], float (&b)[kR], const float *__restrict__ pb) {
-#pragma unroll
-  for (int cc = 0; cc < NC; ++cc) {
-    const int c = C0 + cc;
-    b[(c + kR - 1) % kR] = pb[c + kR - 1];
-#pragma unroll
-    for (int i = 0; i < kR; ++i) s[i] += b[(i + c) % kR];
-  }
-}
-
-// Reload the ring after an exact run that ended at step CE of the block:
-// the ring must hold positions [33 bi + CE, 33 bi + CE + 31].
-template <int CE>
-__device__ __forceinline__ void reload_ring(float (&b)[kR], const float *__restrict__ pb) {
-#pragma unroll
-  for (int j = 0; j < kR - 1; ++j) b[(CE + j) % kR] = pb[CE + j];
-}
-
 // Bound test of one 11-width sub-block of an early block: three groups of
 // 11 bins, each bounded by s_{11 j} plus a pre-summed window of 22 bins.
 __device__ __forceinline__ bool early_bound(const float (&s)[kR], const float *__restrict__ q11, int qb, float tb) {
@@ -249,15 +228,6 @@ __device__ __forceinline__ bool defer_block(const float (&s)[kR], unsigned long 
 #pragma unroll
   for (int i = 0; i < kR; ++i) sp[i * 32] = s[i];
   return true;
-}
-
-// Plain steps w = wa..wb-1 (no ring, no compares): the partial last block.
-__device__ __forceinline__ void tail_steps(float (&s)[kR], const float *__restrict__ lane_buf, int wa, int wb) {
-  for (int w = wa; w < wb; ++w) {
-    const float *pw = lane_buf + (w - 1);
-#pragma unroll
-    for (int i = 0; i < kR; ++i) s[i] += pw[i];
-  }
 }
 
 template <bool kSearch>

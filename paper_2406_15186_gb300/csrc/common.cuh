@@ -136,6 +136,12 @@ struct pulscan_plan_s {
   pulscan_cand *d_cands = nullptr;
   // device buffers owned by the plan for pulscan_search_host
   float *own_x = nullptr, *own_spec = nullptr, *own_power = nullptr;
+  // logsumexp path (allocated on first use)
+  int64_t *d_x_off = nullptr, *d_x_len = nullptr;   // per layout series
+  float *d_dp = nullptr;           // dL/dP (power layout)
+  float *d_tail = nullptr;         // per segment, W-1 bins spilling into the next segment
+  float *d_gspec = nullptr;        // C2R input (spectrum layout)
+  std::vector<ps::FftClass> ifft;  // C2R plans per length class
   // timing
   bool timing = false;
   cudaEvent_t ev[12] = {};
@@ -147,6 +153,10 @@ namespace ps {
 // launchers (defined in the kernel translation units)
 int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats,
                      cudaStream_t s);
+// same, also recording per segment the selected order statistics
+// [med_lo, med_hi, dev_lo, dev_hi] of Re then Im (8 floats) into d_sel
+int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, float *d_sel,
+                         cudaStream_t s);
 int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s);
 int launch_finalize(pulscan_plan p, cudaStream_t s);
 int launch_segmax(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax,

@@ -1,0 +1,626 @@
+// Differentiable extension: a logsumexp relaxation of the per-(segment,
+// width) maximum of Algorithm 4 and its hand-written adjoint.
+//
+//   Y[s, w] = tau * log sum_{k in seg s, k <= M - w} exp(S_w[k] / tau)
+//
+// tends to the maximum as tau -> 0.  The adjoint goes back through the
+// softmax weights, the boxcar bank (whose adjoint is again a boxcar: every
+// weight is added to all bins of its window), P = (a^2 + b^2)/2, the median /
+// MAD normalisation of Eq. 8 (almost-everywhere derivatives at the selected
+// order statistics) and the real FFT, to the time series.
+//
+// Kernels (one CTA per segment; lanes own 33 bins with register running sums
+// as in the search):
+// * lse_forward_kernel: pass 1 finds M[s, w] = max S_w (per step a lane max
+//   into shared memory, merged per width once per 33-width block); pass 2
+//   re-runs the sums and exponentiates only windows within
+//   tau * ln(2^24 L) of M -- every other term is below FP32 resolution of the
+//   sum, which is >= 1 -- so exp work is rare;
+// * lse_backward_kernel: re-runs the sums; each window within
+//   tau * ln(2^24 L) of Y gets weight g = G exp((S - Y) / tau), entered as a
+//   difference pair D[k] += g, D[k + w] -= g in shared memory; one block
+//   prefix sum of D gives dL/dP over the segment and a (W - 1)-bin tail that
+//   spills into the next segment (no global atomics);
+// * normalise_backward_kernel: dL/dP -> dL/d(Re, Im) through Eq. 8, written
+//   as the input of a cuFFT C2R transform with the Hermitian weights (DC 0,
+//   interior halved, Nyquist real), whose output is dL/dx;
+// * inject_kernel / amp_grad_kernel: x = noise + A template and
+//   dL/dA = sum_n dL/dx[n] template[n], per series.
+#include <algorithm>
+#include <cmath>
+
+#include "bank.cuh"
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace ps {
+
+namespace {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kLseMaxWarps = 4;
+
+// Ring steps C0..C0+NC-1 with a per-step callback cb(c) after the adds.
+template <int C0, int NC, class F>
+__device__ __forceinline__ void ring_steps(float (&s)[kR], float (&b)[kR], const float *__restrict__ pb, F &&cb) {
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc) {
+    const int c = C0 + cc;
+    b[(c + kR - 1) % kR] = pb[c + kR - 1];
+#pragma unroll
+    for (int i = 0; i < kR; ++i) s[i] += b[(i + c) % kR];
+    cb(c);
+  }
+}
+
+// Runs widths 1..W over the lane's 33 sums, calling cb(w, c, s) after each
+// width's adds: full 33-width blocks use the ring, the last partial block
+// reads the window straight from shared memory.  block_end(bi, nsteps) is
+// called after every block.
+template <class F, class G>
+__device__ __forceinline__ void walk_widths(float (&s)[kR], const float *__restrict__ lane_buf, int W, F &&cb,
+                                            G &&block_end) {
+  float b[kR];
+#pragma unroll
+  for (int i = 0; i < kR; ++i) s[i] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < kR - 1; ++j) b[j] = lane_buf[j];
+  b[kR - 1] = 0.0f;
+  const int nb = (W + kR - 1) / kR;
+  for (int bi = 0; bi < nb; ++bi) {
+    const float *pb = lane_buf + bi * kR;
+    const int wf = bi * kR + 1;
+    const int nsteps = min(kR, W - bi * kR);
+    if (nsteps == kR) {
+      ring_steps<0, kR>(s, b, pb, [&](int c) { cb(wf + c, c); });
+    } else {
+      for (int c = 0; c < nsteps; ++c) {
+        const float *pw = lane_buf + (wf + c - 1);
+#pragma unroll
+        for (int i = 0; i < kR; ++i) s[i] += pw[i];
+        cb(wf + c, c);
+      }
+    }
+    block_end(bi, nsteps);
+  }
+}
+
+struct SegTile {
+  int64_t m, b0, seg_g;
+  int nb;          // bins of this segment
+  const float *src;
+  float *buf;
+};
+
+// Stage P[b0 .. b0 + buf_len) (zeros beyond M) into shared memory.
+__device__ __forceinline__ bool stage_segment(const SegTile &t, int buf_len, uint64_t *bar, uint32_t *flag,
+                                              uint32_t *counters) {
+  const int64_t avail64 = t.m - t.b0;
+  const int avail = static_cast<int>(min64(avail64, static_cast<int64_t>(buf_len)));
+  const int n_tma = ((reinterpret_cast<uintptr_t>(t.src) & 15u) == 0u && avail > 0) ? (avail & ~3) : 0;
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && n_tma > 0) {
+    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(n_tma) * 4u);
+    tma_load_1d(t.buf, t.src, static_cast<uint32_t>(n_tma) * 4u, bar);
+  }
+  for (int i = n_tma + threadIdx.x; i < buf_len; i += blockDim.x) t.buf[i] = (i < avail) ? t.src[i] : 0.0f;
+  if (threadIdx.x == 0) *flag = (n_tma == 0 || mbar_wait_bounded(bar, 0, 2000000000ull)) ? 1u : 0u;
+  __syncthreads();
+  if (*flag == 0u) {
+    if (threadIdx.x == 0) atomicOr(counters + 2, kErrTimeout);
+    return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ SegTile seg_tile(const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
+                                            int n_series, int seg_len, const float *power, float *buf) {
+  const int64_t g = blockIdx.x;
+  int lo = 0, hi = n_series - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg_off[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const SeriesDev S = series[lo];
+  SegTile t;
+  const int64_t sl = g - S.seg_off;
+  t.m = S.m;
+  t.b0 = sl * seg_len;
+  t.nb = static_cast<int>(((sl == S.n_seg - 1) ? S.m : t.b0 + seg_len) - t.b0);
+  t.seg_g = g;
+  t.src = power + S.p_off + t.b0;
+  t.buf = buf;
+  return t;
+}
+
+// Valid bins of a lane at width w: inside the segment, window inside the spectrum.
+__device__ __forceinline__ int lane_lim(const SegTile &t, int x0, int w) {
+  const int64_t k0 = t.b0 + x0;
+  const int64_t lim = min64(static_cast<int64_t>(t.nb - x0), t.m - w + 1 - k0);
+  return static_cast<int>(max64(min64(lim, kR), 0));
+}
+
+__device__ __forceinline__ float lane_max(const float (&s)[kR], int lim) {
+  float m = -INFINITY;
+  if (lim >= kR) {
+    float t16[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t16[i] = fmaxf(s[2 * i], s[2 * i + 1]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t16[i] = fmaxf(t16[2 * i], t16[2 * i + 1]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t16[i] = fmaxf(t16[2 * i], t16[2 * i + 1]);
+    m = fmaxf(fmaxf(fmaxf(t16[0], t16[1]), fmaxf(t16[2], t16[3])), s[kR - 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kR; ++i) m = fmaxf(m, (i < lim) ? s[i] : -INFINITY);
+  }
+  return m;
+}
+
+__global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
+    const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
+    int n_series, int W, int seg_len, float tau, float cut, float *__restrict__ y, uint32_t *__restrict__ counters,
+    int buf_len) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+  uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
+  float *buf = reinterpret_cast<float *>(smem_raw + 128);
+  float *mrow = buf + buf_len;                   // W: M[s, w]
+  float *lsum = mrow + W;                        // W: sum of exp
+  float *kmax = lsum + W;                        // warps x 33 x 32 lane maxima
+  const int warps = blockDim.x >> 5;
+  const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
+  if (!stage_segment(t, buf_len, bar, flag, counters)) return;
+  for (int j = threadIdx.x; j < W; j += blockDim.x) lsum[j] = 0.0f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x0 = warp * (32 * kR) + lane * kR;
+  const float *lane_buf = buf + x0;
+  float s[kR];
+  // pass 1: M[s, w]
+  walk_widths(
+      s, lane_buf, W,
+      [&](int w, int c) { kmax[(warp * kR + c) * 32 + lane] = lane_max(s, lane_lim(t, x0, w)); },
+      [&](int bi, int nsteps) {
+        __syncthreads();
+        for (int c = threadIdx.x; c < nsteps; c += blockDim.x) {
+          float m = -INFINITY;
+          for (int v = 0; v < warps; ++v)
+            for (int l = 0; l < 32; ++l) m = fmaxf(m, kmax[(v * kR + c) * 32 + ((l + c) & 31)]);
+          mrow[bi * kR + c] = m;
+        }
+        __syncthreads();
+      });
+  // pass 2: sum of exp((S - M) / tau) over windows within `cut` of M
+  const float inv_tau = 1.0f / tau;
+  walk_widths(
+      s, lane_buf, W,
+      [&](int w, int c) {
+        const float mw = mrow[w - 1];
+        const float thr = mw - cut;
+        const int lim = lane_lim(t, x0, w);
+        bool near = false;
+#pragma unroll
+        for (int i = 0; i < kR; ++i) near |= (i < lim) && (s[i] > thr);
+        if (!__any_sync(kFullMask, near)) return;
+        float acc = 0.0f;
+        if (near) {
+#pragma unroll
+          for (int i = 0; i < kR; ++i)
+            if (i < lim && s[i] > thr) acc += expf((s[i] - mw) * inv_tau);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+        if (lane == 0 && acc > 0.0f) atomicAdd(&lsum[w - 1], acc);
+        (void)c;
+      },
+      [&](int, int) {});
+  __syncthreads();
+  for (int j = threadIdx.x; j < W; j += blockDim.x)
+    y[t.seg_g * static_cast<int64_t>(W) + j] = mrow[j] + tau * logf(lsum[j]);
+}
+
+__global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
+    const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
+    int n_series, int W, int seg_len, float tau, float cut, const float *__restrict__ y,
+    const float *__restrict__ gy, float *__restrict__ dp, float *__restrict__ tail, uint32_t *__restrict__ counters,
+    int buf_len, int d_len) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+  uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
+  float *buf = reinterpret_cast<float *>(smem_raw + 128);
+  float *yrow = buf + buf_len;
+  float *grow = yrow + W;
+  float *dd = grow + W;                          // d_len difference entries
+  float *wsum = dd + d_len;                      // per-warp scan totals
+  const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
+  if (!stage_segment(t, buf_len, bar, flag, counters)) return;
+  for (int j = threadIdx.x; j < W; j += blockDim.x) {
+    yrow[j] = y[t.seg_g * static_cast<int64_t>(W) + j];
+    grow[j] = gy[t.seg_g * static_cast<int64_t>(W) + j];
+  }
+  for (int j = threadIdx.x; j < d_len; j += blockDim.x) dd[j] = 0.0f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x0 = warp * (32 * kR) + lane * kR;
+  const float *lane_buf = buf + x0;
+  const float inv_tau = 1.0f / tau;
+  float s[kR];
+  walk_widths(
+      s, lane_buf, W,
+      [&](int w, int c) {
+        const float yw = yrow[w - 1];
+        const float gw = grow[w - 1];
+        const float thr = yw - cut;
+        const int lim = lane_lim(t, x0, w);
+        bool near = false;
+#pragma unroll
+        for (int i = 0; i < kR; ++i) near |= (i < lim) && (s[i] > thr);
+        if (!__any_sync(kFullMask, near) || gw == 0.0f) return;
+        if (near) {
+#pragma unroll
+          for (int i = 0; i < kR; ++i) {
+            if (i < lim && s[i] > thr) {
+              const float g = gw * expf((s[i] - yw) * inv_tau);
+              atomicAdd(&dd[x0 + i], g);
+              atomicAdd(&dd[x0 + i + w], -g);
+            }
+          }
+        }
+        (void)c;
+      },
+      [&](int, int) {});
+  __syncthreads();
+  // inclusive prefix sum of dd: thread t owns a contiguous chunk
+  const int nt = blockDim.x;
+  const int chunk = (d_len + nt - 1) / nt;
+  const int a0 = threadIdx.x * chunk, a1 = min(d_len, a0 + chunk);
+  float run = 0.0f;
+  for (int j = a0; j < a1; ++j) run += dd[j];
+  float incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float u = __shfl_up_sync(kFullMask, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  float base = incl - run;
+  for (int v = 0; v < warp; ++v) base += wsum[v];
+  float acc = base;
+  for (int j = a0; j < a1; ++j) {
+    acc += dd[j];
+    dd[j] = acc;
+  }
+  __syncthreads();
+  // bins of this segment, then the spill into the next one
+  float *out = dp + (t.src - power);   // same offset in the dP buffer
+  for (int j = threadIdx.x; j < t.nb; j += nt) out[j] = dd[j];
+  float *tl = tail + t.seg_g * static_cast<int64_t>(W);
+  for (int j = threadIdx.x; j < W - 1; j += nt) tl[j] = (t.nb + j < d_len) ? dd[t.nb + j] : 0.0f;
+}
+
+// dL/dP -> C2R input, per segment (256 threads).
+constexpr double kKappaB = 1.482602218505602;
+
+__global__ void __launch_bounds__(256) normalise_backward_kernel(
+    const float2 *__restrict__ spec, const float *__restrict__ dp, const float *__restrict__ tail,
+    const float4 *__restrict__ stats, const float *__restrict__ sel, const SeriesDev *__restrict__ series,
+    const int64_t *__restrict__ seg_off, int n_series, int seg_len, int W, float2 *__restrict__ out) {
+  __shared__ float red[8][4];
+  __shared__ int idx_all[8][8];
+  __shared__ int idx_sh[8];
+  __shared__ float sums[4];
+  const int64_t g = blockIdx.x;
+  int lo = 0, hi = n_series - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg_off[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const SeriesDev S = series[lo];
+  const int64_t sl = g - S.seg_off;
+  const int64_t b0 = sl * seg_len;
+  const int n = static_cast<int>(((sl == S.n_seg - 1) ? S.m : b0 + seg_len) - b0);
+  const float2 *x = spec + S.spec_off + b0;
+  const float *dpp = dp + S.p_off + b0;
+  const float *prev_tail = (sl > 0) ? tail + (g - 1) * static_cast<int64_t>(W) : nullptr;
+  const float4 st = stats[g];
+  const float med[2] = {st.x, st.z}, mad[2] = {st.y, st.w};
+  const float *sv = sel + 8 * g;
+  const bool even = (n % 2) == 0;
+  const float inv[2] = {static_cast<float>(1.0 / (kKappaB * static_cast<double>(mad[0]))),
+                        static_cast<float>(1.0 / (kKappaB * static_cast<double>(mad[1])))};
+  const bool ok = mad[0] > 0.0f && mad[1] > 0.0f;
+  auto val = [&](int j) -> float2 { return (b0 + j == 0) ? make_float2(0.0f, 0.0f) : x[j]; };
+  auto dpv = [&](int j) -> float { return dpp[j] + ((prev_tail && j < W - 1) ? prev_tail[j] : 0.0f); };
+  // block sums: S1_c = sum g_a, S2_c = sum g_a (x - med); and the selected indices
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  int idx[8] = {n, n, n, n, n, n, n, n};
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int j = tid; j < n; j += 256) {
+    const float2 v = val(j);
+    const float d = dpv(j);
+    const float a = (v.x - med[0]) * inv[0], b = (v.y - med[1]) * inv[1];
+    acc[0] += d * a;
+    acc[1] += d * a * (v.x - med[0]);
+    acc[2] += d * b;
+    acc[3] += d * b * (v.y - med[1]);
+    const float xv[2] = {v.x, v.y};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float dev = fabsf(xv[c] - med[c]);
+      if (xv[c] == sv[4 * c + 0] && j < idx[4 * c + 0]) idx[4 * c + 0] = j;
+      if (xv[c] == sv[4 * c + 1] && j < idx[4 * c + 1]) idx[4 * c + 1] = j;
+      if (dev == sv[4 * c + 2] && j < idx[4 * c + 2]) idx[4 * c + 2] = j;
+      if (dev == sv[4 * c + 3] && j < idx[4 * c + 3]) idx[4 * c + 3] = j;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(kFullMask, acc[q], o);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) idx[q] = min(idx[q], __shfl_xor_sync(kFullMask, idx[q], o));
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[wid][q] = acc[q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) idx_all[wid][q] = idx[q];
+  }
+  __syncthreads();
+  if (tid < 8) {
+    int m = n;
+    for (int v = 0; v < 8; ++v) m = min(m, idx_all[v][tid]);
+    idx_sh[tid] = m;
+  }
+  if (tid < 4) {
+    float z = 0.0f;
+    for (int v = 0; v < 8; ++v) z += red[v][tid];
+    sums[tid] = z;
+  }
+  __syncthreads();
+  // the second middle statistic may tie with the first: then take the next occurrence
+  if (even) {
+    if (tid < 4) {
+      const int c = tid >> 1, q = (tid & 1) ? 2 : 0;   // (median | deviation) pair of component c
+      const int first = idx_sh[4 * c + q], second = idx_sh[4 * c + q + 1];
+      if (second == first) {
+        int nxt = n;
+        for (int j = first + 1; j < n; ++j) {
+          const float2 v = val(j);
+          const float xv = c ? v.y : v.x;
+          const float test = q ? fabsf(xv - med[c]) : xv;
+          if (test == sv[4 * c + q + 1]) {
+            nxt = j;
+            break;
+          }
+        }
+        idx_sh[4 * c + q + 1] = nxt;
+      }
+    }
+    __syncthreads();
+  }
+  const float wsel = even ? 0.5f : 1.0f;
+  const int64_t half = S.m - 1;   // Nyquist bin index = N / 2
+  for (int j = tid; j < n; j += 256) {
+    const float2 v = val(j);
+    const float d = dpv(j);
+    const float xv[2] = {v.x, v.y};
+    float gx[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float scale_inv = inv[c];
+      const float ac = (xv[c] - med[c]) * scale_inv;
+      const float ga = d * ac;
+      const int m_lo = idx_sh[4 * c + 0], m_hi = even ? idx_sh[4 * c + 1] : -1;
+      const int d_lo = idx_sh[4 * c + 2], d_hi = even ? idx_sh[4 * c + 3] : -1;
+      const float dmed = wsel * ((j == m_lo) ? 1.0f : 0.0f) + wsel * ((j == m_hi) ? 1.0f : 0.0f);
+      // sign(x_m - med) at the selected deviations (read from the staged spectrum)
+      const float x_dlo = (d_lo < n) ? (c ? val(d_lo).y : val(d_lo).x) : med[c];
+      const float x_dhi = (even && d_hi < n) ? (c ? val(d_hi).y : val(d_hi).x) : med[c];
+      const float sg_lo = (x_dlo > med[c]) ? 1.0f : ((x_dlo < med[c]) ? -1.0f : 0.0f);
+      const float sg_hi = even ? ((x_dhi > med[c]) ? 1.0f : ((x_dhi < med[c]) ? -1.0f : 0.0f)) : 0.0f;
+      const float dmad = wsel * sg_lo * ((j == d_lo) ? 1.0f : 0.0f) + wsel * sg_hi * ((j == d_hi) ? 1.0f : 0.0f) -
+                         wsel * (sg_lo + sg_hi) * dmed;
+      const float s1 = sums[2 * c], s2 = sums[2 * c + 1];
+      gx[c] = ok ? (ga * scale_inv - s1 * scale_inv * dmed - s2 * scale_inv / mad[c] * dmad) : 0.0f;
+    }
+    const int64_t k = b0 + j;
+    float2 o;
+    if (k == 0) {
+      o = make_float2(0.0f, 0.0f);           // DC := 0 carries no gradient
+    } else if (k == half) {
+      o = make_float2(gx[0], 0.0f);          // Nyquist: real
+    } else {
+      o = make_float2(0.5f * gx[0], 0.5f * gx[1]);
+    }
+    out[S.spec_off + k] = o;
+  }
+}
+
+__global__ void inject_kernel(const float *__restrict__ noise, const float *__restrict__ tmpl,
+                              const float *__restrict__ amp, const SeriesDev *__restrict__ series,
+                              const int64_t *__restrict__ x_off, const int64_t *__restrict__ x_len, int n_series,
+                              float *__restrict__ x) {
+  const int si = blockIdx.y;
+  if (si >= n_series) return;
+  const int64_t off = x_off[si], len = x_len[si];
+  const float a = amp[series[si].user_index];
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < len;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    x[off + i] = fmaf(a, tmpl[off + i], noise[off + i]);
+}
+
+__global__ void amp_grad_kernel(const float *__restrict__ gx, const float *__restrict__ tmpl,
+                                const SeriesDev *__restrict__ series, const int64_t *__restrict__ x_off,
+                                const int64_t *__restrict__ x_len, int n_series, float *__restrict__ gamp) {
+  const int si = blockIdx.x;
+  if (si >= n_series) return;
+  const int64_t off = x_off[si], len = x_len[si];
+  double acc = 0.0;
+  float part = 0.0f;
+  int cnt = 0;
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+    part = fmaf(gx[off + i], tmpl[off + i], part);
+    if (++cnt == 64) {   // fold into FP64 every 64 terms
+      acc += part;
+      part = 0.0f;
+      cnt = 0;
+    }
+  }
+  acc += part;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double z = 0.0;
+    for (int v = 0; v < static_cast<int>(blockDim.x >> 5); ++v) z += red[v];
+    gamp[series[si].user_index] = static_cast<float>(z);
+  }
+}
+
+int lse_warps(pulscan_plan p) {
+  int64_t max_n = 0;
+  for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
+  return static_cast<int>((max_n + 32 * kR - 1) / (32 * kR));
+}
+
+int lse_buf_len(pulscan_plan p, int warps) {
+  const int nb = (p->z_max + kR - 1) / kR;
+  return ((32 * kR * warps + nb * kR + 3 * kR) + 3) & ~3;
+}
+
+SmemLimit g_lim_fwd, g_lim_bwd;
+
+int lse_prepare(pulscan_plan p) {
+  if (lse_warps(p) > kLseMaxWarps)
+    return fail(PULSCAN_ERR_UNSUPPORTED, "logsumexp path needs segments of at most 4224 bins");
+  return PULSCAN_OK;
+}
+
+int lse_backward_buffers(pulscan_plan p) {
+  if (!p->d_dp) PS_CUDA(cudaMalloc(reinterpret_cast<void **>(&p->d_dp), sizeof(float) * p->p_floats));
+  if (!p->d_tail)
+    PS_CUDA(cudaMalloc(reinterpret_cast<void **>(&p->d_tail), sizeof(float) * p->total_seg * p->z_max));
+  if (!p->d_gspec) PS_CUDA(cudaMalloc(reinterpret_cast<void **>(&p->d_gspec), 2 * sizeof(float) * p->spec_bins));
+  if (p->ifft.empty()) {
+    for (const auto &f : p->fft) {
+      FftClass g = f;
+      g.handle = 0;
+      long long nn = f.n, inembed = f.spec_stride, onembed = f.n;
+      size_t work = 0;
+      cufftResult r = cufftCreate(&g.handle);
+      if (r == CUFFT_SUCCESS)
+        r = cufftMakePlanMany64(g.handle, 1, &nn, &inembed, 1, f.spec_stride, &onembed, 1, f.n, CUFFT_C2R, f.count,
+                                &work);
+      if (r != CUFFT_SUCCESS) {
+        if (g.handle) cufftDestroy(g.handle);
+        return fail(r == CUFFT_ALLOC_FAILED ? PULSCAN_ERR_NOMEM : PULSCAN_ERR_CUDA, "cuFFT C2R plan failed");
+      }
+      p->ifft.push_back(g);
+    }
+  }
+  return PULSCAN_OK;
+}
+
+float lse_cut(pulscan_plan p, float tau) {
+  // terms below 2^-24 / L of the largest one are beyond FP32 resolution of the sum
+  return tau * static_cast<float>(std::log(16777216.0 * static_cast<double>(p->seg_len + p->seg_len)));
+}
+
+}  // namespace
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" {
+
+int pulscan_lse_forward(pulscan_plan p, const float *d_x, float *d_spec, float *d_power, float *d_stats,
+                        float *d_sel, float *d_y, float tau, pulscan_stream stream) {
+  if (!p || !d_x || !d_spec || !d_power || !d_stats || !d_sel || !d_y)
+    return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  if (!(tau > 0.0f) || !std::isfinite(tau)) return fail(PULSCAN_ERR_INVALID_ARG, "tau must be finite and > 0");
+  int rc = lse_prepare(p);
+  if (rc) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  rc = pulscan_rfft(p, d_x, d_spec, stream);
+  if (rc) return rc;
+  rc = launch_normalise_sel(p, d_spec, d_power, d_stats, d_sel, s);
+  if (rc) return rc;
+  const int warps = lse_warps(p);
+  const int buf_len = lse_buf_len(p, warps);
+  const int smem = 128 + 4 * (buf_len + 2 * p->z_max + warps * kR * 32);
+  rc = ensure_smem(lse_forward_kernel, smem, g_lim_fwd);
+  if (rc) return rc;
+  lse_forward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
+      d_power, p->d_series, p->d_seg_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len, tau,
+      lse_cut(p, tau), d_y, p->d_counters, buf_len);
+  PS_CUDA(cudaGetLastError());
+  return PULSCAN_OK;
+}
+
+int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_power, const float *d_stats,
+                         const float *d_sel, const float *d_y, const float *d_gy, float *d_gx, float tau,
+                         pulscan_stream stream) {
+  if (!p || !d_spec || !d_power || !d_stats || !d_sel || !d_y || !d_gy || !d_gx)
+    return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  if (!(tau > 0.0f) || !std::isfinite(tau)) return fail(PULSCAN_ERR_INVALID_ARG, "tau must be finite and > 0");
+  if (lse_warps(p) > kLseMaxWarps)
+    return fail(PULSCAN_ERR_UNSUPPORTED, "logsumexp path needs segments of at most 4224 bins");
+  int rc = lse_backward_buffers(p);
+  if (rc) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int warps = lse_warps(p);
+  const int buf_len = lse_buf_len(p, warps);
+  int64_t max_n = 0;
+  for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
+  const int d_len = static_cast<int>(max_n + p->z_max + 1);
+  const int smem = 128 + 4 * (buf_len + 2 * p->z_max + d_len + 32);
+  rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
+  if (rc) return rc;
+  lse_backward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
+      d_power, p->d_series, p->d_seg_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len, tau,
+      lse_cut(p, tau), d_y, d_gy, p->d_dp, p->d_tail, p->d_counters, buf_len, d_len);
+  PS_CUDA(cudaGetLastError());
+  normalise_backward_kernel<<<static_cast<unsigned>(p->total_seg), 256, 0, s>>>(
+      reinterpret_cast<const float2 *>(d_spec), p->d_dp, p->d_tail, reinterpret_cast<const float4 *>(d_stats),
+      d_sel, p->d_series, p->d_seg_off, static_cast<int>(p->series.size()), p->seg_len, p->z_max,
+      reinterpret_cast<float2 *>(p->d_gspec));
+  PS_CUDA(cudaGetLastError());
+  for (auto &f : p->ifft) {
+    cufftResult r = cufftSetStream(f.handle, s);
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecC2R(f.handle, reinterpret_cast<cufftComplex *>(p->d_gspec) + f.spec_off, d_gx + f.x_off);
+    if (r != CUFFT_SUCCESS) return fail(PULSCAN_ERR_CUDA, "cufftExecC2R failed");
+  }
+  return PULSCAN_OK;
+}
+
+int pulscan_inject(pulscan_plan p, const float *d_noise, const float *d_template, const float *d_amp, float *d_x,
+                   pulscan_stream stream) {
+  if (!p || !d_noise || !d_template || !d_amp || !d_x) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int ns = static_cast<int>(p->series.size());
+  if (ns > 65535) return fail(PULSCAN_ERR_UNSUPPORTED, "too many series for one launch");
+  inject_kernel<<<dim3(64, ns), 256, 0, s>>>(d_noise, d_template, d_amp, p->d_series, p->d_x_off, p->d_x_len, ns,
+                                             d_x);
+  PS_CUDA(cudaGetLastError());
+  return PULSCAN_OK;
+}
+
+int pulscan_amplitude_grad(pulscan_plan p, const float *d_gx, const float *d_template, float *d_gamp,
+                           pulscan_stream stream) {
+  if (!p || !d_gx || !d_template || !d_gamp) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int ns = static_cast<int>(p->series.size());
+  amp_grad_kernel<<<ns, 512, 0, s>>>(d_gx, d_template, p->d_series, p->d_x_off, p->d_x_len, ns, d_gamp);
+  PS_CUDA(cudaGetLastError());
+  return PULSCAN_OK;
+}
+
+}  // extern "C"

@@ -20,7 +20,9 @@
 // select on |x - median|, whose range [0, max deviation] follows from the
 // median pass.  Then a = (x - med) / (kappa MAD), kappa = 1/Phi^{-1}(3/4),
 // and P = (a^2 + b^2)/2, written coalesced.  The DC bin of a series is taken
-// as 0 + 0i.  A segment whose MAD is 0 gets P = 0.
+// as 0 + 0i.  A segment whose MAD is 0 gets P = 0.  On request the kernel
+// also records the selected order statistics (the two middle values of each
+// component and of its deviations), which the adjoint needs.
 //
 // The paper's GPU version estimates the median by median-of-medians (§2.5);
 // this kernel keeps the exact median of the CPU version, which the FP32 and
@@ -325,7 +327,7 @@ __device__ __forceinline__ float mean_of(float a, float b) {
 __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
     const float2 *__restrict__ spec, float *__restrict__ power, float4 *__restrict__ stats,
     const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off, int n_series, int seg_len,
-    uint32_t *__restrict__ counters, int smem_bins) {
+    uint32_t *__restrict__ counters, int smem_bins, float *__restrict__ sel) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   SelShared &sh = *reinterpret_cast<SelShared *>(smem_raw + 128);
@@ -402,6 +404,13 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
     select_levels(sh, raw, n, rank, even, lo_v, hi_v);
   const float med_re = even ? mean_of(lo_v[0], hi_v[0]) : lo_v[0];
   const float med_im = even ? mean_of(lo_v[1], hi_v[1]) : lo_v[1];
+  if (sel != nullptr && threadIdx.x == 0) {
+    // the selected order statistics, for the adjoint of the median
+    sel[8 * g + 0] = lo_v[0];
+    sel[8 * g + 1] = hi_v[0];
+    sel[8 * g + 4] = lo_v[1];
+    sel[8 * g + 5] = hi_v[1];
+  }
 
   // MADs: the same selection on |x - med|, over [0, max deviation]
   auto dev = [&](int e, float &v0, float &v1) {
@@ -415,6 +424,13 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
     select_levels(sh, dev, n, rank, even, lo_v, hi_v);
   const float mad_re = even ? mean_of(lo_v[0], hi_v[0]) : lo_v[0];
   const float mad_im = even ? mean_of(lo_v[1], hi_v[1]) : lo_v[1];
+  if (sel != nullptr && threadIdx.x == 0) {
+    // the selected deviations, for the adjoint of the MAD
+    sel[8 * g + 2] = lo_v[0];
+    sel[8 * g + 3] = hi_v[0];
+    sel[8 * g + 6] = lo_v[1];
+    sel[8 * g + 7] = hi_v[1];
+  }
 
   const bool degenerate = !(mad_re > 0.0f) || !(mad_im > 0.0f);
   const float inv_re = degenerate ? 0.0f : static_cast<float>(1.0 / (kKappa * static_cast<double>(mad_re)));
@@ -448,6 +464,11 @@ SmemLimit g_lim_norm;
 int prepare_normalise(pulscan_plan p) { return ensure_smem(normalise_kernel, normalise_smem(p, nullptr), g_lim_norm); }
 
 int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, cudaStream_t s) {
+  return launch_normalise_sel(p, d_spec, d_power, d_stats, nullptr, s);
+}
+
+int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, float *d_sel,
+                         cudaStream_t s) {
   int bins = 0;
   const int smem = normalise_smem(p, &bins);
   if (p->total_seg > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many segments");
@@ -456,7 +477,7 @@ int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float 
   float4 *st = d_stats ? reinterpret_cast<float4 *>(d_stats) : reinterpret_cast<float4 *>(p->d_stats);
   normalise_kernel<<<static_cast<unsigned>(p->total_seg), kNormThreads, smem, s>>>(
       reinterpret_cast<const float2 *>(d_spec), d_power, st, p->d_series, p->d_seg_off,
-      static_cast<int>(p->series.size()), p->seg_len, p->d_counters, bins);
+      static_cast<int>(p->series.size()), p->seg_len, p->d_counters, bins, d_sel);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }

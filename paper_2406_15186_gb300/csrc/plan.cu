@@ -108,9 +108,12 @@ static void free_plan(pulscan_plan p) {
   if (!p) return;
   for (auto &f : p->fft)
     if (f.handle) cufftDestroy(f.handle);
+  for (auto &f : p->ifft)
+    if (f.handle) cufftDestroy(f.handle);
   void *ptrs[] = {p->d_series, p->d_tile_off, p->d_seg_off, p->d_thresh, p->d_thresh_bound, p->d_ln_trials,
                   p->d_stats,  p->d_slots,    p->d_dirty,   p->d_counters, p->d_cands,     p->own_x,
-                  p->own_spec, p->own_power, p->d_items, p->d_snaps,    p->d_gtab};
+                  p->own_spec, p->own_power, p->d_items, p->d_snaps,    p->d_gtab,     p->d_x_off,
+                  p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (auto &e : p->ev)
@@ -230,7 +233,7 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
       ok(dalloc(&p->d_slots, total_slots)) && ok(dalloc(&p->d_dirty, dirty_words)) &&
       ok(dalloc(&p->d_counters, 4)) && ok(dalloc(&p->d_cands, p->max_cands)) &&
       ok(dalloc(&p->d_items, p->item_cap)) && ok(dalloc(&p->d_snaps, p->item_cap * kR * 32)) &&
-      ok(dalloc(&p->d_gtab, z_max))) {
+      ok(dalloc(&p->d_gtab, z_max)) && ok(dalloc(&p->d_x_off, ns)) && ok(dalloc(&p->d_x_len, ns))) {
     std::vector<SeriesDev> sd(ns);
     std::vector<int64_t> to(ns + 1), so(ns + 1);
     for (size_t i = 0; i < ns; ++i) {
@@ -242,6 +245,13 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
     to[ns] = tl;
     so[ns] = sg;
     ok(cuda_ok_or(cudaMemcpy(p->d_series, sd.data(), ns * sizeof(SeriesDev), cudaMemcpyHostToDevice)));
+    std::vector<int64_t> xo(ns), xl(ns);
+    for (size_t i = 0; i < ns; ++i) {
+      xo[i] = p->series[i].x_off;
+      xl[i] = p->series[i].n;
+    }
+    ok(cuda_ok_or(cudaMemcpy(p->d_x_off, xo.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice)));
+    ok(cuda_ok_or(cudaMemcpy(p->d_x_len, xl.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(cuda_ok_or(cudaMemcpy(p->d_tile_off, to.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(cuda_ok_or(cudaMemcpy(p->d_seg_off, so.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(cuda_ok_or(cudaMemset(p->d_slots, 0, total_slots * sizeof(unsigned long long))));

@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-series batched measurement")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiable 4096-binary measurement")
     return ap.parse_args()
 
 
@@ -242,6 +243,68 @@ def run_batched(torch, pkg, synth, dev, stream, steps):
             "l2": "inputs (8.2 GB) far larger than L2"}
 
 
+def run_diff(torch, pkg, synth, dev, stream, steps):
+    """Differentiable batch: logsumexp forward and hand-written backward over
+    4096 binaries of 2^20 samples (widths 1..512, L = 2048, tau = 0.1)."""
+    cfg = synth.WORKLOADS["diff_4096"]
+    n, n_series, w_max, seg_len, tau = cfg["n"], cfg["n_series"], cfg["z_max"], cfg["segment_len"], cfg["tau"]
+    m = n // 2 + 1
+    lib = pkg.load()
+    plan = pkg.Plan(lengths=[n] * n_series, z_max=w_max, segment_len=seg_len, threshold_sigma=6.0)
+    xo = plan.offsets()[0]
+    f32 = dict(dtype=torch.float32, device=dev)
+    x = torch.empty(plan.x_floats, **f32)
+    tmpl = torch.empty(plan.x_floats, **f32)
+    with torch.cuda.stream(stream):
+        amps = torch.from_numpy(synth.diff_device(x, tmpl, xo, n, n_series)).to(dev)
+    torch.cuda.synchronize()
+    sp = stream.cuda_stream
+    rc = lib.pulscan_inject(plan._h, x.data_ptr(), tmpl.data_ptr(), amps.data_ptr(), x.data_ptr(), sp)
+    assert rc == 0
+    spec = torch.empty(plan.spec_floats, **f32)
+    power = torch.empty(plan.power_floats, **f32)
+    stats = torch.empty(4 * plan.total_segments, **f32)
+    sel = torch.empty(8 * plan.total_segments, **f32)
+    y = torch.empty(plan.total_segments * w_max, **f32)
+    gy = torch.ones_like(y)
+    gx = torch.empty(plan.x_floats, **f32)
+    gamp = torch.empty(n_series, **f32)
+
+    def fwd():
+        return lib.pulscan_lse_forward(plan._h, x.data_ptr(), spec.data_ptr(), power.data_ptr(), stats.data_ptr(),
+                                       sel.data_ptr(), y.data_ptr(), tau, sp)
+
+    def bwd():
+        rc = lib.pulscan_lse_backward(plan._h, spec.data_ptr(), power.data_ptr(), stats.data_ptr(), sel.data_ptr(),
+                                      y.data_ptr(), gy.data_ptr(), gx.data_ptr(), tau, sp)
+        return rc or lib.pulscan_amplitude_grad(plan._h, gx.data_ptr(), tmpl.data_ptr(), gamp.data_ptr(), sp)
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            assert fn() == 0
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    assert fwd() == 0 and bwd() == 0
+    t_f = timed(fwd, steps)
+    t_b = timed(bwd, steps)
+    ok = bool(torch.isfinite(gamp).all())
+    bw = n_series * m * w_max
+    plan.close()
+    return {"workload": f"diff_4096: {n_series} binaries x 2^20 samples (M={m}), widths 1..{w_max}, "
+                        f"segment_len={seg_len}, tau={tau}",
+            "ms_forward": t_f, "ms_backward": t_b, "forward_bin_widths_per_s": bw / (t_f * 1e-3) / 1e9,
+            "forward_backward_bin_widths_per_s": bw / ((t_f + t_b) * 1e-3) / 1e9, "unit": "G bin-widths/s",
+            "finite_gradients": ok,
+            "forward": "rfft + normalise (order statistics kept) + logsumexp of the boxcar bank",
+            "backward": "softmax-weighted boxcar scatter + median/MAD adjoint + C2R + amplitude reduction",
+            "l2": "inputs (17 GB) far larger than L2"}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2406_15186_gb300 as pkg
@@ -368,6 +431,12 @@ def run_ours(args, rank, world, local):
         del d_x, d_spec, d_power
         torch.cuda.empty_cache()
         line["batched"] = run_batched(torch, pkg, synth, dev, stream, max(3, args.steps // 4))
+        torch.cuda.empty_cache()
+    if not args.no_diff:
+        plan.close()
+        d_x = d_spec = d_power = None
+        torch.cuda.empty_cache()
+        line["differentiable"] = run_diff(torch, pkg, synth, dev, stream, 3)
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         spec, t_fft = oracle_fft(x)

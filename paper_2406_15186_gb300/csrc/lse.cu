@@ -21,6 +21,19 @@
 //   difference pair D[k] += g, D[k + w] -= g in shared memory; one block
 //   prefix sum of D gives dL/dP over the segment and a (W - 1)-bin tail that
 //   spills into the next segment (no global atomics);
+// * the register ring only flags, per width, which lanes hold a window
+//   within the cut (one lane max, one ballot per step); the flagged (lane,
+//   width) events are worked off after each 33-width block by the whole warp,
+//   one event at a time with a lane per window.  Keeping the exp / scatter
+//   code out of the 33 unrolled ring steps keeps the loop body small enough
+//   for the instruction cache;
+// * the running FP32 sums pick windows only: an exponent (S - M) / tau
+//   amplifies an absolute error in S by 1 / tau, and a sequential FP32 sum of
+//   w terms of size S carries up to ~ w * 2^-24 * S.  Each picked window's S
+//   is recomputed as F[k + w] - F[k] from a per-segment exclusive prefix sum
+//   F held in shared memory as an unevaluated pair of floats (hi + lo, built
+//   with error-free additions, carried between threads in FP64), which is
+//   accurate to about one rounding of S;
 // * normalise_backward_kernel: dL/dP -> dL/d(Re, Im) through Eq. 8, written
 //   as the input of a cuFFT C2R transform with the Hermitian weights (DC 0,
 //   interior halved, Nyquist real), whose output is dL/dx;
@@ -39,6 +52,64 @@ namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kLseMaxWarps = 4;
+
+// s + e == a + b exactly (Knuth's two-sum; explicit roundings, no contraction).
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+  const float t = __fadd_rn(a, b);
+  const float bb = __fsub_rn(t, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bb)), __fsub_rn(b, bb));
+  return t;
+}
+
+// Exclusive prefix F[j] = sum_{i<j} buf[i] for j = 0..n as fh[j] + fl[j].
+// Each thread sums a contiguous chunk with two-sum, the chunk totals are
+// scanned in FP64 (wtot: one double per warp), then each chunk is re-walked
+// from its FP64 carry split into a float pair.  Ends with a barrier.
+__device__ void build_prefix(const float *__restrict__ buf, int n, float *__restrict__ fh, float *__restrict__ fl,
+                             double *wtot) {
+  const int nt = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int chunk = (n + nt - 1) / nt;
+  const int a0 = min(n, static_cast<int>(threadIdx.x) * chunk), a1 = min(n, a0 + chunk);
+  float h = 0.0f, l = 0.0f, e;
+  for (int j = a0; j < a1; ++j) {
+    h = two_sum(h, buf[j], e);
+    l = __fadd_rn(l, e);
+  }
+  const double tot = static_cast<double>(h) + static_cast<double>(l);
+  double incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  double carry = incl - tot;
+  for (int v = 0; v < warp; ++v) carry += wtot[v];
+  h = static_cast<float>(carry);
+  l = static_cast<float>(carry - static_cast<double>(h));
+  // stored normalised (fast two-sum, |l| << |h|): |fl| <= half an ulp of fh
+  for (int j = a0; j < a1; ++j) {
+    const float hs = __fadd_rn(h, l);
+    fh[j] = hs;
+    fl[j] = __fsub_rn(l, __fsub_rn(hs, h));
+    h = two_sum(h, buf[j], e);
+    l = __fadd_rn(l, e);
+  }
+  if (threadIdx.x == nt - 1) {   // its chunk ends at n, or is empty with the full total as carry
+    const float hs = __fadd_rn(h, l);
+    fh[n] = hs;
+    fl[n] = __fsub_rn(l, __fsub_rn(hs, h));
+  }
+  __syncthreads();
+}
+
+// sum buf[a..b) = F[b] - F[a], to about one rounding.
+__device__ __forceinline__ float window_sum(const float *__restrict__ fh, const float *__restrict__ fl, int a, int b) {
+  float e;
+  const float d = two_sum(fh[b], -fh[a], e);
+  return __fadd_rn(d, __fadd_rn(e, __fsub_rn(fl[b], fl[a])));
+}
 
 // Ring steps C0..C0+NC-1 with a per-step callback cb(c) after the adds.
 template <int C0, int NC, class F>
@@ -134,29 +205,68 @@ __device__ __forceinline__ SegTile seg_tile(const SeriesDev *__restrict__ series
   return t;
 }
 
-// Valid bins of a lane at width w: inside the segment, window inside the spectrum.
-__device__ __forceinline__ int lane_lim(const SegTile &t, int x0, int w) {
-  const int64_t k0 = t.b0 + x0;
-  const int64_t lim = min64(static_cast<int64_t>(t.nb - x0), t.m - w + 1 - k0);
-  return static_cast<int>(max64(min64(lim, kR), 0));
+// Valid windows of the lane starting at local bin x at width w: start inside
+// the segment, window inside the spectrum:  lim(w) = clamp(min(a, b - w), 0, 33)
+// with a = nb - x and b = M - (b0 + x) + 1 fixed per lane.
+struct LaneLim {
+  int a, b;
+  __device__ __forceinline__ int at(int w) const { return max(0, min(kR, min(a, b - w))); }
+};
+
+__device__ __forceinline__ LaneLim lane_lim(const SegTile &t, int x) {
+  const int64_t bb = t.m - (t.b0 + x) + 1;
+  return LaneLim{t.nb - x, static_cast<int>(min64(bb, static_cast<int64_t>(1) << 30))};
 }
 
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// max over the lane's first lim windows (-inf if none).
 __device__ __forceinline__ float lane_max(const float (&s)[kR], int lim) {
   float m = -INFINITY;
   if (lim >= kR) {
-    float t16[16];
+    float t11[11];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) t16[i] = fmaxf(s[2 * i], s[2 * i + 1]);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) t16[i] = fmaxf(t16[2 * i], t16[2 * i + 1]);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) t16[i] = fmaxf(t16[2 * i], t16[2 * i + 1]);
-    m = fmaxf(fmaxf(fmaxf(t16[0], t16[1]), fmaxf(t16[2], t16[3])), s[kR - 1]);
+    for (int i = 0; i < 11; ++i) t11[i] = max3(s[3 * i], s[3 * i + 1], s[3 * i + 2]);
+    m = fmaxf(max3(max3(t11[0], t11[1], t11[2]), max3(t11[3], t11[4], t11[5]), max3(t11[6], t11[7], t11[8])),
+              fmaxf(t11[9], t11[10]));
   } else {
 #pragma unroll
     for (int i = 0; i < kR; ++i) m = fmaxf(m, (i < lim) ? s[i] : -INFINITY);
   }
   return m;
+}
+
+// Works off one width's events of this warp: every flagged lane's windows
+// (33 per event, packed over the warp's lanes) whose exact sum lies above
+// thr call f(k, S) with k the local start bin.  A window is first screened
+// with the high parts of the prefix alone: each is within half an ulp of F,
+// so fh[b] - fh[a] is within 1.5 ulp of S; the margin is 4 ulp of F[b].
+// my_lim: the calling lane's valid window count at w; evl: this warp's
+// 32-entry scratch for the list of flagged lanes.
+template <class F>
+__device__ __forceinline__ void for_event_windows(uint32_t bal, int warp, int lane, int my_lim, int w, float thr,
+                                                  const float *__restrict__ fh, const float *__restrict__ fl,
+                                                  int *evl, F &&f) {
+  if ((bal >> lane) & 1u) evl[__popc(bal & ((1u << lane) - 1u))] = lane | (my_lim << 8);
+  __syncwarp();
+  const int n = kR * __popc(bal);
+  for (int q = lane; q < n; q += 32) {
+    const int e = q / kR, i = q - kR * e;
+    const int ev = evl[e];
+    if (i < (ev >> 8)) {
+      const int k = warp * (32 * kR) + (ev & 255) * kR + i;
+      const float hb = fh[k + w];
+      if (hb - fh[k] > thr - 4.8e-7f * fabsf(hb)) {
+        const float sw = window_sum(fh, fl, k, k + w);
+        if (sw > thr) f(k, sw);
+      }
+    }
+  }
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
@@ -165,60 +275,56 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
     int buf_len) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+  double *wtot = reinterpret_cast<double *>(smem_raw + 32);
   uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
-  float *mrow = buf + buf_len;                   // W: M[s, w]
-  float *lsum = mrow + W;                        // W: sum of exp
-  float *kmax = lsum + W;                        // warps x 33 x 32 lane maxima
+  float *mblk = buf + buf_len;                   // 64: M of the current 33 widths
+  float *lsb = mblk + 64;                        // 64: their sums of exp
+  int *evl = reinterpret_cast<int *>(lsb + 64);  // warps x 32 flagged-lane lists
+  float *kmax = reinterpret_cast<float *>(evl + kLseMaxWarps * 32);   // warps x 33 x 32 lane maxima
   const int warps = blockDim.x >> 5;
+  float *fh = kmax + warps * kR * 32;            // prefix pair, buf_len + 1 each
+  float *fl = fh + buf_len + 1;
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
-  for (int j = threadIdx.x; j < W; j += blockDim.x) lsum[j] = 0.0f;
+  build_prefix(buf, buf_len, fh, fl, wtot);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int x0 = warp * (32 * kR) + lane * kR;
-  const float *lane_buf = buf + x0;
+  const LaneLim ll = lane_lim(t, x0);
+  const float inv_tau = 1.0f / tau;
   float s[kR];
-  // pass 1: M[s, w]
+  // One sweep over the widths.  Per step every lane stores the max of its 33
+  // windows; after each 33-width block the lane maxima give M[s, w] and the
+  // lanes with a window within `cut` of it, whose windows are then summed.
   walk_widths(
-      s, lane_buf, W,
-      [&](int w, int c) { kmax[(warp * kR + c) * 32 + lane] = lane_max(s, lane_lim(t, x0, w)); },
+      s, buf + x0, W, [&](int w, int c) { kmax[(warp * kR + c) * 32 + lane] = lane_max(s, ll.at(w)); },
       [&](int bi, int nsteps) {
         __syncthreads();
         for (int c = threadIdx.x; c < nsteps; c += blockDim.x) {
           float m = -INFINITY;
           for (int v = 0; v < warps; ++v)
             for (int l = 0; l < 32; ++l) m = fmaxf(m, kmax[(v * kR + c) * 32 + ((l + c) & 31)]);
-          mrow[bi * kR + c] = m;
+          mblk[c] = m;
+          lsb[c] = 0.0f;
         }
         __syncthreads();
-      });
-  // pass 2: sum of exp((S - M) / tau) over windows within `cut` of M
-  const float inv_tau = 1.0f / tau;
-  walk_widths(
-      s, lane_buf, W,
-      [&](int w, int c) {
-        const float mw = mrow[w - 1];
-        const float thr = mw - cut;
-        const int lim = lane_lim(t, x0, w);
-        bool near = false;
+        for (int c = 0; c < nsteps; ++c) {
+          const float mw = mblk[c];
+          const float thr = mw - cut;
+          const uint32_t bal = __ballot_sync(kFullMask, kmax[(warp * kR + c) * 32 + lane] > thr);
+          if (bal == 0u) continue;
+          float acc = 0.0f;
+          const int w = bi * kR + c + 1;
+          for_event_windows(bal, warp, lane, ll.at(w), w, thr, fh, fl, evl + warp * 32,
+                            [&](int, float sw) { acc += expf((sw - mw) * inv_tau); });
 #pragma unroll
-        for (int i = 0; i < kR; ++i) near |= (i < lim) && (s[i] > thr);
-        if (!__any_sync(kFullMask, near)) return;
-        float acc = 0.0f;
-        if (near) {
-#pragma unroll
-          for (int i = 0; i < kR; ++i)
-            if (i < lim && s[i] > thr) acc += expf((s[i] - mw) * inv_tau);
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+          if (lane == 0) atomicAdd(&lsb[c], acc);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
-        if (lane == 0 && acc > 0.0f) atomicAdd(&lsum[w - 1], acc);
-        (void)c;
-      },
-      [&](int, int) {});
-  __syncthreads();
-  for (int j = threadIdx.x; j < W; j += blockDim.x)
-    y[t.seg_g * static_cast<int64_t>(W) + j] = mrow[j] + tau * logf(lsum[j]);
+        __syncthreads();
+        for (int c = threadIdx.x; c < nsteps; c += blockDim.x)
+          y[t.seg_g * static_cast<int64_t>(W) + bi * kR + c] = mblk[c] + tau * logf(lsb[c]);
+      });
 }
 
 __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
@@ -228,14 +334,20 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
     int buf_len, int d_len) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+  double *wtot = reinterpret_cast<double *>(smem_raw + 32);
   uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
   float *yrow = buf + buf_len;
   float *grow = yrow + W;
   float *dd = grow + W;                          // d_len difference entries
   float *wsum = dd + d_len;                      // per-warp scan totals
+  uint32_t *evm = reinterpret_cast<uint32_t *>(wsum + 32);   // warps x 33 event ballots
+  int *evl = reinterpret_cast<int *>(evm + kLseMaxWarps * kR);   // warps x 32 flagged-lane lists
+  float *fh = reinterpret_cast<float *>(evl + kLseMaxWarps * 32);   // prefix pair, buf_len + 1 each
+  float *fl = fh + buf_len + 1;
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
+  build_prefix(buf, buf_len, fh, fl, wtot);
   for (int j = threadIdx.x; j < W; j += blockDim.x) {
     yrow[j] = y[t.seg_g * static_cast<int64_t>(W) + j];
     grow[j] = gy[t.seg_g * static_cast<int64_t>(W) + j];
@@ -246,31 +358,32 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   const int x0 = warp * (32 * kR) + lane * kR;
   const float *lane_buf = buf + x0;
   const float inv_tau = 1.0f / tau;
+  uint32_t *wev = evm + warp * kR;
+  const LaneLim ll = lane_lim(t, x0);
   float s[kR];
   walk_widths(
       s, lane_buf, W,
       [&](int w, int c) {
-        const float yw = yrow[w - 1];
-        const float gw = grow[w - 1];
-        const float thr = yw - cut;
-        const int lim = lane_lim(t, x0, w);
-        bool near = false;
-#pragma unroll
-        for (int i = 0; i < kR; ++i) near |= (i < lim) && (s[i] > thr);
-        if (!__any_sync(kFullMask, near) || gw == 0.0f) return;
-        if (near) {
-#pragma unroll
-          for (int i = 0; i < kR; ++i) {
-            if (i < lim && s[i] > thr) {
-              const float g = gw * expf((s[i] - yw) * inv_tau);
-              atomicAdd(&dd[x0 + i], g);
-              atomicAdd(&dd[x0 + i + w], -g);
-            }
-          }
-        }
-        (void)c;
+        const bool ev = grow[w - 1] != 0.0f && lane_max(s, ll.at(w)) > yrow[w - 1] - cut;
+        const uint32_t bal = __ballot_sync(kFullMask, ev);
+        if (lane == 0) wev[c] = bal;
       },
-      [&](int, int) {});
+      [&](int bi, int nsteps) {
+        __syncwarp();
+        for (int c = 0; c < nsteps; ++c) {
+          const uint32_t bal = wev[c];
+          if (bal == 0u) continue;
+          const int w = bi * kR + c + 1;
+          const float yw = yrow[w - 1];
+          const float gw = grow[w - 1];
+          for_event_windows(bal, warp, lane, ll.at(w), w, yw - cut, fh, fl, evl + warp * 32, [&](int k, float sw) {
+            const float g = gw * expf((sw - yw) * inv_tau);
+            atomicAdd(&dd[k], g);
+            atomicAdd(&dd[k + w], -g);
+          });
+        }
+        __syncwarp();
+      });
   __syncthreads();
   // inclusive prefix sum of dd: thread t owns a contiguous chunk
   const int nt = blockDim.x;
@@ -554,7 +667,7 @@ int pulscan_lse_forward(pulscan_plan p, const float *d_x, float *d_spec, float *
   if (rc) return rc;
   const int warps = lse_warps(p);
   const int buf_len = lse_buf_len(p, warps);
-  const int smem = 128 + 4 * (buf_len + 2 * p->z_max + warps * kR * 32);
+  const int smem = 128 + 4 * (buf_len + 128 + kLseMaxWarps * 32 + warps * kR * 32 + 2 * (buf_len + 1));
   rc = ensure_smem(lse_forward_kernel, smem, g_lim_fwd);
   if (rc) return rc;
   lse_forward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
@@ -580,7 +693,8 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   int64_t max_n = 0;
   for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
   const int d_len = static_cast<int>(max_n + p->z_max + 1);
-  const int smem = 128 + 4 * (buf_len + 2 * p->z_max + d_len + 32);
+  const int smem =
+      128 + 4 * (buf_len + 2 * p->z_max + d_len + 32 + kLseMaxWarps * (kR + 32) + 2 * (buf_len + 1));
   rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
   if (rc) return rc;
   lse_backward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(

@@ -165,3 +165,21 @@ def batch_device(x_all, offsets, lengths, tone_mask, workload_id=3):
             device_inject(seg, tones)
             tones_of[i] = tones
     return tones_of
+
+
+def diff_device(noise, template, offsets, n, n_series, workload_id=4):
+    """Fill the differentiable workload on the device: per binary i, noise and
+    its unit-amplitude template (spin bin, drift z and jerk w from
+    binary_params); returns the amplitudes (float32 numpy, log-uniform
+    0.01-0.1)."""
+    import torch
+    amps = np.zeros(n_series, dtype=np.float32)
+    u = torch.arange(int(n), device=noise.device, dtype=torch.float64) / float(n)
+    for i in range(n_series):
+        o = int(offsets[i])
+        noise[o: o + n].copy_(device_noise(n, seed_of(workload_id, i), device=noise.device))
+        b = binary_params(i, n)
+        ph = b["r0"] * u + 0.5 * b["z"] * u * u + (b["w"] / 6.0) * u * u * u
+        template[o: o + n].copy_(torch.cos(2.0 * np.pi * ph + b["phi0"]).to(torch.float32))
+        amps[i] = b["amp"]
+    return amps

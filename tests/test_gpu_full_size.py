@@ -6,6 +6,8 @@
   (stage A and B on their GPU intermediates, candidates).
 * single_2p27: sampled segments (stage A and B), FFT checked on sampled bins
   against the DFT definition.
+* diff_4096: the whole batch forward and backward through torch.autograd;
+  sampled binaries checked against the oracle's logsumexp and adjoint.
 """
 import math
 
@@ -182,3 +184,69 @@ def test_single_2p27_sampled(pkg):
         mx_ref, am_ref = parity.check_maxima(p64, gmx, gam, w_max, seg_len, seg_range=(r, r + 1))
         parity.check_candidates(cands, p64, mx_ref, am_ref, w_max, seg_len, sigma, parity.n_trials_of(m, w_max),
                                 seg_rows=(r, r + 1))
+
+
+
+def test_diff_4096_sampled(pkg):
+    """The differentiable batch at full size (4096 x 2^20, widths 1..512, L =
+    2048, tau = 0.1) forward and backward through torch.autograd; binaries 0
+    and 4095 against the oracle.
+
+    Y against the oracle's FP64 chain from the same float32 x, to 1e-4 *
+    max(|Y|, w) (the oracle recomputes the FFT and the medians in FP64, so the
+    powers differ by a few 1e-6).  dL/dx against the oracle's adjoint taken
+    from the GPU's own spectrum: the median / MAD derivatives sit on selected
+    order statistics, and an FP32 and an FP64 spectrum of the same x can
+    select different elements where two deviations are within rounding of
+    each other (binary 4095 has one such block), which moves a whole block's
+    MAD term to another bin.  rel-L2 5e-3: amplitudes <= 0.1 keep |S| and |Y|
+    below 4096, whose half ulp is 2.4e-4, and the kernels' window sums and Y
+    are each within about one rounding, so a softmax weight
+    exp((S - Y) / tau) is off by <= 4.9e-4 / tau in the worst case.  dL/dA:
+    the amplitude kernel's reduction against the FP64 dot product of the
+    GPU's own dL/dx with the template, to 1e-5 of sum |g t|."""
+    from oracle import lse as olse
+    from oracle import normalise as onorm
+    from paper_2406_15186_gb300 import lse
+    cfg = synth.WORKLOADS["diff_4096"]
+    n, n_series, w_max, seg_len, tau = cfg["n"], cfg["n_series"], cfg["z_max"], cfg["segment_len"], cfg["tau"]
+    m = n // 2 + 1
+    plan = pkg.Plan(lengths=[n] * n_series, z_max=w_max, segment_len=seg_len, threshold_sigma=6.0)
+    xo, so, _, go = plan.offsets()
+    noise = torch.empty(plan.x_floats, device="cuda")
+    tmpl = torch.empty(plan.x_floats, device="cuda")
+    amps = synth.diff_device(noise, tmpl, xo, n, n_series)
+    amp = torch.from_numpy(amps).cuda().requires_grad_(True)
+    x = lse.inject(noise, tmpl, amp, plan)
+    x.retain_grad()
+    y = lse.lse_statistic(x, plan, tau)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(4044)
+    gy = torch.randn(tuple(y.shape), generator=g, device="cuda")
+    (y * gy).sum().backward()
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all() and torch.isfinite(amp.grad).all() and torch.isfinite(x.grad).all()
+    del noise
+    spec = torch.empty(plan.spec_floats, device="cuda")
+    plan.rfft(x.detach(), spec)
+    torch.cuda.synchronize()
+    n_seg = m // seg_len
+    w = np.arange(1, w_max + 1)[None, :]
+    ga_gpu = amp.grad.cpu().numpy().astype(np.float64)
+    for i in (0, n_series - 1):
+        xi = x.detach()[xo[i]: xo[i] + n].cpu().numpy().astype(np.float64)
+        ti = tmpl[xo[i]: xo[i] + n].cpu().numpy().astype(np.float64)
+        yi = y.detach()[go[i]: go[i] + n_seg].cpu().numpy().astype(np.float64)
+        gyi = gy[go[i]: go[i] + n_seg].cpu().numpy().astype(np.float64)
+        gxi = x.grad[xo[i]: xo[i] + n].cpu().numpy().astype(np.float64)
+        y_ref, _ = olse.forward(xi, w_max, seg_len, tau)
+        assert np.all(np.abs(yi - y_ref) <= 1e-4 * np.maximum(np.abs(y_ref), w)), i
+        z = spec[2 * so[i]: 2 * (so[i] + m)].cpu().numpy().reshape(-1, 2).astype(np.float64)
+        zi = z[:, 0] + 1j * z[:, 1]
+        p_ref, stats, flags = onorm.normalise_power(zi, seg_len)
+        assert not flags.any()
+        y_o = olse.forward_power(p_ref, w_max, seg_len, tau)
+        gx_ref = olse.backward(xi, dict(spec=zi, p=p_ref, stats=stats), y_o, gyi, w_max, seg_len, tau)
+        rel = np.linalg.norm(gxi - gx_ref) / np.linalg.norm(gx_ref)
+        assert rel <= 5e-3, (i, rel)
+        assert abs(ga_gpu[i] - float(np.dot(gxi, ti))) <= 1e-5 * float(np.sum(np.abs(gxi * ti))), i

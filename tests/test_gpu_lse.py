@@ -9,9 +9,10 @@ pulscan_amplitude_grad and torch.autograd.
 Tolerances.  Y: 1e-5 * max(|Y_ref|, w), as for the boxcar maxima (Y is a
 smoothed maximum of the same sums).  Gradients: the softmax weights
 exp((S - Y) / tau) turn an error dS in a sum into a relative weight error
-dS / tau; FP32 sums of the power carry dS ~ 1e-6 S, so for sums up to a few
-hundred the weights, and the gradient, agree to a few 1e-3 at tau = 0.1 and
-a few 1e-4 at tau = 1: rel-L2 <= 5e-3 (tau 0.1) and 1e-3 (tau 1).
+dS / tau.  The kernels take S of every weighted window from a float-pair
+prefix sum (about one rounding of S) and Y is FP32, so dS <= 2^-23 |S|; with
+|S| < 256 here that is <= 1.5e-5 / tau per weight, and the FP32 difference
+array, normalisation adjoint and C2R add ~1e-5: rel-L2 <= 1e-3 at both tau.
 """
 import numpy as np
 import pytest
@@ -24,7 +25,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-GRAD_TOL = {0.1: 5e-3, 1.0: 1e-3}
+GRAD_TOL = {0.1: 1e-3, 1.0: 1e-3}
 
 
 @pytest.fixture(scope="module")

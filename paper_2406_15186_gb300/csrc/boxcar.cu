@@ -367,39 +367,53 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
   }
 }
 
-// Lane's best window among its bins [ia, ib) (power bits << 32 | ~bin), or 0.
-__device__ __forceinline__ unsigned long long lane_best(const float (&s)[kR], int64_t k0, int ia, int ib) {
-  float v[kR];
-#pragma unroll
-  for (int i = 0; i < kR; ++i) v[i] = (i >= ia && i < ib) ? s[i] : -1.0f;
-  // max over 33 values as a tree (short dependency chains)
-  float m16[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) m16[i] = fmaxf(v[2 * i], v[2 * i + 1]);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) m16[i] = fmaxf(m16[2 * i], m16[2 * i + 1]);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) m16[i] = fmaxf(m16[2 * i], m16[2 * i + 1]);
-  const float m = fmaxf(fmaxf(fmaxf(m16[0], m16[1]), fmaxf(m16[2], m16[3])), v[kR - 1]);
-  if (!(m >= 0.0f)) return 0ull;
-  uint32_t eq = 0u;
-#pragma unroll
-  for (int i = 0; i < 32; ++i) eq |= (v[i] == m) ? (1u << i) : 0u;
-  const int first = eq ? (__ffs(static_cast<int>(eq)) - 1) : (kR - 1);
-  return slot_key(m, static_cast<uint32_t>(k0 + first));
+// Deferred blocks, one CTA of four warps per work item.  The item is the
+// 32 x 33 x 33 block (lanes x bins x widths) one warp of the search kernel
+// left, with its 33 x 32 running sums saved in a snapshot.  Warp q takes bins
+// [kSplit[q], kSplit[q + 1]) of every lane's 33 (9 + 8 + 8 + 8), so each thread
+// carries at most 9 running sums through the block's remaining widths and the
+// serial chain per item is a quarter of one warp doing it all.  The P window
+// (32 x 33 bins plus the 66-bin reach of one block) is staged in shared
+// memory.  Phase 1: per step each thread forms the best key of its bins in
+// each segment part, and only when that reaches T_w (rare) merges it into
+// keys[part][lane][step] with a shared 64-bit max.  Phase 2: one thread per
+// width merges the 32 lanes' keys segment by segment and sends every maximum
+// to its slot.
+constexpr int kRegion = 32 * kR + 2 * kR;
+constexpr int kDeferWarps = 4;
+constexpr int kSubBins = 9;
+__constant__ int kSplit[kDeferWarps + 1] = {0, 9, 17, 25, 33};
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
 }
 
-// Deferred blocks, one warp per work item.  The warp reloads its 33 x 32
-// running sums from the snapshot and stages the block's window of P (32 x 33
-// bins plus the 66-bin reach of one block) into shared memory.  Phase 1 runs
-// the remaining steps of the block: per step each lane records the key of its
-// best window per segment part in shared memory (no warp-wide operation in
-// the step loop).  Phase 2 gives each lane one width: it merges the 32 lanes'
-// keys segment by segment and sends every maximum that reaches T_w to its
-// slot.  Items are independent, so the warps of the whole GPU share them
-// instead of one warp walking every width of a busy region.
-constexpr int kRegion = 32 * kR + 2 * kR;
-constexpr int kDeferWarps = 2;
+// Key of the best of v[0..n) whose lane index i0 + j lies in [ia, ib), or 0
+// when that best is below T.  v[n..9) hold -1 (never a window sum).  In
+// deferred blocks most windows reach T, so the first-index search is a
+// branch-free equality mask.
+__device__ __forceinline__ unsigned long long sub_key(const float (&v)[kSubBins], int n, int i0, int ia, int ib,
+                                                      int64_t k0, float T) {
+  uint32_t in = 0x1ffu;   // bits j of v that lie in [ia, ib)
+  float m;
+  if (ia <= i0 && ib >= i0 + n) {
+    m = fmaxf(max3f(max3f(v[0], v[1], v[2]), max3f(v[3], v[4], v[5]), max3f(v[6], v[7], v[8])), -1.0f);
+  } else {
+    const int lo = max(ia - i0, 0), hi = min(ib - i0, n);
+    in = (hi > lo) ? (((1u << hi) - 1u) & ~((1u << lo) - 1u)) : 0u;
+    m = -1.0f;
+#pragma unroll
+    for (int j = 0; j < kSubBins; ++j) m = fmaxf(m, ((in >> j) & 1u) ? v[j] : -1.0f);
+  }
+  if (!(m >= T) || !(m >= 0.0f)) return 0ull;
+  uint32_t eq = 0u;
+#pragma unroll
+  for (int j = 0; j < kSubBins; ++j) eq |= (v[j] == m) ? (1u << j) : 0u;
+  eq &= in;
+  return slot_key(m, static_cast<uint32_t>(k0 + i0 + (__ffs(static_cast<int>(eq)) - 1)));
+}
 
 __global__ void __launch_bounds__(32 * kDeferWarps) deferred_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
@@ -407,15 +421,15 @@ __global__ void __launch_bounds__(32 * kDeferWarps) deferred_kernel(
     uint32_t *__restrict__ dirty, const uint32_t *__restrict__ counters,
     const unsigned long long *__restrict__ items, const float *__restrict__ snaps, uint32_t item_cap,
     int tile_bins) {
-  __shared__ float region_all[kDeferWarps][kRegion];
-  // keys[part][lane][step]: lane-major so both phases are bank-conflict free
-  __shared__ unsigned long long keys_all[kDeferWarps][2][32][kR];
-  __shared__ long long segs_all[kDeferWarps][32];
+  __shared__ float region[kRegion];
+  // keys[part][lane][step]: lane-major so phase 2 reads are bank-conflict free
+  __shared__ unsigned long long keys[2][32][kR];
+  __shared__ long long segs[32];
+  __shared__ float tcache[kR];   // T_w of the block's widths
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float *region = region_all[warp];
+  const int i0 = kSplit[warp], nb = kSplit[warp + 1] - i0;
   const uint32_t n_items = min(counters[0], item_cap);
-  const uint32_t stride = gridDim.x * kDeferWarps;
-  for (uint32_t it = blockIdx.x * kDeferWarps + warp; it < n_items; it += stride) {
+  for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const unsigned long long item = items[it];
     const int64_t tile = static_cast<int64_t>(item & 0xffffffffffull);
     const int wv = static_cast<int>((item >> 40) & 3ull);
@@ -426,50 +440,51 @@ __global__ void __launch_bounds__(32 * kDeferWarps) deferred_kernel(
     const int64_t t0 = (tile - S.tile_off) * static_cast<int64_t>(tile_bins);
     const int64_t r0 = t0 + wv * (32 * kR) + bi * kR + cx;   // first bin of the staged window
     const float *src = power + S.p_off;
-    __syncwarp();
-    for (int j = lane; j < kRegion; j += 32) region[j] = (r0 + j < S.m) ? src[r0 + j] : 0.0f;
-    __syncwarp();
-    const LaneCtx c = lane_ctx(S, t0, tile_bins, wv, lane, W, seg_len, slots, dirty);
-    float s[kR];
-    const float *sp = snaps + static_cast<size_t>(it) * (kR * 32) + lane;
-#pragma unroll
-    for (int i = 0; i < kR; ++i) s[i] = sp[i * 32];
-    // lane_buf[w - 1 + i] must address bin k0 + w - 1 + i of the window
-    const float *lane_buf = region + lane * kR - (bi * kR + cx);
+    __syncthreads();   // the previous item is finished with the shared arrays
+    for (int j = threadIdx.x; j < kRegion; j += blockDim.x) region[j] = (r0 + j < S.m) ? src[r0 + j] : 0.0f;
+    for (int j = threadIdx.x; j < 2 * 32 * kR; j += blockDim.x) (&keys[0][0][0])[j] = 0ull;
     const int nsteps = min(kR, W - bi * kR);
     const int wf = bi * kR + 1;
     const float *thr = thr_all + static_cast<int64_t>(si) * W;
-    if (seg_len < 2 * kR) {
-      // lane bins may span three segments: merge per step (test shapes only)
-      exact_steps<true>(s, lane_buf, wf, cx, nsteps, thr, c);
-      continue;
-    }
-    const bool any_split = __any_sync(kFull, c.ib < kR);
-    unsigned long long(*keys)[32][kR] = keys_all[warp];
-    long long *segs = segs_all[warp];
-    segs[lane] = c.seg_a;
+    if (threadIdx.x < nsteps) tcache[threadIdx.x] = thr[wf - 1 + threadIdx.x];
+    const float *sp = snaps + static_cast<size_t>(it) * (kR * 32) + lane;
+    float v[kSubBins];
+#pragma unroll
+    for (int j = 0; j < kSubBins; ++j) v[j] = (j < nb) ? sp[(i0 + j) * 32] : -1.0f;
+    const LaneCtx c = lane_ctx(S, t0, tile_bins, wv, lane, W, seg_len, slots, dirty);
+    if (warp == 0) segs[lane] = c.seg_a;
+    __syncthreads();
+    // lane_buf[w - 1 + i] addresses bin k0 + w - 1 + i of the window
+    const float *lane_buf = region + lane * kR - (bi * kR + cx);
+    const bool split = c.ib < kR;
+    // valid windows of the lane at width w: min(lim_tile, max(0, base - w))
+    const int base = static_cast<int>(min64(c.m + 1 - c.k0, static_cast<int64_t>(1) << 30));
     for (int cc = cx; cc < nsteps; ++cc) {
       const int w = wf + cc;
-      const float *pw = lane_buf + (w - 1);
+      const float *pw = lane_buf + (w - 1) + i0;
 #pragma unroll
-      for (int i = 0; i < kR; ++i) s[i] += pw[i];
-      const int64_t lim64 = c.m - w + 1 - c.k0;
-      const int lim = static_cast<int>(min64(static_cast<int64_t>(c.lim_tile), max64(lim64, 0)));
-      keys[0][lane][cc] = lane_best(s, c.k0, 0, min(c.ib, lim));
-      keys[1][lane][cc] = any_split ? lane_best(s, c.k0, c.ib, lim) : 0ull;
+      for (int j = 0; j < kSubBins - 1; ++j) v[j] += pw[j];
+      if (nb == kSubBins) v[kSubBins - 1] += pw[kSubBins - 1];
+      const int lim = min(c.lim_tile, max(0, base - w));
+      const float T = tcache[cc];
+      const unsigned long long ka = sub_key(v, nb, i0, 0, min(c.ib, lim), c.k0, T);
+      if (ka) atomicMax(&keys[0][lane][cc], ka);
+      if (split) {
+        const unsigned long long kb = sub_key(v, nb, i0, c.ib, lim, c.k0, T);
+        if (kb) atomicMax(&keys[1][lane][cc], kb);
+      }
     }
-    __syncwarp();
-    // phase 2: lane -> width.  The lanes' segments are non-decreasing along
+    __syncthreads();
+    // phase 2: thread -> width.  The lanes' segments are non-decreasing along
     // (lane, part A, part B), so a running maximum is flushed whenever the
     // segment changes.
-    for (int cc = cx + lane; cc < nsteps; cc += 32) {
+    const int cc = cx + static_cast<int>(threadIdx.x);
+    if (cc < nsteps) {
       const int w = wf + cc;
-      const float T = thr[w - 1];
       int64_t cur = -1;
       unsigned long long best = 0ull;
       auto flush = [&]() {
-        if (best != 0ull && __uint_as_float(static_cast<uint32_t>(best >> 32)) >= T)
-          emit_slot<true>(slots, dirty, static_cast<uint64_t>(cur) * W + (w - 1), best);
+        if (best != 0ull) emit_slot<true>(slots, dirty, static_cast<uint64_t>(cur) * W + (w - 1), best);
       };
       for (int l = 0; l < 32; ++l) {
         const int64_t sa = segs[l];
@@ -480,20 +495,55 @@ __global__ void __launch_bounds__(32 * kDeferWarps) deferred_kernel(
           best = 0ull;
         }
         best = max(best, ka);
-        if (any_split) {
-          const unsigned long long kb = keys[1][l][cc];
-          if (kb != 0ull) {
-            if (sa + 1 != cur) {
-              flush();
-              cur = sa + 1;
-              best = 0ull;
-            }
-            best = max(best, kb);
+        const unsigned long long kb = keys[1][l][cc];
+        if (kb != 0ull) {
+          if (sa + 1 != cur) {
+            flush();
+            cur = sa + 1;
+            best = 0ull;
           }
+          best = max(best, kb);
         }
       }
       flush();
     }
+  }
+}
+
+// Deferred blocks when segments are shorter than 66 bins (a lane's 33 bins
+// may then reach a third segment, and every bin is merged on its own; only
+// tiny test shapes): one warp per item with all 33 sums.
+__global__ void __launch_bounds__(128) deferred_small_kernel(
+    const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
+    int n_series, int W, int seg_len, const float *__restrict__ thr_all, unsigned long long *__restrict__ slots,
+    uint32_t *__restrict__ dirty, const uint32_t *__restrict__ counters,
+    const unsigned long long *__restrict__ items, const float *__restrict__ snaps, uint32_t item_cap,
+    int tile_bins) {
+  __shared__ float region_all[4][kRegion];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *region = region_all[warp];
+  const uint32_t n_items = min(counters[0], item_cap);
+  for (uint32_t it = blockIdx.x * 4 + warp; it < n_items; it += gridDim.x * 4) {
+    const unsigned long long item = items[it];
+    const int64_t tile = static_cast<int64_t>(item & 0xffffffffffull);
+    const int wv = static_cast<int>((item >> 40) & 3ull);
+    const int bi = static_cast<int>((item >> 42) & 0x3fffull);
+    const int cx = static_cast<int>((item >> 56) & 0xffull);
+    const int si = series_of_tile(tile_off, n_series, tile);
+    const SeriesDev S = series[si];
+    const int64_t t0 = (tile - S.tile_off) * static_cast<int64_t>(tile_bins);
+    const int64_t r0 = t0 + wv * (32 * kR) + bi * kR + cx;
+    const float *src = power + S.p_off;
+    __syncwarp();
+    for (int j = lane; j < kRegion; j += 32) region[j] = (r0 + j < S.m) ? src[r0 + j] : 0.0f;
+    __syncwarp();
+    const LaneCtx c = lane_ctx(S, t0, tile_bins, wv, lane, W, seg_len, slots, dirty);
+    float s[kR];
+    const float *sp = snaps + static_cast<size_t>(it) * (kR * 32) + lane;
+#pragma unroll
+    for (int i = 0; i < kR; ++i) s[i] = sp[i * 32];
+    exact_steps<true>(s, region + lane * kR - (bi * kR + cx), bi * kR + 1, cx, min(kR, W - bi * kR),
+                      thr_all + static_cast<int64_t>(si) * W, c);
   }
 }
 
@@ -556,9 +606,14 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
     PS_CUDA(cudaGetLastError());
     record(p, 5, s);
     record(p, 6, s);
-    deferred_kernel<<<p->defer_grid, 32 * kDeferWarps, 0, s>>>(
-        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
-        p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
+    if (p->seg_len >= 2 * kR)
+      deferred_kernel<<<p->defer_grid, 32 * kDeferWarps, 0, s>>>(
+          d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+          p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
+    else
+      deferred_small_kernel<<<p->defer_grid, 128, 0, s>>>(
+          d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+          p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
     PS_CUDA(cudaGetLastError());
     record(p, 7, s);
   } else {

@@ -28,6 +28,8 @@
 //
 // Dump mode (pulscan_segment_maxima) runs every block exactly and merges the
 // maximum of every (segment, width) with no threshold.
+#include <algorithm>
+
 #include "bank.cuh"
 #include "common.cuh"
 #include "ptx.cuh"
@@ -230,14 +232,15 @@ __device__ __forceinline__ bool defer_block(const float (&s)[kR], unsigned long 
   return true;
 }
 
+// One tile: stage P[t0, t0 + buf_len) by a TMA bulk copy, form the bound
+// sums, run the bank.  Returns false when the copy timed out (flagged).
 template <bool kSearch>
-__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
-    const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
-    int n_series, int W, int seg_len, const float *__restrict__ thr_all, const float *__restrict__ thrb_all,
-    unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty, uint32_t *__restrict__ counters,
-    unsigned long long *__restrict__ items, float *__restrict__ snaps, uint32_t item_cap, int tile_bins,
-    int buf_len) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ bool boxcar_tile(
+    int64_t tile, unsigned char *smem_raw, const float *__restrict__ power, const SeriesDev *__restrict__ series,
+    const int64_t *__restrict__ tile_off, int n_series, int W, int seg_len, const float *__restrict__ thr_all,
+    const float *__restrict__ thrb_all, unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty,
+    uint32_t *__restrict__ counters, unsigned long long *__restrict__ items, float *__restrict__ snaps,
+    uint32_t item_cap, int tile_bins, int buf_len) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
   const int nq33 = buf_len / kR;        // 33-bin block sums
@@ -246,7 +249,6 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
   float *q11 = q33 + nq33 + 1;
   const int nthreads = blockDim.x;
 
-  const int64_t tile = blockIdx.x;
   const int si = series_of_tile(tile_off, n_series, tile);
   const SeriesDev S = series[si];
   const int64_t t0 = (tile - S.tile_off) * static_cast<int64_t>(tile_bins);
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
   __syncthreads();
   if (q33[0] == 0.0f) {
     if (threadIdx.x == 0) atomicOr(counters + 2, kErrTimeout);
-    return;   // nothing else is in flight: the only copy is this one
+    return false;   // nothing else is in flight: the only copy is this one
   }
   __syncthreads();
 
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
 
   if (!kSearch) {
     exact_steps<false>(s, lane_buf, 1, 0, W, thr, c);
-    return;
+    return true;
   }
 
 #pragma unroll
@@ -364,6 +366,86 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
       continue;
     }
     fast_steps<2 * kSub, kSub>(s, b, pb);
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t sm_id() {
+  uint32_t id;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+  return id;
+}
+
+// The bank over all tiles.  With tile_ctr == nullptr every CTA takes tile
+// blockIdx.x.  Otherwise the launch is persistent (a few CTAs per SM): the
+// tiles are split into n_ranges contiguous ranges [range_lo[r],
+// range_lo[r + 1]), one per SM, each with a claim counter in tile_ctr
+// (zeroed before the launch).  A CTA claims tiles from the range of the SM
+// it runs on (%smid modulo n_ranges), one atomic per tile, issued before the
+// current tile runs so its latency is hidden; when that range is drained,
+// warp 0 reads all counters at once and claims from any range with tiles
+// left.  So every SM gets the same share of the work however the hardware
+// places the CTAs, and no tile is left while any CTA runs.  (A
+// one-CTA-per-tile grid refills the SMs that free their slots first, which
+// leaves a partial last wave on some SMs only.)
+template <bool kSearch>
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
+    const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
+    int n_series, int W, int seg_len, const float *__restrict__ thr_all, const float *__restrict__ thrb_all,
+    unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty, uint32_t *__restrict__ counters,
+    unsigned long long *__restrict__ items, float *__restrict__ snaps, uint32_t item_cap, int tile_bins,
+    int buf_len, uint32_t *__restrict__ tile_ctr, const int64_t *__restrict__ range_lo, int n_ranges) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (tile_ctr == nullptr) {
+    boxcar_tile<kSearch>(blockIdx.x, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all, thrb_all,
+                         slots, dirty, counters, items, snaps, item_cap, tile_bins, buf_len);
+    return;
+  }
+  int64_t *claim = reinterpret_cast<int64_t *>(smem_raw + 64);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int home = static_cast<int>(sm_id() % static_cast<uint32_t>(n_ranges));
+  const int64_t home_lo = range_lo[home], home_hi = range_lo[home + 1];
+  bool home_open = true;   // thread 0
+  auto claim_home = [&]() -> int64_t {
+    if (!home_open) return -1;
+    const int64_t t = home_lo + atomicAdd(tile_ctr + home, 1u);
+    if (t < home_hi) return t;
+    home_open = false;
+    return -1;
+  };
+  int64_t mine = (threadIdx.x == 0) ? claim_home() : -1;
+  for (;;) {
+    if (warp == 0) {
+      int64_t t = __shfl_sync(kFull, mine, 0);
+      // home drained: claim from any range with tiles left (every range is
+      // visited once per pass; claims only grow, so the pass ends)
+      for (int base = 0; t < 0 && base < n_ranges; base += 32) {
+        const int r = base + lane;
+        bool left = false;
+        if (r < n_ranges) left = static_cast<int64_t>(__ldcg(tile_ctr + r)) < range_lo[r + 1] - range_lo[r];
+        uint32_t m = __ballot_sync(kFull, left);
+        while (m != 0u && t < 0) {
+          const int rr = base + __ffs(static_cast<int>(m)) - 1;
+          m &= m - 1u;
+          int64_t c = -1;
+          if (lane == 0) {
+            const int64_t v = range_lo[rr] + atomicAdd(tile_ctr + rr, 1u);
+            c = (v < range_lo[rr + 1]) ? v : -1;
+          }
+          t = __shfl_sync(kFull, c, 0);
+        }
+      }
+      if (lane == 0) *claim = t;
+    }
+    __syncthreads();
+    const int64_t tile = *claim;
+    __syncthreads();
+    if (tile < 0) return;
+    if (threadIdx.x == 0) mine = claim_home();
+    if (!boxcar_tile<kSearch>(tile, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all, thrb_all,
+                              slots, dirty, counters, items, snaps, item_cap, tile_bins, buf_len))
+      return;
+    __syncthreads();   // the tile's shared memory is free for the next one
   }
 }
 
@@ -584,14 +666,28 @@ int prepare_bank(pulscan_plan p) {
   if (smem > 220 * 1024) return fail(PULSCAN_ERR_UNSUPPORTED, "z_max too large for the shared-memory tile");
   int rc = ensure_smem(boxcar_kernel<true>, smem, g_lim_search);
   if (!rc) rc = ensure_smem(boxcar_kernel<false>, smem, g_lim_dump);
-  return rc;
+  if (rc) return rc;
+  // persistent grid: as many CTAs as fit on the GPU at once
+  int b0 = 0, b1 = 0;
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, boxcar_kernel<true>, 32 * p->search_warps, smem));
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, boxcar_kernel<false>, 32 * p->search_warps, smem));
+  p->persist_grid[0] = b0 * p->n_ranges;
+  p->persist_grid[1] = b1 * p->n_ranges;
+  return PULSCAN_OK;
 }
 
 static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaStream_t s) {
   int buf_len = 0;
   const int smem = search_smem_bytes(p->z_max, p->search_warps, &buf_len);
   if (p->total_tiles > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many search tiles");
-  const dim3 grid(static_cast<unsigned>(p->total_tiles));
+  // persistent for grids of three or more full waves (claim counters zeroed
+  // by the caller); a smaller grid keeps one CTA per tile, since each SM
+  // needs all its resident warps busy for full issue and a persistent grid
+  // would run its last round with fewer CTAs per SM
+  const int pg0 = p->persist_grid[search ? 0 : 1];
+  const int pg = (pg0 > 0 && p->total_tiles >= 3LL * pg0) ? pg0 : 0;
+  uint32_t *ctr = pg > 0 ? p->d_counters + 4 : nullptr;
+  const dim3 grid(static_cast<unsigned>(pg > 0 ? std::min<int64_t>(p->total_tiles, pg) : p->total_tiles));
   const dim3 block(32 * p->search_warps);
   const int tile_bins = search_tile_bins(p->search_warps);
   const uint32_t cap = static_cast<uint32_t>(p->item_cap);
@@ -602,7 +698,7 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
     boxcar_kernel<true><<<grid, block, smem, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
         p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
-        tile_bins, buf_len);
+        tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges);
     PS_CUDA(cudaGetLastError());
     record(p, 5, s);
     record(p, 6, s);
@@ -620,7 +716,7 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
     boxcar_kernel<false><<<grid, block, smem, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
         p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, 0u,
-        tile_bins, buf_len);
+        tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges);
   }
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
@@ -641,7 +737,7 @@ int launch_segmax_raw(const float *d_power, const SeriesDev *d_series, const int
   if (rc) return rc;
   boxcar_kernel<false><<<static_cast<unsigned>(tiles), 32 * warps, smem, s>>>(
       d_power, d_series, d_tile_off, 1, W, seg_len, nullptr, nullptr, d_slots, nullptr, d_counters, nullptr,
-      nullptr, 0u, search_tile_bins(warps), buf_len);
+      nullptr, 0u, search_tile_bins(warps), buf_len, nullptr, nullptr, 1);
   PS_CUDA(cudaGetLastError());
   unpack_kernel<<<1024, 256, 0, s>>>(d_slots, n_slots, d_max, d_argmax);
   PS_CUDA(cudaGetLastError());
@@ -655,6 +751,7 @@ int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s) {
 int launch_segmax(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax, cudaStream_t s) {
   const int64_t n = p->total_seg * static_cast<int64_t>(p->z_max);
   PS_CUDA(cudaMemsetAsync(p->d_slots, 0, static_cast<size_t>(n) * sizeof(unsigned long long), s));
+  PS_CUDA(cudaMemsetAsync(p->d_counters + 4, 0, static_cast<size_t>(p->n_ranges) * sizeof(uint32_t), s));
   record(p, 10, s);
   int rc = launch_bank(p, d_power, false, s);
   if (rc) return rc;

@@ -127,7 +127,11 @@ struct pulscan_plan_s {
   float *d_stats = nullptr;        // 4 * total_seg
   unsigned long long *d_slots = nullptr;  // total_seg * z_max keys, 0 at rest
   uint32_t *d_dirty = nullptr;     // one bit per slot touched by the search, 0 at rest
-  uint32_t *d_counters = nullptr;  // [0] deferred items, [1] candidates, [2] error flags, [3] spare
+  uint32_t *d_counters = nullptr;  // [0] deferred items, [1] candidates, [2] error flags, [3] spare,
+                                   // [4, 4 + n_ranges) tile claim counters of the persistent bank
+  int n_ranges = 1;                // tile ranges of the persistent bank (one per SM)
+  int64_t *d_ranges = nullptr;     // their first tiles, n_ranges + 1 entries
+  int persist_grid[2] = {0, 0};    // persistent bank grid: [0] search, [1] maxima (0: one CTA per tile)
   unsigned long long *d_items = nullptr;  // deferred boxcar blocks
   float *d_snaps = nullptr;        // their running-sum snapshots (33 x 32 floats each)
   int64_t item_cap = 0;           // deferred items in use (<= alloc_item_cap)

@@ -113,7 +113,7 @@ static void free_plan(pulscan_plan p) {
   void *ptrs[] = {p->d_series, p->d_tile_off, p->d_seg_off, p->d_thresh, p->d_thresh_bound, p->d_ln_trials,
                   p->d_stats,  p->d_slots,    p->d_dirty,   p->d_counters, p->d_cands,     p->own_x,
                   p->own_spec, p->own_power, p->d_items, p->d_snaps,    p->d_gtab,     p->d_x_off,
-                  p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec};
+                  p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec,   p->d_ranges};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (auto &e : p->ev)
@@ -231,9 +231,10 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
       ok(dalloc(&p->d_thresh, ns * z_max)) && ok(dalloc(&p->d_thresh_bound, ns * z_max)) &&
       ok(dalloc(&p->d_ln_trials, ns)) && ok(dalloc(&p->d_stats, 4 * sg)) &&
       ok(dalloc(&p->d_slots, total_slots)) && ok(dalloc(&p->d_dirty, dirty_words)) &&
-      ok(dalloc(&p->d_counters, 4)) && ok(dalloc(&p->d_cands, p->max_cands)) &&
+      ok(dalloc(&p->d_counters, 4 + static_cast<size_t>(n_sm))) && ok(dalloc(&p->d_cands, p->max_cands)) &&
       ok(dalloc(&p->d_items, p->item_cap)) && ok(dalloc(&p->d_snaps, p->item_cap * kR * 32)) &&
-      ok(dalloc(&p->d_gtab, z_max)) && ok(dalloc(&p->d_x_off, ns)) && ok(dalloc(&p->d_x_len, ns))) {
+      ok(dalloc(&p->d_gtab, z_max)) && ok(dalloc(&p->d_x_off, ns)) && ok(dalloc(&p->d_x_len, ns)) &&
+      ok(dalloc(&p->d_ranges, static_cast<size_t>(n_sm) + 1))) {
     std::vector<SeriesDev> sd(ns);
     std::vector<int64_t> to(ns + 1), so(ns + 1);
     for (size_t i = 0; i < ns; ++i) {
@@ -256,7 +257,11 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
     ok(cuda_ok_or(cudaMemcpy(p->d_seg_off, so.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(cuda_ok_or(cudaMemset(p->d_slots, 0, total_slots * sizeof(unsigned long long))));
     ok(cuda_ok_or(cudaMemset(p->d_dirty, 0, dirty_words * sizeof(uint32_t))));
-    ok(cuda_ok_or(cudaMemset(p->d_counters, 0, 4 * sizeof(uint32_t))));
+    p->n_ranges = n_sm;
+    ok(cuda_ok_or(cudaMemset(p->d_counters, 0, (4 + static_cast<size_t>(n_sm)) * sizeof(uint32_t))));
+    std::vector<int64_t> rl(static_cast<size_t>(n_sm) + 1);
+    for (int r = 0; r <= n_sm; ++r) rl[r] = tl * r / n_sm;   // equal contiguous tile ranges, one per SM
+    ok(cuda_ok_or(cudaMemcpy(p->d_ranges, rl.data(), rl.size() * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(upload_thresholds(p));
     std::vector<float> gt(z_max);
     for (int w = 1; w <= z_max; ++w) gt[w - 1] = static_cast<float>(g_of(static_cast<double>(w)));
@@ -399,7 +404,7 @@ int pulscan_power_normalise(pulscan_plan p, const float *d_spec, float *d_power,
 }
 
 static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s) {
-  PS_CUDA(cudaMemsetAsync(p->d_counters, 0, 4 * sizeof(uint32_t), s));
+  PS_CUDA(cudaMemsetAsync(p->d_counters, 0, (4 + static_cast<size_t>(p->n_ranges)) * sizeof(uint32_t), s));
   record(p, 4, s);
   int rc = launch_search(p, d_power, s);   // records 5, 6, 7 around the deferred kernel
   if (rc) return rc;

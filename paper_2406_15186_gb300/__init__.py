@@ -210,15 +210,16 @@ class Plan:
         _check(load().pulscan_search(self._h, _ptr(d_x), _ptr(d_spec), _ptr(d_power), int(bool(use_graph)),
                                      _stream(stream)))
 
-    def search_host(self, h_x, use_graph=True, cap=4096, stream=None):
+    def search_host(self, h_x, use_graph=True, cap=None, stream=None):
         """Whole path from host memory (numpy array or pinned CPU tensor); returns candidates."""
         lib = load()
         n = ctypes.c_int64(0)
-        out = np.empty(int(cap), dtype=CAND_DTYPE)
-        rc = lib.pulscan_search_host(self._h, _ptr(h_x), out.ctypes.data, int(cap), ctypes.byref(n),
+        size = min(self.max_candidates, 1 << 16) if cap is None else int(cap)
+        out = np.empty(size, dtype=CAND_DTYPE)
+        rc = lib.pulscan_search_host(self._h, _ptr(h_x), out.ctypes.data, size, ctypes.byref(n),
                                      int(bool(use_graph)), _stream(stream))
-        if rc == -4 and n.value <= self.max_candidates:
-            return self.candidates(stream=stream)
+        if rc == -4 and cap is None and n.value <= self.max_candidates:
+            return self.candidates(cap=n.value, stream=stream)   # more than the first read held
         _check(rc)
         return out[: n.value]
 

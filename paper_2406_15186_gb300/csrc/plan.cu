@@ -434,19 +434,20 @@ int pulscan_candidates(pulscan_plan p, pulscan_cand *h_out, int64_t cap, int64_t
     PS_CUDA(cudaMemcpyAsync(tmp.data(), p->d_cands, have * sizeof(pulscan_cand), cudaMemcpyDeviceToHost, s));
     PS_CUDA(cudaStreamSynchronize(s));
   }
-  // order by (series, segment, width)
-  auto seg_of = [&](const pulscan_cand &c) {
+  // order by (series, segment, width): integer keys formed once per candidate
+  // ((series << 32 | segment), (width << 32 | index)); segments and widths
+  // are below 2^32, the index below 2^24
+  std::vector<std::pair<uint64_t, uint64_t>> key(static_cast<size_t>(have));
+  for (int64_t i = 0; i < have; ++i) {
+    const pulscan_cand &c = tmp[i];
     const Series &se = p->series[p->layout_of_user[c.series]];
-    return std::min<int64_t>(static_cast<int64_t>(c.bin) / p->seg_len, se.n_seg - 1);
-  };
-  std::sort(tmp.begin(), tmp.end(), [&](const pulscan_cand &a, const pulscan_cand &b) {
-    if (a.series != b.series) return a.series < b.series;
-    const int64_t sa = seg_of(a), sb = seg_of(b);
-    if (sa != sb) return sa < sb;
-    return a.width < b.width;
-  });
+    const int64_t seg = std::min<int64_t>(static_cast<int64_t>(c.bin) / p->seg_len, se.n_seg - 1);
+    key[i] = {(static_cast<uint64_t>(c.series) << 32) | static_cast<uint64_t>(seg),
+              (static_cast<uint64_t>(c.width) << 32) | static_cast<uint64_t>(i)};
+  }
+  std::sort(key.begin(), key.end());
   const int64_t ncopy = std::min<int64_t>(have, cap);
-  if (ncopy > 0) std::memcpy(h_out, tmp.data(), ncopy * sizeof(pulscan_cand));
+  for (int64_t i = 0; i < ncopy; ++i) h_out[i] = tmp[key[i].second & 0xffffffffull];
   if (ctr[2] & kErrTimeout) return fail(PULSCAN_ERR_TIMEOUT, "a bounded device wait timed out");
   if (count > cap || count > p->max_cands)
     return fail(PULSCAN_ERR_CAPACITY, "more candidates than the output capacity");

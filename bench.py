@@ -375,6 +375,24 @@ def run_ours(args, rank, world, local):
         ms = float(tt.item())
     value = world * m * w_max / (ms * 1e-3) / 1e9
 
+    # searched-width subsets (every width still summed): the same step with
+    # the z mod 8 and log2 z samplings
+    sampling = {}
+    for name, mode, stp in (("step8", 1, 8), ("log2", 2, 1)):
+        plan.set_widths(mode, stp)
+        step()
+        ts = []
+        for _ in range(max(3, args.steps // 2)):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            step()
+            t = plan.timings()
+            ts.append(t[2] + t[3] + t[4])
+        sampling[name] = {"search_ms": statistics.mean(ts), "candidates": len(plan.candidates(stream=stream))}
+    plan.set_widths(0, 1)
+    sampling["all"] = {"search_ms": statistics.mean(k_search) + statistics.mean(k_def) + statistics.mean(k_fin),
+                       "candidates": n_cands}
+
     # end to end through the host-buffer entry point (H2D of the series, D2H of candidates)
     plan.enable_timing(False)
     x_pin = torch.from_numpy(x).pin_memory()
@@ -420,6 +438,8 @@ def run_ours(args, rank, world, local):
                            "boxcar_search": statistics.mean(k_search), "deferred_blocks": statistics.mean(k_def),
                            "finalise": statistics.mean(k_fin)},
             "candidates": n_cands,
+            "width_sampling": dict(sampling, note="boxcar + deferred + finalise per step; all widths summed, "
+                                                  "only the sampled ones compared (z mod 8 == 0; z a power of two)"),
             "roofline": roofline,
             "e2e": {"value": world * m * w_max / (e2e_ms_mean * 1e-3) / 1e9, "unit": UNIT,
                     "ms_per_step": e2e_ms_mean, "h2d_bytes_per_step": 4 * n,

@@ -113,8 +113,33 @@ PULSCAN_API int pulscan_plan_offsets(pulscan_plan plan, int64_t *h_x_off, int64_
                          int64_t *h_power_off, int64_t *h_seg_off);
 
 /* Override the Bonferroni trial count of every series (n_trials >= 1; 1 turns
- * the correction off) and recompute the threshold table. Host-synchronous. */
+ * the correction off) and recompute the threshold table. Host-synchronous.
+ * The count then stays fixed when the searched widths change. */
 PULSCAN_API int pulscan_plan_set_trials(pulscan_plan plan, double n_trials);
+
+/* Which widths are searched for candidates (the user-selected step of §2.2.3
+ * and Algorithm 4's "z mod z_step = 0" test; the logarithmic z sampling of
+ * §4.1.4 that the GPU version searches).  Every width 1..z_max is still
+ * summed -- the recursion of §2.2.5 needs them all -- but only searched
+ * widths are compared with a threshold and reported; the others get
+ * T_w = +inf.  With z = w - 1:
+ *   PULSCAN_WIDTHS_ALL  (0): every width (the default);
+ *   PULSCAN_WIDTHS_STEP (1): widths with z mod step == 0, i.e. w = 1, 1 + step, ...;
+ *   PULSCAN_WIDTHS_LOG2 (2): widths with z a power of two, i.e. w = 2, 3, 5, 9, ...
+ * Unless pulscan_plan_set_trials fixed it, the Bonferroni count becomes
+ * M x (number of searched widths) per series.  Host-synchronous.
+ * Errors: INVALID_ARG (unknown mode, step < 1, or no width searched). */
+#define PULSCAN_WIDTHS_ALL 0
+#define PULSCAN_WIDTHS_STEP 1
+#define PULSCAN_WIDTHS_LOG2 2
+PULSCAN_API int pulscan_plan_set_widths(pulscan_plan plan, int32_t mode, int32_t step);
+
+/* Approximate r-bin output (§2.4, "Pulscan R-Block"): with block_width > 0,
+ * pulscan_candidates / pulscan_search_host report in `bin` the block index
+ * floor(k / block_width) of each candidate instead of its start bin k (the
+ * paper's default block width is 32768); 0 restores exact bins.  The order
+ * of the records is unchanged.  Errors: INVALID_ARG (block_width < 0). */
+PULSCAN_API int pulscan_plan_set_rblock(pulscan_plan plan, int64_t block_width);
 
 /* Copy the FP32 power threshold T_w of series `series` (w = 1..z_max) to
  * h_thresh[0..z_max-1]: the smallest float S with sigma(S) >= threshold_sigma.

@@ -49,6 +49,8 @@ _SIGS = {
     "pulscan_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(_Info)]),
     "pulscan_plan_offsets": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, _I64P]),
     "pulscan_plan_set_trials": (ctypes.c_int, [_P, ctypes.c_double]),
+    "pulscan_plan_set_widths": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "pulscan_plan_set_rblock": (ctypes.c_int, [_P, ctypes.c_int64]),
     "pulscan_plan_thresholds": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pulscan_rfft": (ctypes.c_int, [_P, _P, _P, _P]),
     "pulscan_power_normalise": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -121,6 +123,9 @@ def _stream(stream):
     return stream.cuda_stream
 
 
+WIDTHS_ALL, WIDTHS_STEP, WIDTHS_LOG2 = 0, 1, 2
+
+
 class Plan:
     """A search plan: one series (``n``) or a batch (``lengths``)."""
 
@@ -174,6 +179,14 @@ class Plan:
 
     def set_trials(self, n_trials):
         _check(load().pulscan_plan_set_trials(self._h, float(n_trials)))
+
+    def set_widths(self, mode=0, step=1):
+        """Searched widths: WIDTHS_ALL, WIDTHS_STEP (z mod step == 0) or WIDTHS_LOG2 (z a power of two)."""
+        _check(load().pulscan_plan_set_widths(self._h, int(mode), int(step)))
+
+    def set_rblock(self, block_width):
+        """Report block indices floor(bin / block_width) instead of bins (0: exact bins)."""
+        _check(load().pulscan_plan_set_rblock(self._h, int(block_width)))
 
     # -- the path
     def rfft(self, d_x, d_spec, stream=None):

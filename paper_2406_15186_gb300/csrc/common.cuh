@@ -111,6 +111,9 @@ struct pulscan_plan_s {
   std::vector<ps::Series> series;
   std::vector<ps::FftClass> fft;
   std::vector<double> n_trials;     // per series (layout order)
+  std::vector<uint8_t> searched;    // per width: compared and reported (1) or only summed (0)
+  bool trials_fixed = false;        // n_trials set by the caller (kept when the widths change)
+  int64_t rblock = 0;               // > 0: candidates report floor(bin / rblock)
   std::vector<int> layout_of_user;  // user series index -> layout index
   std::vector<float> h_thresh;      // n_series * z_max, layout order
   int64_t x_floats = 0, spec_bins = 0, p_floats = 0, total_seg = 0, total_tiles = 0;

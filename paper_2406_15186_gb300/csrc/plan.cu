@@ -75,7 +75,7 @@ static void compute_thresholds(pulscan_plan p) {
     if (it == cache.end()) {
       std::vector<float> t(W);
       const double y = lsf - std::log(nt);
-      for (int w = 1; w <= W; ++w) t[w - 1] = threshold_for(w, y);
+      for (int w = 1; w <= W; ++w) t[w - 1] = p->searched[w - 1] ? threshold_for(w, y) : INFINITY;
       it = cache.emplace(nt, std::move(t)).first;
     }
     std::copy(it->second.begin(), it->second.end(), p->h_thresh.begin() + i * W);
@@ -218,6 +218,7 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
   p->item_cap = std::min<int64_t>(total_warps * nb, std::min<int64_t>(std::max<int64_t>(total_warps, 8192), 65536));
   p->alloc_item_cap = p->item_cap;
   p->defer_grid = 4 * n_sm;   // 4-warp CTAs, one item each at a time: 16 warps per SM
+  p->searched.assign(z_max, 1);
   for (auto &s : p->series) p->n_trials.push_back(static_cast<double>(s.m) * z_max);
   compute_thresholds(p);
 
@@ -362,8 +363,38 @@ int pulscan_plan_set_trials(pulscan_plan p, double n_trials) {
   if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
   if (!(n_trials >= 1.0) || !std::isfinite(n_trials)) return fail(PULSCAN_ERR_INVALID_ARG, "n_trials must be >= 1");
   for (auto &t : p->n_trials) t = n_trials;
+  p->trials_fixed = true;
   compute_thresholds(p);
   return upload_thresholds(p);
+}
+
+int pulscan_plan_set_widths(pulscan_plan p, int32_t mode, int32_t step) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  if (mode != PULSCAN_WIDTHS_ALL && mode != PULSCAN_WIDTHS_STEP && mode != PULSCAN_WIDTHS_LOG2)
+    return fail(PULSCAN_ERR_INVALID_ARG, "unknown width mode");
+  if (mode == PULSCAN_WIDTHS_STEP && step < 1) return fail(PULSCAN_ERR_INVALID_ARG, "step must be >= 1");
+  std::vector<uint8_t> sel(p->z_max, 0);
+  int64_t n_sel = 0;
+  for (int w = 1; w <= p->z_max; ++w) {
+    const int z = w - 1;
+    bool on = true;
+    if (mode == PULSCAN_WIDTHS_STEP) on = (z % step) == 0;
+    if (mode == PULSCAN_WIDTHS_LOG2) on = z > 0 && (z & (z - 1)) == 0;
+    sel[w - 1] = on ? 1 : 0;
+    n_sel += on ? 1 : 0;
+  }
+  if (n_sel == 0) return fail(PULSCAN_ERR_INVALID_ARG, "no width searched");
+  p->searched = sel;
+  if (!p->trials_fixed)
+    for (size_t i = 0; i < p->series.size(); ++i) p->n_trials[i] = static_cast<double>(p->series[i].m) * n_sel;
+  compute_thresholds(p);
+  return upload_thresholds(p);
+}
+
+int pulscan_plan_set_rblock(pulscan_plan p, int64_t block_width) {
+  if (!p || block_width < 0) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
+  p->rblock = block_width;
+  return PULSCAN_OK;
 }
 
 int pulscan_plan_thresholds(pulscan_plan p, int32_t series, float *h_thresh) {
@@ -447,7 +478,10 @@ int pulscan_candidates(pulscan_plan p, pulscan_cand *h_out, int64_t cap, int64_t
   }
   std::sort(key.begin(), key.end());
   const int64_t ncopy = std::min<int64_t>(have, cap);
-  for (int64_t i = 0; i < ncopy; ++i) h_out[i] = tmp[key[i].second & 0xffffffffull];
+  for (int64_t i = 0; i < ncopy; ++i) {
+    h_out[i] = tmp[key[i].second & 0xffffffffull];
+    if (p->rblock > 0) h_out[i].bin /= static_cast<uint64_t>(p->rblock);   // R-Block: the block index
+  }
   if (ctr[2] & kErrTimeout) return fail(PULSCAN_ERR_TIMEOUT, "a bounded device wait timed out");
   if (count > cap || count > p->max_cands)
     return fail(PULSCAN_ERR_CAPACITY, "more candidates than the output capacity");

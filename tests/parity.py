@@ -93,12 +93,13 @@ def check_maxima(p64, mx_gpu, am_gpu, w_max, seg_len, seg_range=None):
     return mx_ref, am_ref
 
 
-def oracle_decisions(mx_ref, n_trials, sigma_thr):
-    """(passes, ambiguous) per (segment, width) from the oracle maxima."""
+def oracle_decisions(mx_ref, n_trials, sigma_thr, widths=None):
+    """(passes, ambiguous) per (segment, width) from the oracle maxima; only
+    searched widths (all when widths is None) can pass."""
     n_seg, w_max = mx_ref.shape
     dec = np.zeros(mx_ref.shape, dtype=bool)
     amb = np.zeros(mx_ref.shape, dtype=bool)
-    for wi in range(w_max):
+    for wi in (range(w_max) if widths is None else [w - 1 for w in widths]):
         col = mx_ref[:, wi]
         ok = ~np.isnan(col)
         if not ok.any():
@@ -112,11 +113,12 @@ def oracle_decisions(mx_ref, n_trials, sigma_thr):
     return dec, amb
 
 
-def check_candidates(cands, p64, mx_ref, am_ref, w_max, seg_len, sigma_thr, n_trials, series=0, seg_rows=None):
+def check_candidates(cands, p64, mx_ref, am_ref, w_max, seg_len, sigma_thr, n_trials, series=0, seg_rows=None,
+                     widths=None):
     """Candidate set of one series vs the oracle decisions on its maxima."""
     m = len(p64)
     n_seg = mx_ref.shape[0]
-    dec, amb = oracle_decisions(mx_ref, n_trials, sigma_thr)
+    dec, amb = oracle_decisions(mx_ref, n_trials, sigma_thr, widths)
     if seg_rows is not None:
         keep = np.zeros(n_seg, dtype=bool)
         keep[seg_rows[0]:seg_rows[1]] = True

@@ -186,3 +186,38 @@ def test_plans_of_different_sizes_coexist(pkg):
     a = np.sort(first["cands"], order=["series", "bin", "width"])
     b = np.sort(again["cands"], order=["series", "bin", "width"])
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode,step", [(1, 3), (1, 7), (2, 1)])
+def test_searched_width_subsets(pkg, mode, step):
+    """Width sampling: only the searched widths are compared and reported, with
+    the Bonferroni count over the searched widths (all widths still summed)."""
+    n, w_max, seg_len, sigma = 1 << 16, 70, 512, 2.0
+    x = _series(n, seed=9)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    plan.set_widths(mode, step)
+    out = parity.run_gpu(plan, x)
+    m = n // 2 + 1
+    ws = opipe.searched_widths(w_max, {1: "step", 2: "log2"}[mode], step)
+    t = plan.thresholds()
+    assert np.all(np.isinf(np.delete(t, np.array(ws) - 1))) and np.all(np.isfinite(t[np.array(ws) - 1]))
+    p64 = out["power"][:m].astype(np.float64)
+    mx_ref, am_ref = parity.check_maxima(p64, out["mx"], out["am"], w_max, seg_len)
+    k = parity.check_candidates(out["cands"], p64, mx_ref, am_ref, w_max, seg_len, sigma,
+                                opipe.n_trials_default(m, w_max, ws), widths=ws)
+    assert k >= 10
+    assert set(int(w) for w in out["cands"]["width"]) <= set(ws)
+
+
+def test_rblock_reports_block_index(pkg):
+    n, w_max, seg_len, sigma = 1 << 16, 48, 512, 2.0
+    x = _series(n, seed=10)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    plan.set_trials(1.0)
+    exact = parity.run_gpu(plan, x)["cands"]
+    plan.set_rblock(1000)
+    approx = parity.run_gpu(plan, x)["cands"]
+    assert len(exact) == len(approx) > 100
+    assert np.array_equal(approx["bin"], exact["bin"] // 1000)
+    for f in ("series", "width", "power", "sigma"):
+        assert np.array_equal(approx[f], exact[f])

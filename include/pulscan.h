@@ -54,17 +54,21 @@ typedef struct pulscan_plan_s *pulscan_plan;
 #define PULSCAN_ERR_TIMEOUT (-5)     /* a bounded device wait gave up           */
 #define PULSCAN_ERR_UNSUPPORTED (-6) /* valid request this build cannot serve   */
 
-/* One candidate: the maximum boxcar power of one (series, segment, width) that
- * passes the sigma threshold (Algorithm 4 keeps one per chunk and width).
- * `bin` is the window's first bin k within its series (the centre is
- * k + (width - 1)/2); `power` is S_w[k] in FP32; `sigma` is the
- * Bonferroni-corrected Gaussian-equivalent significance (§2.2.3).  24 bytes. */
+/* One candidate: the maximum boxcar power of one (series, harmonic stage,
+ * segment, width) that passes the sigma threshold (Algorithm 4 keeps one per
+ * chunk and width).  `bin` is the window's first bin k within its (stage)
+ * spectrum (the centre is k + (width - 1)/2); `power` is S_w[k] in FP32;
+ * `sigma` is the Bonferroni-corrected Gaussian-equivalent significance
+ * (§2.2.3); `harmonics` is the number H of harmonics summed (§2.3; 1 without
+ * harmonic summing).  32 bytes. */
 typedef struct {
   uint32_t series;
   uint32_t width;
   uint64_t bin;
   float power;
   float sigma;
+  uint32_t harmonics;
+  uint32_t reserved;
 } pulscan_cand;
 
 /* Sizes of the caller-owned buffers of a plan.  All counts are elements. */
@@ -98,6 +102,26 @@ PULSCAN_API int pulscan_plan_create(pulscan_plan *out, int64_t n, int32_t z_max,
 PULSCAN_API int pulscan_plan_create_batch(pulscan_plan *out, const int64_t *h_lengths, int32_t n_series,
                               int32_t z_max, int32_t segment_len, double threshold_sigma);
 
+/* As pulscan_plan_create_batch, plus harmonic summing (§2.3, the GPU
+ * decimation listing): for H = 2..numharm the normalised power of every
+ * series is decimated by summing adjacent non-overlapping groups of h bins,
+ * h = 1..H, aligned at bin 0 and added,
+ *   X_H[r] = sum_{h=1}^{H} sum_{j=0}^{h-1} P[h r + j],  r < floor(M / H),
+ * which is chi^2 with H(H+1) degrees of freedom per bin for noise; each X_H
+ * is searched like the power itself (same widths, segment length and sigma
+ * threshold) with a width-w sum distributed as chi^2 with H(H+1) w degrees of
+ * freedom, and its own Bonferroni count floor(M / H) x (searched widths).
+ * The stage spectra sit in the power buffer after the series' powers
+ * (power_floats covers them); the segments of all stages are counted in
+ * total_segments (stages after the series, in the same series order);
+ * candidates carry H in `harmonics`.  numharm = 1 is pulscan_plan_create_batch.
+ * Extra validation (INVALID_ARG): 1 <= numharm <= 8 and
+ * segment_len <= floor(M / numharm) for every series.  The logsumexp entry
+ * points return PULSCAN_ERR_UNSUPPORTED on such a plan. */
+PULSCAN_API int pulscan_plan_create_harmonic(pulscan_plan *out, const int64_t *h_lengths, int32_t n_series,
+                                             int32_t z_max, int32_t segment_len, double threshold_sigma,
+                                             int32_t numharm);
+
 /* Destroy a plan and free its scratch (after the plan's last stream work). */
 PULSCAN_API void pulscan_plan_destroy(pulscan_plan plan);
 
@@ -111,6 +135,14 @@ PULSCAN_API int pulscan_plan_get_info(pulscan_plan plan, pulscan_plan_info *h_in
  * i's extent (spectrum/power extents include alignment padding). */
 PULSCAN_API int pulscan_plan_offsets(pulscan_plan plan, int64_t *h_x_off, int64_t *h_spec_off,
                          int64_t *h_power_off, int64_t *h_seg_off);
+
+/* Where harmonic stage H (1..numharm; 1 = the series' own power) of every
+ * series lives: h_power_off[i] (floats of the power buffer), h_seg_off[i]
+ * (first global segment) and h_bins[i] (floor(M_i / H) bins) for series i in
+ * the caller's order, each a host array of n_series + 1 entries or NULL;
+ * entry n_series is the end of the stage (0 for h_bins).  Errors: INVALID_ARG. */
+PULSCAN_API int pulscan_plan_stage_offsets(pulscan_plan plan, int32_t harmonics, int64_t *h_power_off,
+                                           int64_t *h_seg_off, int64_t *h_bins);
 
 /* Override the Bonferroni trial count of every series (n_trials >= 1; 1 turns
  * the correction off) and recompute the threshold table. Host-synchronous.
@@ -155,7 +187,9 @@ PULSCAN_API int pulscan_rfft(pulscan_plan plan, const float *d_x, float *d_spec,
  * bin taken as 0), a = (Re - med)/(kappa MAD), kappa = 1/Phi^{-1}(3/4),
  * P = (a^2 + b^2)/2.  d_spec float[spec_floats] -> d_power float[power_floats].
  * d_stats (nullable) receives float[4 * total_segments]: per segment
- * (med_re, mad_re, med_im, mad_im).  A segment with MAD = 0 gets P = 0. */
+ * (med_re, mad_re, med_im, mad_im).  A segment with MAD = 0 gets P = 0.
+ * On a harmonic plan the call also writes the stage spectra X_H into
+ * d_power (their d_stats rows are left untouched). */
 PULSCAN_API int pulscan_power_normalise(pulscan_plan plan, const float *d_spec, float *d_power, float *d_stats,
                             pulscan_stream stream);
 
@@ -256,8 +290,8 @@ PULSCAN_API int pulscan_amplitude_grad(pulscan_plan plan, const float *d_gx, con
 /* Per-kernel timing with CUDA events on the launch stream: enable (on != 0)
  * or disable recording; pulscan_plan_timings then writes the milliseconds of
  * the most recent launch of [rfft, normalise, boxcar search kernel,
- * deferred-block kernel, candidate finalise, segment-maxima kernel] (-1
- * where not run) to h_ms[0..min(n,6)-1].  Synchronises the events. */
+ * deferred-block kernel, candidate finalise, segment-maxima kernel, harmonic
+ * sums] (-1 where not run) to h_ms[0..min(n,7)-1].  Synchronises the events. */
 PULSCAN_API int pulscan_plan_enable_timing(pulscan_plan plan, int on);
 PULSCAN_API int pulscan_plan_timings(pulscan_plan plan, float *h_ms, int32_t n);
 
@@ -268,8 +302,10 @@ PULSCAN_API int pulscan_plan_timings(pulscan_plan plan, float *h_ms, int32_t n);
  * inside the main kernel instead (same results, slower). */
 PULSCAN_API int pulscan_plan_counters(pulscan_plan plan, int64_t *h_out, int32_t n);
 
-/* Limit the deferred-block list to cap items (0 = every flagged block is
- * run exactly by its own warp); cap is clipped to the allocated capacity. */
+/* Set the deferred-block list to cap items (0 = every flagged block is run
+ * exactly by its own warp; at most 2^24).  A cap above the allocated one
+ * reallocates the list (4.2 KB per item; synchronises the device and drops
+ * the plan's captured graph).  Errors: INVALID_ARG, NOMEM. */
 PULSCAN_API int pulscan_plan_set_defer_capacity(pulscan_plan plan, int64_t cap);
 
 /* Message of the last error on this thread ("" if none). */

@@ -7,7 +7,8 @@ restatement of what the accelerated path computes, written from the paper:
 * ``normalise``    -- per-block median / MAD normalisation and power (§2.2.3, Eq. 8)
 * ``boxcar``       -- recursive boxcar bank and per-segment maxima (§2.2.5, Algorithm 4)
 * ``significance`` -- chi-square survival, Bonferroni, Gaussian sigma (§2.2.3, Eq. 9)
-* ``pipeline``     -- the end-to-end search in the paper's order
+* ``pipeline``     -- the end-to-end search in the paper's order (width sampling, R-Block)
+* ``harmonic``     -- harmonic summing by decimation and its search (§2.3)
 * ``lse``          -- logsumexp relaxation of the segment maximum and its adjoint
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline and

@@ -39,12 +39,14 @@ def n_trials_default(m, w_max, widths=None):
     return float(m) * float(w_max if widths is None else len(widths))
 
 
-def candidates_from_maxima(mx, am, w_max, n_trials, sigma_thr, widths=None, rblock=0):
+def candidates_from_maxima(mx, am, w_max, n_trials, sigma_thr, widths=None, rblock=0, shape_mult=1):
     """Candidate records from per-(segment, width) maxima.
 
     Returns a list of dicts ordered by (segment, width), one per (s, w) with w
     searched whose maximum passes the sigma threshold.  rblock > 0 reports the
     block index bin // rblock instead of the bin (§2.4, "R-Block").
+    shape_mult: gamma shape per unit width of the searched spectrum (1 for the
+    power; H(H+1)/2 for an H-harmonic sum, §2.3).
     """
     out = []
     for w in (range(1, w_max + 1) if widths is None else widths):
@@ -54,7 +56,7 @@ def candidates_from_maxima(mx, am, w_max, n_trials, sigma_thr, widths=None, rblo
             continue
         segs = np.nonzero(ok)[0]
         pw = col[segs]
-        lp = significance.log_p_adjusted(w, pw, n_trials)
+        lp = significance.log_p_adjusted(shape_mult * w, pw, n_trials)
         keep = lp <= significance.log_sf_normal(sigma_thr)
         if not keep.any():
             continue

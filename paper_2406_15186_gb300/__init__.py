@@ -16,8 +16,9 @@ __all__ = ["Plan", "PulscanError", "load", "lib_path", "CAND_DTYPE"]
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
 
-CAND_DTYPE = np.dtype([("series", "<u4"), ("width", "<u4"), ("bin", "<u8"), ("power", "<f4"), ("sigma", "<f4")])
-assert CAND_DTYPE.itemsize == 24
+CAND_DTYPE = np.dtype([("series", "<u4"), ("width", "<u4"), ("bin", "<u8"), ("power", "<f4"), ("sigma", "<f4"),
+                       ("harmonics", "<u4"), ("reserved", "<u4")])
+assert CAND_DTYPE.itemsize == 32
 
 
 class PulscanError(RuntimeError):
@@ -48,6 +49,9 @@ _SIGS = {
     "pulscan_plan_destroy": (None, [_P]),
     "pulscan_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(_Info)]),
     "pulscan_plan_offsets": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, _I64P]),
+    "pulscan_plan_create_harmonic": (ctypes.c_int, [ctypes.POINTER(_P), _I64P, ctypes.c_int32, ctypes.c_int32,
+                                                    ctypes.c_int32, ctypes.c_double, ctypes.c_int32]),
+    "pulscan_plan_stage_offsets": (ctypes.c_int, [_P, ctypes.c_int32, _I64P, _I64P, _I64P]),
     "pulscan_plan_set_trials": (ctypes.c_int, [_P, ctypes.c_double]),
     "pulscan_plan_set_widths": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "pulscan_plan_set_rblock": (ctypes.c_int, [_P, ctypes.c_int64]),
@@ -129,16 +133,22 @@ WIDTHS_ALL, WIDTHS_STEP, WIDTHS_LOG2 = 0, 1, 2
 class Plan:
     """A search plan: one series (``n``) or a batch (``lengths``)."""
 
-    def __init__(self, n=None, z_max=256, segment_len=1024, threshold_sigma=6.0, lengths=None):
+    def __init__(self, n=None, z_max=256, segment_len=1024, threshold_sigma=6.0, lengths=None, numharm=1):
         lib = load()
         h = _P()
-        if lengths is None:
+        if numharm != 1:
+            ls = [int(n)] if lengths is None else [int(v) for v in lengths]
+            arr = (ctypes.c_int64 * len(ls))(*ls)
+            _check(lib.pulscan_plan_create_harmonic(ctypes.byref(h), arr, len(ls), int(z_max), int(segment_len),
+                                                    float(threshold_sigma), int(numharm)))
+        elif lengths is None:
             _check(lib.pulscan_plan_create(ctypes.byref(h), int(n), int(z_max), int(segment_len),
                                            float(threshold_sigma)))
         else:
             arr = (ctypes.c_int64 * len(lengths))(*[int(v) for v in lengths])
             _check(lib.pulscan_plan_create_batch(ctypes.byref(h), arr, len(lengths), int(z_max),
                                                  int(segment_len), float(threshold_sigma)))
+        self.numharm = int(numharm)
         self._h = h
         info = _Info()
         _check(lib.pulscan_plan_get_info(h, ctypes.byref(info)))
@@ -241,10 +251,20 @@ class Plan:
         _check(load().pulscan_plan_enable_timing(self._h, int(bool(on))))
 
     def timings(self):
-        """ms of the last [rfft, normalise, boxcar kernel, deferred blocks, finalise, segment maxima] (-1: not run)."""
-        out = (ctypes.c_float * 6)()
-        _check(load().pulscan_plan_timings(self._h, out, 6))
+        """ms of the last [rfft, normalise, boxcar kernel, deferred blocks, finalise, segment maxima,
+        harmonic sums] (-1: not run)."""
+        out = (ctypes.c_float * 7)()
+        _check(load().pulscan_plan_timings(self._h, out, 7))
         return list(out)
+
+    def stage_offsets(self, harmonics):
+        """(power offsets, first segments, bins) of harmonic stage H per series (entry n_series: the end)."""
+        po = np.zeros(self.n_series + 1, dtype=np.int64)
+        so = np.zeros(self.n_series + 1, dtype=np.int64)
+        nb = np.zeros(self.n_series + 1, dtype=np.int64)
+        _check(load().pulscan_plan_stage_offsets(self._h, int(harmonics), po.ctypes.data_as(_I64P),
+                                                 so.ctypes.data_as(_I64P), nb.ctypes.data_as(_I64P)))
+        return po, so, nb
 
     def counters(self):
         """[deferred blocks, deferred capacity, candidates, candidate capacity] of the last search."""

@@ -73,6 +73,7 @@ struct Series {
   int64_t seg_off;    // first global segment
   int64_t tile_off;   // first global search tile
   uint32_t user_index;
+  uint32_t harm = 1;  // harmonics summed (1: the series' own power; H >= 2: a stage spectrum, n = 0)
 };
 
 // device-side view of one series (what the kernels need)
@@ -84,7 +85,7 @@ struct SeriesDev {
   int64_t seg_off;
   int64_t tile_off;
   uint32_t user_index;
-  uint32_t pad_;
+  uint32_t harm;      // harmonics summed: a width-w sum has gamma shape H(H+1)/2 * w
 };
 
 struct FftClass {
@@ -108,7 +109,10 @@ struct pulscan_plan_s {
   int32_t z_max = 0;
   int32_t seg_len = 0;
   double sigma_thr = 0.0;
-  std::vector<ps::Series> series;
+  std::vector<ps::Series> series;   // the series (layout order), then their harmonic stages
+  int32_t numharm = 1;              // harmonics summed up to (1: none)
+  int64_t n_base = 0;               // entries of `series` that are series (the rest are stages)
+  int64_t base_seg = 0;             // segments of those (normalised); stage segments follow
   std::vector<ps::FftClass> fft;
   std::vector<double> n_trials;     // per series (layout order)
   std::vector<uint8_t> searched;    // per width: compared and reported (1) or only summed (0)
@@ -126,7 +130,7 @@ struct pulscan_plan_s {
   float *d_thresh = nullptr;       // n_series * z_max
   float *d_thresh_bound = nullptr; // same, scaled down slightly for bound checks
   double *d_ln_trials = nullptr;   // ln(n_trials) per series
-  float *d_gtab = nullptr;         // g(w) = w ln w - w - ln Gamma(w), w = 1..z_max
+  float *d_gtab = nullptr;         // g(a) = a ln a - a - ln Gamma(a), a = H(H+1)/2 w: [H - 1][w - 1]
   float *d_stats = nullptr;        // 4 * total_seg
   unsigned long long *d_slots = nullptr;  // total_seg * z_max keys, 0 at rest
   uint32_t *d_dirty = nullptr;     // one bit per slot touched by the search, 0 at rest
@@ -151,8 +155,8 @@ struct pulscan_plan_s {
   std::vector<ps::FftClass> ifft;  // C2R plans per length class
   // timing
   bool timing = false;
-  cudaEvent_t ev[12] = {};
-  bool ran[6] = {};
+  cudaEvent_t ev[14] = {};
+  bool ran[7] = {};
   ps::GraphCache graph;
 };
 
@@ -166,6 +170,7 @@ int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, fl
                          cudaStream_t s);
 int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s);
 int launch_finalize(pulscan_plan p, cudaStream_t s);
+int launch_harmonic_sums(pulscan_plan p, float *d_power, cudaStream_t s);   // stage spectra X_H
 int launch_segmax(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax,
                   cudaStream_t s);
 void record(pulscan_plan p, int idx, cudaStream_t s);  // timing event helper

@@ -7,7 +7,8 @@
 // bit in a dirty bitmap.  This kernel scans the bitmap (one word per warp,
 // one slot per lane, grid-stride), visits the slots whose bits are set, converts each to a
 // record, computes
-// ln p = ln Q(w, S) + ln n_trials (Bonferroni, capped at 0) and the
+// ln p = ln Q(a, S) + ln n_trials (Bonferroni, capped at 0; a = w, or
+// H(H+1)/2 w for the H-harmonic sum of §2.3) and the
 // Gaussian-equivalent sigma (FP32, cancellation-free form, see signif.cuh),
 // appends the record, and clears the slot
 // and the bitmap word so both are zero again for the next search.
@@ -54,7 +55,10 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t
     }
     const float pw = __uint_as_float(static_cast<uint32_t>(key >> 32));
     const uint32_t bin = 0xffffffffu - static_cast<uint32_t>(key & 0xffffffffull);
-    const float lp = fminf(0.0f, log_q_f32(static_cast<float>(w), pw, gtab[w - 1]) +
+    // gamma shape of a width-w sum: w, or H(H+1)/2 w for harmonic stage H
+    const uint32_t hh = series[lo].harm;
+    const float a = static_cast<float>(hh * (hh + 1) / 2) * static_cast<float>(w);
+    const float lp = fminf(0.0f, log_q_f32(a, pw, gtab[(hh - 1) * static_cast<uint32_t>(W) + (w - 1)]) +
                                      static_cast<float>(ln_trials[lo]));
     const float sg = sigma_from_log_p_f32(lp);
     const uint32_t o = base + static_cast<uint32_t>(__popc(act & ((1u << lane) - 1u)));
@@ -65,6 +69,8 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t
       c.bin = bin;
       c.power = pw;
       c.sigma = sg;
+      c.harmonics = hh;
+      c.reserved = 0u;
       cands[o] = c;
     }
   }

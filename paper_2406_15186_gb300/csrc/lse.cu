@@ -610,6 +610,7 @@ int lse_buf_len(pulscan_plan p, int warps) {
 SmemLimit g_lim_fwd, g_lim_bwd;
 
 int lse_prepare(pulscan_plan p) {
+  if (p->numharm > 1) return fail(PULSCAN_ERR_UNSUPPORTED, "logsumexp path on a harmonic plan");
   if (lse_warps(p) > kLseMaxWarps)
     return fail(PULSCAN_ERR_UNSUPPORTED, "logsumexp path needs segments of at most 4224 bins");
   return PULSCAN_OK;
@@ -683,9 +684,9 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   if (!p || !d_spec || !d_power || !d_stats || !d_sel || !d_y || !d_gy || !d_gx)
     return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   if (!(tau > 0.0f) || !std::isfinite(tau)) return fail(PULSCAN_ERR_INVALID_ARG, "tau must be finite and > 0");
-  if (lse_warps(p) > kLseMaxWarps)
-    return fail(PULSCAN_ERR_UNSUPPORTED, "logsumexp path needs segments of at most 4224 bins");
-  int rc = lse_backward_buffers(p);
+  int rc = lse_prepare(p);
+  if (rc) return rc;
+  rc = lse_backward_buffers(p);
   if (rc) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int warps = lse_warps(p);
@@ -719,7 +720,7 @@ int pulscan_inject(pulscan_plan p, const float *d_noise, const float *d_template
                    pulscan_stream stream) {
   if (!p || !d_noise || !d_template || !d_amp || !d_x) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int ns = static_cast<int>(p->series.size());
+  const int ns = static_cast<int>(p->n_base);
   if (ns > 65535) return fail(PULSCAN_ERR_UNSUPPORTED, "too many series for one launch");
   inject_kernel<<<dim3(64, ns), 256, 0, s>>>(d_noise, d_template, d_amp, p->d_series, p->d_x_off, p->d_x_len, ns,
                                              d_x);
@@ -731,7 +732,7 @@ int pulscan_amplitude_grad(pulscan_plan p, const float *d_gx, const float *d_tem
                            pulscan_stream stream) {
   if (!p || !d_gx || !d_template || !d_gamp) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int ns = static_cast<int>(p->series.size());
+  const int ns = static_cast<int>(p->n_base);
   amp_grad_kernel<<<ns, 512, 0, s>>>(d_gx, d_template, p->d_series, p->d_x_off, p->d_x_len, ns, d_gamp);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;

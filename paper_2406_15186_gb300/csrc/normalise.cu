@@ -811,7 +811,10 @@ constexpr int kRegK[] = {1, 2, 3, 4, 5, 6, 8, 9, 12, 16, 17, 24, 32};
 
 int reg_bins_per_thread(pulscan_plan p) {
   int64_t max_n = 0;
-  for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
+  for (int64_t i = 0; i < p->n_base; ++i) {
+    const auto &se = p->series[i];
+    max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
+  }
   for (int k : kRegK)
     if (max_n <= static_cast<int64_t>(k) * kNormThreads) return k;
   return 0;
@@ -819,14 +822,15 @@ int reg_bins_per_thread(pulscan_plan p) {
 
 template <int K>
 void launch_reg(pulscan_plan p, const float *d_spec, float *d_power, float4 *st4, float *d_sel, cudaStream_t s) {
-  normalise_reg_kernel<K><<<static_cast<unsigned>(p->total_seg), kNormThreads, sizeof(SelShared), s>>>(
+  normalise_reg_kernel<K><<<static_cast<unsigned>(p->base_seg), kNormThreads, sizeof(SelShared), s>>>(
       reinterpret_cast<const float2 *>(d_spec), d_power, st4, p->d_series, p->d_seg_off,
-      static_cast<int>(p->series.size()), p->seg_len, d_sel);
+      static_cast<int>(p->n_base), p->seg_len, d_sel);
 }
 
 int normalise_smem(pulscan_plan p, int *bins_out) {
   int64_t max_n = 0;
-  for (const auto &se : p->series) {
+  for (int64_t i = 0; i < p->n_base; ++i) {
+    const auto &se = p->series[i];
     const int64_t last = se.m - (se.n_seg - 1) * p->seg_len;
     max_n = std::max<int64_t>(max_n, last);
   }
@@ -848,7 +852,7 @@ int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float 
 
 int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, float *d_sel,
                          cudaStream_t s) {
-  if (p->total_seg > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many segments");
+  if (p->base_seg > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many segments");
   float4 *st4 = d_stats ? reinterpret_cast<float4 *>(d_stats) : reinterpret_cast<float4 *>(p->d_stats);
   switch (reg_bins_per_thread(p)) {
     case 0: break;
@@ -876,9 +880,9 @@ int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, fl
   const int rc = ensure_smem(normalise_kernel, smem, g_lim_norm);
   if (rc) return rc;
   float4 *st = d_stats ? reinterpret_cast<float4 *>(d_stats) : reinterpret_cast<float4 *>(p->d_stats);
-  normalise_kernel<<<static_cast<unsigned>(p->total_seg), kNormThreads, smem, s>>>(
+  normalise_kernel<<<static_cast<unsigned>(p->base_seg), kNormThreads, smem, s>>>(
       reinterpret_cast<const float2 *>(d_spec), d_power, st, p->d_series, p->d_seg_off,
-      static_cast<int>(p->series.size()), p->seg_len, p->d_counters, bins, d_sel);
+      static_cast<int>(p->n_base), p->seg_len, p->d_counters, bins, d_sel);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }

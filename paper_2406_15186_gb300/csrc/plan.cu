@@ -49,10 +49,11 @@ static double log_sf_normal(double s) {
   return -0.5 * s2 - std::log(s) - 0.5 * std::log(2.0 * M_PI) + std::log(series);
 }
 
-// Smallest float T with ln Q(w, T) <= y (bisection on the FP64 ln Q).
-static float threshold_for(int w, double y) {
+// Smallest float T with ln Q(a, T) <= y (bisection on the FP64 ln Q); a is
+// the gamma shape of a width-w sum: w, or H(H+1)/2 w for harmonic stage H.
+static float threshold_for(double w, double y) {
   if (y >= 0.0) return 0.0f;
-  double lo = 0.0, hi = static_cast<double>(w) + 1.0;
+  double lo = 0.0, hi = w + 1.0;
   while (log_q_gamma(w, hi) > y) hi *= 2.0;
   for (int it = 0; it < 300 && hi - lo > 1e-13 * hi; ++it) {
     const double mid = 0.5 * (lo + hi);
@@ -67,16 +68,18 @@ static void compute_thresholds(pulscan_plan p) {
   const int W = p->z_max;
   const size_t ns = p->series.size();
   p->h_thresh.assign(ns * W, 0.0f);
-  std::map<double, std::vector<float>> cache;
+  std::map<std::pair<double, uint32_t>, std::vector<float>> cache;
   const double lsf = log_sf_normal(p->sigma_thr);
   for (size_t i = 0; i < ns; ++i) {
     const double nt = p->n_trials[i];
-    auto it = cache.find(nt);
+    const uint32_t h = p->series[i].harm;
+    auto it = cache.find({nt, h});
     if (it == cache.end()) {
       std::vector<float> t(W);
       const double y = lsf - std::log(nt);
-      for (int w = 1; w <= W; ++w) t[w - 1] = p->searched[w - 1] ? threshold_for(w, y) : INFINITY;
-      it = cache.emplace(nt, std::move(t)).first;
+      const double c = 0.5 * h * (h + 1);   // gamma shape per unit width
+      for (int w = 1; w <= W; ++w) t[w - 1] = p->searched[w - 1] ? threshold_for(c * w, y) : INFINITY;
+      it = cache.emplace(std::make_pair(nt, h), std::move(t)).first;
     }
     std::copy(it->second.begin(), it->second.end(), p->h_thresh.begin() + i * W);
   }
@@ -144,19 +147,23 @@ static int check_shape(int64_t n, int32_t z_max, int32_t seg_len, double sigma) 
 }
 
 static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_series, int32_t z_max,
-                      int32_t seg_len, double sigma) {
+                      int32_t seg_len, double sigma, int32_t numharm = 1) {
   if (!out) return fail(PULSCAN_ERR_INVALID_ARG, "null plan pointer");
   *out = nullptr;
   if (n_series < 1 || !lengths) return fail(PULSCAN_ERR_INVALID_ARG, "need at least one series");
+  if (numharm < 1 || numharm > 8) return fail(PULSCAN_ERR_INVALID_ARG, "numharm must be in 1..8");
   for (int32_t i = 0; i < n_series; ++i) {
     const int rc = check_shape(lengths[i], z_max, seg_len, sigma);
     if (rc) return rc;
+    if (seg_len > (lengths[i] / 2 + 1) / numharm)
+      return fail(PULSCAN_ERR_INVALID_ARG, "segment_len must be <= floor(M / numharm)");
   }
   pulscan_plan p = new (std::nothrow) pulscan_plan_s();
   if (!p) return fail(PULSCAN_ERR_NOMEM, "host allocation failed");
   p->z_max = z_max;
   p->seg_len = seg_len;
   p->sigma_thr = sigma;
+  p->numharm = numharm;
   // layout: series grouped by length (stable in the caller's order) so every
   // length class is one strided batched FFT
   std::vector<int> order(n_series);
@@ -193,10 +200,36 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
     p->layout_of_user[ui] = li;
     x += s.n;
     const int64_t mpad = (s.m + 31) / 32 * 32;
-    sp += (li + 1 < n_series) ? mpad : s.m;
-    pw += (li + 1 < n_series) ? mpad : s.m;
+    const bool last = li + 1 == n_series;
+    sp += last ? s.m : mpad;
+    pw += (last && numharm == 1) ? s.m : mpad;
     sg += s.n_seg;
     tl += (s.m + tile_bins - 1) / tile_bins;
+  }
+  p->n_base = n_series;
+  p->base_seg = sg;
+  // harmonic stages H = 2..numharm of every series (layout order): spectra of
+  // floor(M / H) bins in the power buffer after the series' powers
+  for (int h = 2; h <= numharm; ++h) {
+    for (int li = 0; li < n_series; ++li) {
+      const Series &b = p->series[li];
+      Series s{};
+      s.n = 0;
+      s.m = b.m / h;
+      s.n_seg = std::max<int64_t>(1, s.m / seg_len);
+      s.x_off = b.x_off;
+      s.spec_off = b.spec_off;
+      s.p_off = pw;
+      s.seg_off = sg;
+      s.tile_off = tl;
+      s.user_index = b.user_index;
+      s.harm = static_cast<uint32_t>(h);
+      p->series.push_back(s);
+      const bool last = h == numharm && li + 1 == n_series;
+      pw += last ? s.m : (s.m + 31) / 32 * 32;
+      sg += s.n_seg;
+      tl += (s.m + tile_bins - 1) / tile_bins;
+    }
   }
   p->x_floats = x;
   p->spec_bins = sp;
@@ -210,12 +243,13 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
   }
   p->max_cands = std::min<int64_t>(total_slots, int64_t(1) << 24);
   const int64_t dirty_words = (total_slots + 31) / 32;
-  // deferred-block list: at most one item per (warp, block); the capacity
-  // scales with the warps and is capped (an overflowing block is then run
-  // exactly by its own warp)
+  // deferred-block list: at most one item per (warp, block), capped at 2^16
+  // items (277 MB of snapshots); an overflowing block is run exactly by its
+  // own warp, which is far slower when whole regions are hot (the harmonic
+  // stages of strong tones flag tens of thousands of blocks)
   const int64_t total_warps = tl * p->search_warps;
   const int64_t nb = (z_max + kR - 1) / kR;
-  p->item_cap = std::min<int64_t>(total_warps * nb, std::min<int64_t>(std::max<int64_t>(total_warps, 8192), 65536));
+  p->item_cap = std::min<int64_t>(total_warps * nb, 65536);
   p->alloc_item_cap = p->item_cap;
   p->defer_grid = 4 * n_sm;   // 4-warp CTAs, one item each at a time: 16 warps per SM
   p->searched.assign(z_max, 1);
@@ -234,13 +268,14 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
       ok(dalloc(&p->d_slots, total_slots)) && ok(dalloc(&p->d_dirty, dirty_words)) &&
       ok(dalloc(&p->d_counters, 4 + static_cast<size_t>(n_sm))) && ok(dalloc(&p->d_cands, p->max_cands)) &&
       ok(dalloc(&p->d_items, p->item_cap)) && ok(dalloc(&p->d_snaps, p->item_cap * kR * 32)) &&
-      ok(dalloc(&p->d_gtab, z_max)) && ok(dalloc(&p->d_x_off, ns)) && ok(dalloc(&p->d_x_len, ns)) &&
+      ok(dalloc(&p->d_gtab, static_cast<size_t>(numharm) * z_max)) && ok(dalloc(&p->d_x_off, ns)) &&
+      ok(dalloc(&p->d_x_len, ns)) &&
       ok(dalloc(&p->d_ranges, static_cast<size_t>(n_sm) + 1))) {
     std::vector<SeriesDev> sd(ns);
     std::vector<int64_t> to(ns + 1), so(ns + 1);
     for (size_t i = 0; i < ns; ++i) {
       const Series &s = p->series[i];
-      sd[i] = SeriesDev{s.m, s.n_seg, s.p_off, s.spec_off, s.seg_off, s.tile_off, s.user_index, 0u};
+      sd[i] = SeriesDev{s.m, s.n_seg, s.p_off, s.spec_off, s.seg_off, s.tile_off, s.user_index, s.harm};
       to[i] = s.tile_off;
       so[i] = s.seg_off;
     }
@@ -264,16 +299,19 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
     for (int r = 0; r <= n_sm; ++r) rl[r] = tl * r / n_sm;   // equal contiguous tile ranges, one per SM
     ok(cuda_ok_or(cudaMemcpy(p->d_ranges, rl.data(), rl.size() * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(upload_thresholds(p));
-    std::vector<float> gt(z_max);
-    for (int w = 1; w <= z_max; ++w) gt[w - 1] = static_cast<float>(g_of(static_cast<double>(w)));
-    ok(cuda_ok_or(cudaMemcpy(p->d_gtab, gt.data(), z_max * sizeof(float), cudaMemcpyHostToDevice)));
+    std::vector<float> gt(static_cast<size_t>(numharm) * z_max);
+    for (int h = 1; h <= numharm; ++h)
+      for (int w = 1; w <= z_max; ++w)
+        gt[(h - 1) * static_cast<size_t>(z_max) + w - 1] = static_cast<float>(g_of(0.5 * h * (h + 1) * w));
+    ok(cuda_ok_or(cudaMemcpy(p->d_gtab, gt.data(), gt.size() * sizeof(float), cudaMemcpyHostToDevice)));
     ok(prepare_bank(p));
     ok(prepare_normalise(p));
   }
-  // cuFFT: one strided batched plan per length class
-  for (size_t i = 0; rc == PULSCAN_OK && i < ns;) {
+  // cuFFT: one strided batched plan per length class (the series only)
+  const size_t nb_fft = static_cast<size_t>(p->n_base);
+  for (size_t i = 0; rc == PULSCAN_OK && i < nb_fft;) {
     size_t j = i;
-    while (j < ns && p->series[j].n == p->series[i].n) ++j;
+    while (j < nb_fft && p->series[j].n == p->series[i].n) ++j;
     FftClass f{};
     f.n = p->series[i].n;
     f.count = static_cast<int>(j - i);
@@ -324,11 +362,16 @@ int pulscan_plan_create_batch(pulscan_plan *out, const int64_t *h_lengths, int32
   return build_plan(out, h_lengths, n_series, z_max, segment_len, threshold_sigma);
 }
 
+int pulscan_plan_create_harmonic(pulscan_plan *out, const int64_t *h_lengths, int32_t n_series, int32_t z_max,
+                                 int32_t segment_len, double threshold_sigma, int32_t numharm) {
+  return build_plan(out, h_lengths, n_series, z_max, segment_len, threshold_sigma, numharm);
+}
+
 void pulscan_plan_destroy(pulscan_plan plan) { free_plan(plan); }
 
 int pulscan_plan_get_info(pulscan_plan p, pulscan_plan_info *info) {
   if (!p || !info) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
-  info->n_series = static_cast<int64_t>(p->series.size());
+  info->n_series = p->n_base;
   info->x_floats = p->x_floats;
   info->spec_floats = 2 * p->spec_bins;
   info->power_floats = p->p_floats;
@@ -343,8 +386,9 @@ int pulscan_plan_get_info(pulscan_plan p, pulscan_plan_info *info) {
 int pulscan_plan_offsets(pulscan_plan p, int64_t *x_off, int64_t *spec_off, int64_t *power_off,
                          int64_t *seg_off) {
   if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
-  const size_t ns = p->series.size();
-  // offsets are reported in the caller's series order; entry ns is the total
+  const size_t ns = static_cast<size_t>(p->n_base);
+  // offsets are reported in the caller's series order; entry ns is the end
+  // of the series' own data (harmonic stages follow it)
   for (size_t u = 0; u < ns; ++u) {
     const Series &s = p->series[p->layout_of_user[u]];
     if (x_off) x_off[u] = s.x_off;
@@ -354,8 +398,8 @@ int pulscan_plan_offsets(pulscan_plan p, int64_t *x_off, int64_t *spec_off, int6
   }
   if (x_off) x_off[ns] = p->x_floats;
   if (spec_off) spec_off[ns] = p->spec_bins;
-  if (power_off) power_off[ns] = p->p_floats;
-  if (seg_off) seg_off[ns] = p->total_seg;
+  if (power_off) power_off[ns] = (p->numharm > 1) ? p->series[ns].p_off : p->p_floats;
+  if (seg_off) seg_off[ns] = p->base_seg;
   return PULSCAN_OK;
 }
 
@@ -397,9 +441,28 @@ int pulscan_plan_set_rblock(pulscan_plan p, int64_t block_width) {
   return PULSCAN_OK;
 }
 
+int pulscan_plan_stage_offsets(pulscan_plan p, int32_t harmonics, int64_t *h_power_off, int64_t *h_seg_off,
+                               int64_t *h_bins) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  if (harmonics < 1 || harmonics > p->numharm) return fail(PULSCAN_ERR_INVALID_ARG, "no such harmonic stage");
+  const size_t nb = static_cast<size_t>(p->n_base);
+  const size_t first = nb * static_cast<size_t>(harmonics - 1);   // stage entries follow the layout order
+  for (size_t u = 0; u < nb; ++u) {
+    const Series &s = p->series[first + p->layout_of_user[u]];
+    if (h_power_off) h_power_off[u] = s.p_off;
+    if (h_seg_off) h_seg_off[u] = s.seg_off;
+    if (h_bins) h_bins[u] = s.m;
+  }
+  const Series &last = p->series[first + nb - 1];
+  if (h_power_off) h_power_off[nb] = last.p_off + last.m;
+  if (h_seg_off) h_seg_off[nb] = last.seg_off + last.n_seg;
+  if (h_bins) h_bins[nb] = 0;
+  return PULSCAN_OK;
+}
+
 int pulscan_plan_thresholds(pulscan_plan p, int32_t series, float *h_thresh) {
   if (!p || !h_thresh) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
-  if (series < 0 || series >= static_cast<int32_t>(p->series.size()))
+  if (series < 0 || series >= static_cast<int32_t>(p->n_base))
     return fail(PULSCAN_ERR_INVALID_ARG, "series index out of range");
   const int li = p->layout_of_user[series];
   std::memcpy(h_thresh, p->h_thresh.data() + static_cast<size_t>(li) * p->z_max, p->z_max * sizeof(float));
@@ -429,8 +492,12 @@ int pulscan_power_normalise(pulscan_plan p, const float *d_spec, float *d_power,
   if (d_stats && !aligned16(d_stats)) return fail(PULSCAN_ERR_INVALID_ARG, "stats buffer must be 16-byte aligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   record(p, 2, s);
-  const int rc = launch_normalise(p, d_spec, d_power, d_stats, s);
+  int rc = launch_normalise(p, d_spec, d_power, d_stats, s);
   record(p, 3, s);
+  if (rc || p->numharm <= 1) return rc;
+  record(p, 12, s);
+  rc = launch_harmonic_sums(p, d_power, s);
+  record(p, 13, s);
   return rc;
 }
 
@@ -465,15 +532,18 @@ int pulscan_candidates(pulscan_plan p, pulscan_cand *h_out, int64_t cap, int64_t
     PS_CUDA(cudaMemcpyAsync(tmp.data(), p->d_cands, have * sizeof(pulscan_cand), cudaMemcpyDeviceToHost, s));
     PS_CUDA(cudaStreamSynchronize(s));
   }
-  // order by (series, segment, width): integer keys formed once per candidate
-  // ((series << 32 | segment), (width << 32 | index)); segments and widths
-  // are below 2^32, the index below 2^24
+  // order by (series, harmonics, segment, width): integer keys formed once
+  // per candidate ((series << 36 | harmonics << 32 | segment), (width << 32 |
+  // index)); series < 2^28, harmonics <= 8, segments and widths < 2^32, the
+  // index below 2^24
   std::vector<std::pair<uint64_t, uint64_t>> key(static_cast<size_t>(have));
   for (int64_t i = 0; i < have; ++i) {
     const pulscan_cand &c = tmp[i];
-    const Series &se = p->series[p->layout_of_user[c.series]];
+    const size_t e = static_cast<size_t>(p->n_base) * (c.harmonics - 1) + p->layout_of_user[c.series];
+    const Series &se = p->series[e];
     const int64_t seg = std::min<int64_t>(static_cast<int64_t>(c.bin) / p->seg_len, se.n_seg - 1);
-    key[i] = {(static_cast<uint64_t>(c.series) << 32) | static_cast<uint64_t>(seg),
+    key[i] = {(static_cast<uint64_t>(c.series) << 36) | (static_cast<uint64_t>(c.harmonics) << 32) |
+                  static_cast<uint64_t>(seg),
               (static_cast<uint64_t>(c.width) << 32) | static_cast<uint64_t>(i)};
   }
   std::sort(key.begin(), key.end());
@@ -566,11 +636,27 @@ int pulscan_plan_counters(pulscan_plan p, int64_t *h_out, int32_t n) {
 }
 
 int pulscan_plan_set_defer_capacity(pulscan_plan p, int64_t cap) {
-  if (!p || cap < 0) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
-  const int64_t nb = (p->z_max + kR - 1) / kR;
-  const int64_t limit = p->alloc_item_cap;
-  p->item_cap = std::min<int64_t>(cap, limit);
-  (void)nb;
+  if (!p || cap < 0 || cap > (int64_t(1) << 24)) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
+  if (cap > p->alloc_item_cap) {
+    // grow the list (the captured graph holds the old pointers: drop it)
+    PS_CUDA(cudaDeviceSynchronize());
+    unsigned long long *items = nullptr;
+    float *snaps = nullptr;
+    if (dalloc(&items, static_cast<size_t>(cap)) || dalloc(&snaps, static_cast<size_t>(cap) * kR * 32)) {
+      if (items) cudaFree(items);
+      return fail(PULSCAN_ERR_NOMEM, "deferred-block list allocation failed");
+    }
+    cudaFree(p->d_items);
+    cudaFree(p->d_snaps);
+    p->d_items = items;
+    p->d_snaps = snaps;
+    p->alloc_item_cap = cap;
+    if (p->graph.exec) {
+      cudaGraphExecDestroy(p->graph.exec);
+      p->graph.exec = nullptr;
+    }
+  }
+  p->item_cap = cap;
   return PULSCAN_OK;
 }
 
@@ -587,7 +673,7 @@ int pulscan_plan_enable_timing(pulscan_plan p, int on) {
 
 int pulscan_plan_timings(pulscan_plan p, float *h_ms, int32_t n) {
   if (!p || !h_ms || n < 0) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
-  for (int i = 0; i < std::min(n, 6); ++i) {
+  for (int i = 0; i < std::min(n, 7); ++i) {
     h_ms[i] = -1.0f;
     if (!p->ran[i] || !p->ev[2 * i]) continue;
     PS_CUDA(cudaEventSynchronize(p->ev[2 * i + 1]));

@@ -93,9 +93,10 @@ def check_maxima(p64, mx_gpu, am_gpu, w_max, seg_len, seg_range=None):
     return mx_ref, am_ref
 
 
-def oracle_decisions(mx_ref, n_trials, sigma_thr, widths=None):
+def oracle_decisions(mx_ref, n_trials, sigma_thr, widths=None, shape_mult=1):
     """(passes, ambiguous) per (segment, width) from the oracle maxima; only
-    searched widths (all when widths is None) can pass."""
+    searched widths (all when widths is None) can pass.  shape_mult: gamma
+    shape per unit width (H(H+1)/2 for an H-harmonic sum)."""
     n_seg, w_max = mx_ref.shape
     dec = np.zeros(mx_ref.shape, dtype=bool)
     amb = np.zeros(mx_ref.shape, dtype=bool)
@@ -105,20 +106,21 @@ def oracle_decisions(mx_ref, n_trials, sigma_thr, widths=None):
         if not ok.any():
             continue
         s = col[ok]
-        d = osig.passes(wi + 1, s, n_trials, sigma_thr)
-        lo = osig.passes(wi + 1, s * (1 - BAND), n_trials, sigma_thr)
-        hi = osig.passes(wi + 1, s * (1 + BAND), n_trials, sigma_thr)
+        a = shape_mult * (wi + 1)
+        d = osig.passes(a, s, n_trials, sigma_thr)
+        lo = osig.passes(a, s * (1 - BAND), n_trials, sigma_thr)
+        hi = osig.passes(a, s * (1 + BAND), n_trials, sigma_thr)
         dec[ok, wi] = d
         amb[ok, wi] = lo != hi
     return dec, amb
 
 
 def check_candidates(cands, p64, mx_ref, am_ref, w_max, seg_len, sigma_thr, n_trials, series=0, seg_rows=None,
-                     widths=None):
+                     widths=None, shape_mult=1):
     """Candidate set of one series vs the oracle decisions on its maxima."""
     m = len(p64)
     n_seg = mx_ref.shape[0]
-    dec, amb = oracle_decisions(mx_ref, n_trials, sigma_thr, widths)
+    dec, amb = oracle_decisions(mx_ref, n_trials, sigma_thr, widths, shape_mult)
     if seg_rows is not None:
         keep = np.zeros(n_seg, dtype=bool)
         keep[seg_rows[0]:seg_rows[1]] = True
@@ -146,7 +148,7 @@ def check_candidates(cands, p64, mx_ref, am_ref, w_max, seg_len, sigma_thr, n_tr
         if int(r["bin"]) != am_ref[s, w - 1]:
             k = int(r["bin"])
             assert float(np.sum(p64[k:k + w])) >= sref - S_TOL * scale
-        sg_ref = osig.sigma_of(w, float(r["power"]), n_trials)[0]
+        sg_ref = osig.sigma_of(shape_mult * w, float(r["power"]), n_trials)[0]
         assert abs(float(r["sigma"]) - sg_ref) <= SIG_TOL * max(1.0, abs(sg_ref)), (s, w, r["sigma"], sg_ref)
         assert float(r["sigma"]) >= sigma_thr - 1e-3
     del m

@@ -71,5 +71,5 @@ def test_invalid_arguments_rejected_before_cuda(lib):
 
 def test_candidate_record_layout():
     import paper_2406_15186_gb300 as pkg
-    assert pkg.CAND_DTYPE.itemsize == 24
+    assert pkg.CAND_DTYPE.itemsize == 32
     assert [pkg.CAND_DTYPE.fields[k][1] for k in ("series", "width", "bin", "power", "sigma")] == [0, 4, 8, 16, 20]

@@ -9,6 +9,8 @@ restatement of what the accelerated path computes, written from the paper:
 * ``significance`` -- chi-square survival, Bonferroni, Gaussian sigma (§2.2.3, Eq. 9)
 * ``pipeline``     -- the end-to-end search in the paper's order (width sampling, R-Block)
 * ``harmonic``     -- harmonic summing by decimation and its search (§2.3)
+* ``fidelity``     -- the paper's GPU approximations: median of medians (§2.5)
+                      and the polynomial log p (§2.6)
 * ``lse``          -- logsumexp relaxation of the segment maximum and its adjoint
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline and

@@ -290,6 +290,33 @@ def run_harmonic(torch, pkg, synth, dev, stream, x, cfg, steps, flush):
             "candidates_by_stage": [int((cands["harmonics"] == h).sum()) for h in range(1, numharm + 1)]}
 
 
+def run_fidelity(torch, pkg, plan, step, stream, steps, flush):
+    """The bench step in the paper-GPU fidelity mode (median of medians, every
+    (segment, width) maximum, polynomial log p)."""
+    plan.set_fidelity(pkg.FIDELITY_PAPER_GPU)
+    step()
+    ms, kn, kb, kf = [], [], [], []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        t = plan.timings()
+        kn.append(t[1])
+        kb.append(t[2])
+        kf.append(t[4])
+    n_c = len(plan.candidates(stream=stream))
+    plan.set_fidelity(pkg.FIDELITY_EXACT)
+    return {"ms_per_step": statistics.mean(ms), "normalise_mom_ms": statistics.mean(kn),
+            "all_maxima_ms": statistics.mean(kb), "poly_finalise_ms": statistics.mean(kf), "candidates": n_c,
+            "note": "median of medians over each 4096-bin block, the unthresholded bank (every segment x width "
+                    "maximum), the fitted polynomial log p per maximum"}
+
+
 def run_diff(torch, pkg, synth, dev, stream, steps):
     """Differentiable batch: logsumexp forward and hand-written backward over
     4096 binaries of 2^20 samples (widths 1..512, L = 2048, tau = 0.1)."""
@@ -438,6 +465,7 @@ def run_ours(args, rank, world, local):
         sampling[name] = {"search_ms": statistics.mean(ts), "candidates": len(plan.candidates(stream=stream))}
     plan.set_widths(0, 1)
     harmonic = run_harmonic(torch, pkg, synth, dev, stream, x, cfg, max(3, args.steps // 2), flush)
+    fidelity = run_fidelity(torch, pkg, plan, step, stream, max(3, args.steps // 2), flush)
     sampling["all"] = {"search_ms": statistics.mean(k_search) + statistics.mean(k_def) + statistics.mean(k_fin),
                        "candidates": n_cands}
 
@@ -489,6 +517,7 @@ def run_ours(args, rank, world, local):
             "width_sampling": dict(sampling, note="boxcar + deferred + finalise per step; all widths summed, "
                                                   "only the sampled ones compared (z mod 8 == 0; z a power of two)"),
             "harmonics": harmonic,
+            "paper_gpu_fidelity": fidelity,
             "roofline": roofline,
             "e2e": {"value": world * m * w_max / (e2e_ms_mean * 1e-3) / 1e9, "unit": UNIT,
                     "ms_per_step": e2e_ms_mean, "h2d_bytes_per_step": 4 * n,

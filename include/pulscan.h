@@ -166,6 +166,22 @@ PULSCAN_API int pulscan_plan_set_trials(pulscan_plan plan, double n_trials);
 #define PULSCAN_WIDTHS_LOG2 2
 PULSCAN_API int pulscan_plan_set_widths(pulscan_plan plan, int32_t mode, int32_t step);
 
+/* Paper-GPU fidelity (§2.5, §2.6 and their appendix listings), for comparing
+ * the GPU version's approximations with the exact path:
+ *   PULSCAN_FIDELITY_EXACT (0): exact median/MAD and exact chi-square
+ *     significance (the default);
+ *   PULSCAN_FIDELITY_PAPER_GPU (1): median and MAD of each component by
+ *     median of medians over the first segment_len bins of each block (stride-4
+ *     groups of local medians, scale 1.4826), and significance by the fitted
+ *     polynomial log p(pow = 2 S, dof = 2 a) of §2.6 for every (segment,
+ *     width) maximum (the polynomial is not monotone in the power, so every
+ *     maximum is evaluated; the search then costs the unthresholded bank).
+ * Mode 1 needs segment_len = 4^k <= 16384 (INVALID_ARG / UNSUPPORTED).  The
+ * logsumexp entry points return UNSUPPORTED in mode 1. */
+#define PULSCAN_FIDELITY_EXACT 0
+#define PULSCAN_FIDELITY_PAPER_GPU 1
+PULSCAN_API int pulscan_plan_set_fidelity(pulscan_plan plan, int32_t mode);
+
 /* Approximate r-bin output (§2.4, "Pulscan R-Block"): with block_width > 0,
  * pulscan_candidates / pulscan_search_host report in `bin` the block index
  * floor(k / block_width) of each candidate instead of its start bin k (the

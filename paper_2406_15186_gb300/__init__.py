@@ -55,6 +55,7 @@ _SIGS = {
     "pulscan_plan_set_trials": (ctypes.c_int, [_P, ctypes.c_double]),
     "pulscan_plan_set_widths": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "pulscan_plan_set_rblock": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "pulscan_plan_set_fidelity": (ctypes.c_int, [_P, ctypes.c_int32]),
     "pulscan_plan_thresholds": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pulscan_rfft": (ctypes.c_int, [_P, _P, _P, _P]),
     "pulscan_power_normalise": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -128,6 +129,7 @@ def _stream(stream):
 
 
 WIDTHS_ALL, WIDTHS_STEP, WIDTHS_LOG2 = 0, 1, 2
+FIDELITY_EXACT, FIDELITY_PAPER_GPU = 0, 1
 
 
 class Plan:
@@ -193,6 +195,10 @@ class Plan:
     def set_widths(self, mode=0, step=1):
         """Searched widths: WIDTHS_ALL, WIDTHS_STEP (z mod step == 0) or WIDTHS_LOG2 (z a power of two)."""
         _check(load().pulscan_plan_set_widths(self._h, int(mode), int(step)))
+
+    def set_fidelity(self, mode):
+        """FIDELITY_EXACT (default) or FIDELITY_PAPER_GPU (median of medians + polynomial log p)."""
+        _check(load().pulscan_plan_set_fidelity(self._h, int(mode)))
 
     def set_rblock(self, block_width):
         """Report block indices floor(bin / block_width) instead of bins (0: exact bins)."""

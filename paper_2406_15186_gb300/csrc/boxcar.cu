@@ -744,6 +744,10 @@ int launch_segmax_raw(const float *d_power, const SeriesDev *d_series, const int
   return PULSCAN_OK;
 }
 
+int launch_maxima_only(pulscan_plan p, const float *d_power, cudaStream_t s) {
+  return launch_bank(p, d_power, false, s);   // tile claim counters zeroed with the others by the caller
+}
+
 int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s) {
   return launch_bank(p, d_power, true, s);
 }

@@ -118,6 +118,8 @@ struct pulscan_plan_s {
   std::vector<uint8_t> searched;    // per width: compared and reported (1) or only summed (0)
   bool trials_fixed = false;        // n_trials set by the caller (kept when the widths change)
   int64_t rblock = 0;               // > 0: candidates report floor(bin / rblock)
+  int32_t fidelity = 0;             // PULSCAN_FIDELITY_*: exact, or the paper's GPU approximations
+  uint8_t *d_searched = nullptr;    // device copy of `searched`
   std::vector<int> layout_of_user;  // user series index -> layout index
   std::vector<float> h_thresh;      // n_series * z_max, layout order
   int64_t x_floats = 0, spec_bins = 0, p_floats = 0, total_seg = 0, total_tiles = 0;
@@ -171,6 +173,12 @@ int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, fl
 int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s);
 int launch_finalize(pulscan_plan p, cudaStream_t s);
 int launch_harmonic_sums(pulscan_plan p, float *d_power, cudaStream_t s);   // stage spectra X_H
+// paper-GPU fidelity mode
+bool is_power_of_four(int64_t v);
+int launch_normalise_mom(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, cudaStream_t s);
+int launch_maxima_only(pulscan_plan p, const float *d_power, cudaStream_t s);   // all maxima into the slots
+int launch_poly_finalize(pulscan_plan p, cudaStream_t s);
+double host_log_sf_normal(double s);   // ln Phi_c(s), FP64 on the host
 int launch_segmax(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax,
                   cudaStream_t s);
 void record(pulscan_plan p, int idx, cudaStream_t s);  // timing event helper

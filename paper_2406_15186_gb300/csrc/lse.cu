@@ -611,6 +611,8 @@ SmemLimit g_lim_fwd, g_lim_bwd;
 
 int lse_prepare(pulscan_plan p) {
   if (p->numharm > 1) return fail(PULSCAN_ERR_UNSUPPORTED, "logsumexp path on a harmonic plan");
+  if (p->fidelity != PULSCAN_FIDELITY_EXACT)
+    return fail(PULSCAN_ERR_UNSUPPORTED, "logsumexp path in the median-of-medians mode");
   if (lse_warps(p) > kLseMaxWarps)
     return fail(PULSCAN_ERR_UNSUPPORTED, "logsumexp path needs segments of at most 4224 bins");
   return PULSCAN_OK;

@@ -852,6 +852,10 @@ int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float 
 
 int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, float *d_sel,
                          cudaStream_t s) {
+  if (p->fidelity == PULSCAN_FIDELITY_PAPER_GPU) {
+    if (d_sel != nullptr) return fail(PULSCAN_ERR_UNSUPPORTED, "no adjoint for the median-of-medians statistics");
+    return launch_normalise_mom(p, d_spec, d_power, d_stats, s);
+  }
   if (p->base_seg > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many segments");
   float4 *st4 = d_stats ? reinterpret_cast<float4 *>(d_stats) : reinterpret_cast<float4 *>(p->d_stats);
   switch (reg_bins_per_thread(p)) {

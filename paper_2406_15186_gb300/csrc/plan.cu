@@ -42,7 +42,7 @@ void record(pulscan_plan p, int idx, cudaStream_t s) {
 
 // ln Phi_c(s) on the host: erfc while it is representable, else the
 // asymptotic (Mills-ratio) series phi(s)/s (1 - 1/s^2 + 3/s^4 - 15/s^6 + 105/s^8).
-static double log_sf_normal(double s) {
+double host_log_sf_normal(double s) {
   if (s < 30.0) return std::log(0.5 * std::erfc(s / std::sqrt(2.0)));
   const double s2 = s * s;
   const double series = 1.0 - 1.0 / s2 + 3.0 / (s2 * s2) - 15.0 / (s2 * s2 * s2) + 105.0 / (s2 * s2 * s2 * s2);
@@ -69,7 +69,7 @@ static void compute_thresholds(pulscan_plan p) {
   const size_t ns = p->series.size();
   p->h_thresh.assign(ns * W, 0.0f);
   std::map<std::pair<double, uint32_t>, std::vector<float>> cache;
-  const double lsf = log_sf_normal(p->sigma_thr);
+  const double lsf = host_log_sf_normal(p->sigma_thr);
   for (size_t i = 0; i < ns; ++i) {
     const double nt = p->n_trials[i];
     const uint32_t h = p->series[i].harm;
@@ -104,6 +104,7 @@ static int upload_thresholds(pulscan_plan p) {
   PS_CUDA(cudaMemcpy(p->d_thresh, p->h_thresh.data(), ns * W * sizeof(float), cudaMemcpyHostToDevice));
   PS_CUDA(cudaMemcpy(p->d_thresh_bound, tb.data(), ns * W * sizeof(float), cudaMemcpyHostToDevice));
   PS_CUDA(cudaMemcpy(p->d_ln_trials, lt.data(), ns * sizeof(double), cudaMemcpyHostToDevice));
+  PS_CUDA(cudaMemcpy(p->d_searched, p->searched.data(), W * sizeof(uint8_t), cudaMemcpyHostToDevice));
   return PULSCAN_OK;
 }
 
@@ -116,7 +117,7 @@ static void free_plan(pulscan_plan p) {
   void *ptrs[] = {p->d_series, p->d_tile_off, p->d_seg_off, p->d_thresh, p->d_thresh_bound, p->d_ln_trials,
                   p->d_stats,  p->d_slots,    p->d_dirty,   p->d_counters, p->d_cands,     p->own_x,
                   p->own_spec, p->own_power, p->d_items, p->d_snaps,    p->d_gtab,     p->d_x_off,
-                  p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec,   p->d_ranges};
+                  p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec,   p->d_ranges,  p->d_searched};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (auto &e : p->ev)
@@ -270,7 +271,7 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
       ok(dalloc(&p->d_items, p->item_cap)) && ok(dalloc(&p->d_snaps, p->item_cap * kR * 32)) &&
       ok(dalloc(&p->d_gtab, static_cast<size_t>(numharm) * z_max)) && ok(dalloc(&p->d_x_off, ns)) &&
       ok(dalloc(&p->d_x_len, ns)) &&
-      ok(dalloc(&p->d_ranges, static_cast<size_t>(n_sm) + 1))) {
+      ok(dalloc(&p->d_ranges, static_cast<size_t>(n_sm) + 1)) && ok(dalloc(&p->d_searched, z_max))) {
     std::vector<SeriesDev> sd(ns);
     std::vector<int64_t> to(ns + 1), so(ns + 1);
     for (size_t i = 0; i < ns; ++i) {
@@ -435,6 +436,22 @@ int pulscan_plan_set_widths(pulscan_plan p, int32_t mode, int32_t step) {
   return upload_thresholds(p);
 }
 
+int pulscan_plan_set_fidelity(pulscan_plan p, int32_t mode) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  if (mode != PULSCAN_FIDELITY_EXACT && mode != PULSCAN_FIDELITY_PAPER_GPU)
+    return fail(PULSCAN_ERR_INVALID_ARG, "unknown fidelity mode");
+  if (mode == PULSCAN_FIDELITY_PAPER_GPU && !is_power_of_four(p->seg_len))
+    return fail(PULSCAN_ERR_INVALID_ARG, "median of medians needs segment_len = 4^k");
+  if (mode == PULSCAN_FIDELITY_PAPER_GPU && p->seg_len > 16384)
+    return fail(PULSCAN_ERR_UNSUPPORTED, "median of medians over more than 16384 bins");
+  p->fidelity = mode;
+  if (p->graph.exec) {   // the captured graph holds the other mode's kernels
+    cudaGraphExecDestroy(p->graph.exec);
+    p->graph.exec = nullptr;
+  }
+  return PULSCAN_OK;
+}
+
 int pulscan_plan_set_rblock(pulscan_plan p, int64_t block_width) {
   if (!p || block_width < 0) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
   p->rblock = block_width;
@@ -503,6 +520,17 @@ int pulscan_power_normalise(pulscan_plan p, const float *d_spec, float *d_power,
 
 static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s) {
   PS_CUDA(cudaMemsetAsync(p->d_counters, 0, (4 + static_cast<size_t>(p->n_ranges)) * sizeof(uint32_t), s));
+  if (p->fidelity == PULSCAN_FIDELITY_PAPER_GPU) {
+    // every (segment, width) maximum, then the polynomial significance of each
+    record(p, 4, s);
+    int rc = launch_maxima_only(p, d_power, s);
+    if (rc) return rc;
+    record(p, 5, s);
+    record(p, 8, s);
+    rc = launch_poly_finalize(p, s);
+    record(p, 9, s);
+    return rc;
+  }
   record(p, 4, s);
   int rc = launch_search(p, d_power, s);   // records 5, 6, 7 around the deferred kernel
   if (rc) return rc;

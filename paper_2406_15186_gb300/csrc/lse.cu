@@ -13,18 +13,18 @@
 // as in the search):
 // * lse_forward_kernel: pass 1 finds M[s, w] = max S_w (per step a lane max
 //   into shared memory, merged per width once per 33-width block); pass 2
-//   re-runs the sums and exponentiates only windows within
-//   tau * ln(2^24 L) of M -- every other term is below FP32 resolution of the
-//   sum, which is >= 1 -- so exp work is rare;
+//   re-runs the sums and exponentiates only windows within tau * ln 2^24 of
+//   M -- every other term weighs < 2^-24 of the largest, and at most 2L of
+//   them change Y by < tau 2L 2^-24 -- so exp work is rare;
 // * lse_backward_kernel: re-runs the sums; each window within
-//   tau * ln(2^24 L) of Y gets weight g = G exp((S - Y) / tau), entered as a
+//   tau * ln 2^24 of Y gets weight g = G exp((S - Y) / tau), entered as a
 //   difference pair D[k] += g, D[k + w] -= g in shared memory; one block
 //   prefix sum of D gives dL/dP over the segment and a (W - 1)-bin tail that
 //   spills into the next segment (no global atomics);
-// * the register ring only flags, per width, which lanes hold a window
-//   within the cut (one lane max, one ballot per step); the flagged (lane,
-//   width) events are worked off after each 33-width block by the whole warp,
-//   one event at a time with a lane per window.  Keeping the exp / scatter
+// * the register ring only flags, per width, which 11-bin groups of which
+//   lanes hold a window within the cut (three group maxima per step); the
+//   flagged (group, width) events are worked off after each 33-width block
+//   by the whole warp, a lane per window.  Keeping the exp / scatter
 //   code out of the 33 unrolled ring steps keeps the loop body small enough
 //   for the instruction cache;
 // * the running FP32 sums pick windows only: an exponent (S - M) / tau
@@ -240,25 +240,56 @@ __device__ __forceinline__ float lane_max(const float (&s)[kR], int lim) {
   return m;
 }
 
-// Works off one width's events of this warp: every flagged lane's windows
-// (33 per event, packed over the warp's lanes) whose exact sum lies above
-// thr call f(k, S) with k the local start bin.  A window is first screened
-// with the high parts of the prefix alone: each is within half an ulp of F,
-// so fh[b] - fh[a] is within 1.5 ulp of S; the margin is 4 ulp of F[b].
-// my_lim: the calling lane's valid window count at w; evl: this warp's
-// 32-entry scratch for the list of flagged lanes.
+// Maxima of the lane's three 11-bin groups (windows i < lim only; -inf where
+// none) and their maximum.
+constexpr int kGrp = 11;
+__device__ __forceinline__ float lane_groups(const float (&s)[kR], int lim, float (&g)[3]) {
+  if (lim >= kR) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int o = kGrp * j;
+      g[j] = max3(max3(max3(s[o], s[o + 1], s[o + 2]), max3(s[o + 3], s[o + 4], s[o + 5]),
+                       max3(s[o + 6], s[o + 7], s[o + 8])), s[o + 9], s[o + 10]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float m = -INFINITY;
+#pragma unroll
+      for (int i = 0; i < kGrp; ++i) m = fmaxf(m, (kGrp * j + i < lim) ? s[kGrp * j + i] : -INFINITY);
+      g[j] = m;
+    }
+  }
+  return max3(g[0], g[1], g[2]);
+}
+
+// Works off one width's events of this warp: the 11-bin groups flagged by
+// their lanes (grp: this lane's 3-bit mask, zero if not flagged), their
+// windows packed over the warp's lanes; every window whose exact sum lies
+// above thr calls f(k, S) with k the local start bin.  A window is first
+// screened with the high parts of the prefix alone: each is within half an
+// ulp of F, so fh[b] - fh[a] is within 1.5 ulp of S; the margin is 4 ulp of
+// F[b].  my_lim: the calling lane's valid window count at w; evl: this warp's
+// 96-entry scratch for the list of flagged groups.
 template <class F>
-__device__ __forceinline__ void for_event_windows(uint32_t bal, int warp, int lane, int my_lim, int w, float thr,
+__device__ __forceinline__ void for_event_windows(uint32_t grp, int warp, int lane, int my_lim, int w, float thr,
                                                   const float *__restrict__ fh, const float *__restrict__ fl,
                                                   int *evl, F &&f) {
-  if ((bal >> lane) & 1u) evl[__popc(bal & ((1u << lane) - 1u))] = lane | (my_lim << 8);
+  int n_ev = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const uint32_t bj = __ballot_sync(kFullMask, (grp >> j) & 1u);
+    if ((bj >> lane) & 1u) evl[n_ev + __popc(bj & ((1u << lane) - 1u))] = lane | (j << 5) | (my_lim << 8);
+    n_ev += __popc(bj);
+  }
   __syncwarp();
-  const int n = kR * __popc(bal);
+  const int n = kGrp * n_ev;
   for (int q = lane; q < n; q += 32) {
-    const int e = q / kR, i = q - kR * e;
+    const int e = q / kGrp;
     const int ev = evl[e];
+    const int i = kGrp * ((ev >> 5) & 7) + (q - kGrp * e);   // bin of the lane
     if (i < (ev >> 8)) {
-      const int k = warp * (32 * kR) + (ev & 255) * kR + i;
+      const int k = warp * (32 * kR) + (ev & 31) * kR + i;
       const float hb = fh[k + w];
       if (hb - fh[k] > thr - 4.8e-7f * fabsf(hb)) {
         const float sw = window_sum(fh, fl, k, k + w);
@@ -280,10 +311,11 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
   float *mblk = buf + buf_len;                   // 64: M of the current 33 widths
   float *lsb = mblk + 64;                        // 64: their sums of exp
-  int *evl = reinterpret_cast<int *>(lsb + 64);  // warps x 32 flagged-lane lists
-  float *kmax = reinterpret_cast<float *>(evl + kLseMaxWarps * 32);   // warps x 33 x 32 lane maxima
+  int *evl = reinterpret_cast<int *>(lsb + 64);  // warps x 96 flagged-group lists
+  float *kmax = reinterpret_cast<float *>(evl + kLseMaxWarps * 96);   // warps x 33 x 32 lane maxima
   const int warps = blockDim.x >> 5;
-  float *fh = kmax + warps * kR * 32;            // prefix pair, buf_len + 1 each
+  uint8_t *kgrp = reinterpret_cast<uint8_t *>(kmax + warps * kR * 32);   // their group masks
+  float *fh = kmax + warps * kR * 32 + warps * kR * 8;   // prefix pair, buf_len + 1 each
   float *fl = fh + buf_len + 1;
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
@@ -294,10 +326,20 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   const float inv_tau = 1.0f / tau;
   float s[kR];
   // One sweep over the widths.  Per step every lane stores the max of its 33
-  // windows; after each 33-width block the lane maxima give M[s, w] and the
-  // lanes with a window within `cut` of it, whose windows are then summed.
+  // windows and which of its 11-bin groups come within `cut` of that max;
+  // after each 33-width block the lane maxima give M[s, w], and the groups
+  // of the lanes within `cut` of M (a group below lane max - cut is below
+  // M - cut too) have their windows summed.
   walk_widths(
-      s, buf + x0, W, [&](int w, int c) { kmax[(warp * kR + c) * 32 + lane] = lane_max(s, ll.at(w)); },
+      s, buf + x0, W,
+      [&](int w, int c) {
+        float g[3];
+        const float lm = lane_groups(s, ll.at(w), g);
+        kmax[(warp * kR + c) * 32 + lane] = lm;
+        const float lo = lm - cut;
+        kgrp[(warp * kR + c) * 32 + lane] =
+            static_cast<uint8_t>((g[0] >= lo ? 1u : 0u) | (g[1] >= lo ? 2u : 0u) | (g[2] >= lo ? 4u : 0u));
+      },
       [&](int bi, int nsteps) {
         __syncthreads();
         for (int c = threadIdx.x; c < nsteps; c += blockDim.x) {
@@ -311,11 +353,12 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
         for (int c = 0; c < nsteps; ++c) {
           const float mw = mblk[c];
           const float thr = mw - cut;
-          const uint32_t bal = __ballot_sync(kFullMask, kmax[(warp * kR + c) * 32 + lane] > thr);
-          if (bal == 0u) continue;
+          const bool hot = kmax[(warp * kR + c) * 32 + lane] > thr;
+          if (!__any_sync(kFullMask, hot)) continue;
           float acc = 0.0f;
           const int w = bi * kR + c + 1;
-          for_event_windows(bal, warp, lane, ll.at(w), w, thr, fh, fl, evl + warp * 32,
+          const uint32_t grp = hot ? kgrp[(warp * kR + c) * 32 + lane] : 0u;
+          for_event_windows(grp, warp, lane, ll.at(w), w, thr, fh, fl, evl + warp * 96,
                             [&](int, float sw) { acc += expf((sw - mw) * inv_tau); });
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
@@ -342,8 +385,9 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   float *dd = grow + W;                          // d_len difference entries
   float *wsum = dd + d_len;                      // per-warp scan totals
   uint32_t *evm = reinterpret_cast<uint32_t *>(wsum + 32);   // warps x 33 event ballots
-  int *evl = reinterpret_cast<int *>(evm + kLseMaxWarps * kR);   // warps x 32 flagged-lane lists
-  float *fh = reinterpret_cast<float *>(evl + kLseMaxWarps * 32);   // prefix pair, buf_len + 1 each
+  int *evl = reinterpret_cast<int *>(evm + kLseMaxWarps * kR);   // warps x 96 flagged-group lists
+  uint8_t *kgrp = reinterpret_cast<uint8_t *>(evl + kLseMaxWarps * 96);   // warps x 33 x 32 group masks
+  float *fh = reinterpret_cast<float *>(kgrp + kLseMaxWarps * kR * 32);   // prefix pair, buf_len + 1 each
   float *fl = fh + buf_len + 1;
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
@@ -364,8 +408,12 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   walk_widths(
       s, lane_buf, W,
       [&](int w, int c) {
-        const bool ev = grow[w - 1] != 0.0f && lane_max(s, ll.at(w)) > yrow[w - 1] - cut;
-        const uint32_t bal = __ballot_sync(kFullMask, ev);
+        float g[3];
+        lane_groups(s, ll.at(w), g);
+        const float thr = grow[w - 1] != 0.0f ? yrow[w - 1] - cut : INFINITY;
+        const uint32_t m = (g[0] > thr ? 1u : 0u) | (g[1] > thr ? 2u : 0u) | (g[2] > thr ? 4u : 0u);
+        kgrp[(warp * kR + c) * 32 + lane] = static_cast<uint8_t>(m);
+        const uint32_t bal = __ballot_sync(kFullMask, m != 0u);
         if (lane == 0) wev[c] = bal;
       },
       [&](int bi, int nsteps) {
@@ -376,7 +424,8 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
           const int w = bi * kR + c + 1;
           const float yw = yrow[w - 1];
           const float gw = grow[w - 1];
-          for_event_windows(bal, warp, lane, ll.at(w), w, yw - cut, fh, fl, evl + warp * 32, [&](int k, float sw) {
+          for_event_windows(kgrp[(warp * kR + c) * 32 + lane], warp, lane, ll.at(w), w, yw - cut, fh, fl,
+                            evl + warp * 96, [&](int k, float sw) {
             const float g = gw * expf((sw - yw) * inv_tau);
             atomicAdd(&dd[k], g);
             atomicAdd(&dd[k + w], -g);
@@ -644,8 +693,13 @@ int lse_backward_buffers(pulscan_plan p) {
 }
 
 float lse_cut(pulscan_plan p, float tau) {
-  // terms below 2^-24 / L of the largest one are beyond FP32 resolution of the sum
-  return tau * static_cast<float>(std::log(16777216.0 * static_cast<double>(p->seg_len + p->seg_len)));
+  // windows more than tau ln 2^24 below the maximum each weigh < 2^-24 of it;
+  // at most 2L of them (a segment's start bins) add < 2L 2^-24 to the sum
+  // (>= 1), i.e. < tau 2L 2^-24 to Y (1.2e-5 tau per 1000 bins of segment),
+  // below Y's FP32 resolution except for the smallest widths, and each
+  // dropped weight changes dL/dP by < 2^-24 of the largest one
+  (void)p;
+  return tau * static_cast<float>(std::log(16777216.0));
 }
 
 }  // namespace
@@ -670,7 +724,7 @@ int pulscan_lse_forward(pulscan_plan p, const float *d_x, float *d_spec, float *
   if (rc) return rc;
   const int warps = lse_warps(p);
   const int buf_len = lse_buf_len(p, warps);
-  const int smem = 128 + 4 * (buf_len + 128 + kLseMaxWarps * 32 + warps * kR * 32 + 2 * (buf_len + 1));
+  const int smem = 128 + 4 * (buf_len + 128 + kLseMaxWarps * 96 + warps * kR * 32 + warps * kR * 8 + 2 * (buf_len + 1));
   rc = ensure_smem(lse_forward_kernel, smem, g_lim_fwd);
   if (rc) return rc;
   lse_forward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
@@ -696,8 +750,8 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   int64_t max_n = 0;
   for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
   const int d_len = static_cast<int>(max_n + p->z_max + 1);
-  const int smem =
-      128 + 4 * (buf_len + 2 * p->z_max + d_len + 32 + kLseMaxWarps * (kR + 32) + 2 * (buf_len + 1));
+  const int smem = 128 + 4 * (buf_len + 2 * p->z_max + d_len + 32 + kLseMaxWarps * (kR + 96) +
+                              kLseMaxWarps * kR * 8 + 2 * (buf_len + 1));
   rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
   if (rc) return rc;
   lse_backward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(

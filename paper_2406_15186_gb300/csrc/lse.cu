@@ -42,6 +42,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cuda_fp16.h>
+
 #include "bank.cuh"
 #include "common.cuh"
 #include "ptx.cuh"
@@ -61,11 +63,13 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
   return t;
 }
 
-// Exclusive prefix F[j] = sum_{i<j} buf[i] for j = 0..n as fh[j] + fl[j].
+// Exclusive prefix F[j] = sum_{i<j} buf[i] for j = 0..n as fh[j] + fl[j];
+// fl (at most half an ulp of fh) is kept in FP16, whose 11-bit mantissa
+// leaves an error below 2^-12 ulp of F.
 // Each thread sums a contiguous chunk with two-sum, the chunk totals are
 // scanned in FP64 (wtot: one double per warp), then each chunk is re-walked
 // from its FP64 carry split into a float pair.  Ends with a barrier.
-__device__ void build_prefix(const float *__restrict__ buf, int n, float *__restrict__ fh, float *__restrict__ fl,
+__device__ void build_prefix(const float *__restrict__ buf, int n, float *__restrict__ fh, __half *__restrict__ fl,
                              double *wtot) {
   const int nt = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int chunk = (n + nt - 1) / nt;
@@ -92,23 +96,23 @@ __device__ void build_prefix(const float *__restrict__ buf, int n, float *__rest
   for (int j = a0; j < a1; ++j) {
     const float hs = __fadd_rn(h, l);
     fh[j] = hs;
-    fl[j] = __fsub_rn(l, __fsub_rn(hs, h));
+    fl[j] = __float2half_rn(__fsub_rn(l, __fsub_rn(hs, h)));
     h = two_sum(h, buf[j], e);
     l = __fadd_rn(l, e);
   }
   if (threadIdx.x == nt - 1) {   // its chunk ends at n, or is empty with the full total as carry
     const float hs = __fadd_rn(h, l);
     fh[n] = hs;
-    fl[n] = __fsub_rn(l, __fsub_rn(hs, h));
+    fl[n] = __float2half_rn(__fsub_rn(l, __fsub_rn(hs, h)));
   }
   __syncthreads();
 }
 
 // sum buf[a..b) = F[b] - F[a], to about one rounding.
-__device__ __forceinline__ float window_sum(const float *__restrict__ fh, const float *__restrict__ fl, int a, int b) {
+__device__ __forceinline__ float window_sum(const float *__restrict__ fh, const __half *__restrict__ fl, int a, int b) {
   float e;
   const float d = two_sum(fh[b], -fh[a], e);
-  return __fadd_rn(d, __fadd_rn(e, __fsub_rn(fl[b], fl[a])));
+  return __fadd_rn(d, __fadd_rn(e, __fsub_rn(__half2float(fl[b]), __half2float(fl[a]))));
 }
 
 // Ring steps C0..C0+NC-1 with a per-step callback cb(c) after the adds.
@@ -273,7 +277,7 @@ __device__ __forceinline__ float lane_groups(const float (&s)[kR], int lim, floa
 // 96-entry scratch for the list of flagged groups.
 template <class F>
 __device__ __forceinline__ void for_event_windows(uint32_t grp, int warp, int lane, int my_lim, int w, float thr,
-                                                  const float *__restrict__ fh, const float *__restrict__ fl,
+                                                  const float *__restrict__ fh, const __half *__restrict__ fl,
                                                   int *evl, F &&f) {
   int n_ev = 0;
 #pragma unroll
@@ -315,8 +319,9 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   float *kmax = reinterpret_cast<float *>(evl + kLseMaxWarps * 96);   // warps x 33 x 32 lane maxima
   const int warps = blockDim.x >> 5;
   uint8_t *kgrp = reinterpret_cast<uint8_t *>(kmax + warps * kR * 32);   // their group masks
-  float *fh = kmax + warps * kR * 32 + warps * kR * 8;   // prefix pair, buf_len + 1 each
-  float *fl = fh + buf_len + 1;
+  float *wmax = kmax + warps * kR * 32 + warps * kR * 8;   // warps x 33 per-warp maxima
+  float *fh = wmax + kLseMaxWarps * kR;                   // prefix: high part, buf_len + 1
+  __half *fl = reinterpret_cast<__half *>(fh + buf_len + 1);   // low part, buf_len + 1
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
   build_prefix(buf, buf_len, fh, fl, wtot);
@@ -341,11 +346,19 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
             static_cast<uint8_t>((g[0] >= lo ? 1u : 0u) | (g[1] >= lo ? 2u : 0u) | (g[2] >= lo ? 4u : 0u));
       },
       [&](int bi, int nsteps) {
+        // M per width: each warp reduces its own lanes (lane c takes width c,
+        // skewed reads are conflict-free), then the warps' maxima are merged
+        __syncthreads();
+        for (int c = lane; c < nsteps; c += 32) {
+          float m = -INFINITY;
+#pragma unroll 8
+          for (int l = 0; l < 32; ++l) m = fmaxf(m, kmax[(warp * kR + c) * 32 + ((l + c) & 31)]);
+          wmax[warp * kR + c] = m;
+        }
         __syncthreads();
         for (int c = threadIdx.x; c < nsteps; c += blockDim.x) {
           float m = -INFINITY;
-          for (int v = 0; v < warps; ++v)
-            for (int l = 0; l < 32; ++l) m = fmaxf(m, kmax[(v * kR + c) * 32 + ((l + c) & 31)]);
+          for (int v = 0; v < warps; ++v) m = fmaxf(m, wmax[v * kR + c]);
           mblk[c] = m;
           lsb[c] = 0.0f;
         }
@@ -387,8 +400,8 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   uint32_t *evm = reinterpret_cast<uint32_t *>(wsum + 32);   // warps x 33 event ballots
   int *evl = reinterpret_cast<int *>(evm + kLseMaxWarps * kR);   // warps x 96 flagged-group lists
   uint8_t *kgrp = reinterpret_cast<uint8_t *>(evl + kLseMaxWarps * 96);   // warps x 33 x 32 group masks
-  float *fh = reinterpret_cast<float *>(kgrp + kLseMaxWarps * kR * 32);   // prefix pair, buf_len + 1 each
-  float *fl = fh + buf_len + 1;
+  float *fh = reinterpret_cast<float *>(kgrp + kLseMaxWarps * kR * 32);   // prefix: high part, buf_len + 1
+  __half *fl = reinterpret_cast<__half *>(fh + buf_len + 1);   // low part, buf_len + 1
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
   build_prefix(buf, buf_len, fh, fl, wtot);
@@ -724,7 +737,8 @@ int pulscan_lse_forward(pulscan_plan p, const float *d_x, float *d_spec, float *
   if (rc) return rc;
   const int warps = lse_warps(p);
   const int buf_len = lse_buf_len(p, warps);
-  const int smem = 128 + 4 * (buf_len + 128 + kLseMaxWarps * 96 + warps * kR * 32 + warps * kR * 8 + 2 * (buf_len + 1));
+  const int smem = 128 + 4 * (buf_len + 128 + kLseMaxWarps * 96 + warps * kR * 32 + warps * kR * 8 +
+                              kLseMaxWarps * kR + (buf_len + 1)) + 2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_forward_kernel, smem, g_lim_fwd);
   if (rc) return rc;
   lse_forward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
@@ -751,7 +765,7 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
   const int d_len = static_cast<int>(max_n + p->z_max + 1);
   const int smem = 128 + 4 * (buf_len + 2 * p->z_max + d_len + 32 + kLseMaxWarps * (kR + 96) +
-                              kLseMaxWarps * kR * 8 + 2 * (buf_len + 1));
+                              kLseMaxWarps * kR * 8 + (buf_len + 1)) + 2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
   if (rc) return rc;
   lse_backward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(

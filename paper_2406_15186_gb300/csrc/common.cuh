@@ -136,6 +136,8 @@ struct pulscan_plan_s {
   float *d_stats = nullptr;        // 4 * total_seg
   unsigned long long *d_slots = nullptr;  // total_seg * z_max keys, 0 at rest
   uint32_t *d_dirty = nullptr;     // one bit per slot touched by the search, 0 at rest
+  uint32_t *d_word_off = nullptr;  // per bitmap word: set bits before it in its 2048-word block
+  uint32_t *d_block_off = nullptr; // per 2048-word block: set bits before it
   uint32_t *d_counters = nullptr;  // [0] deferred items, [1] candidates, [2] error flags, [3] spare,
                                    // [4, 4 + n_ranges) tile claim counters of the persistent bank
   int n_ranges = 1;                // tile ranges of the persistent bank (one per SM)

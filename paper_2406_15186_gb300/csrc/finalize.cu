@@ -4,8 +4,12 @@
 //
 // The search kernel leaves, for every (segment, width) whose maximum reached
 // T_w, a 64-bit key (power bits << 32 | ~bin) in its slot and sets the slot's
-// bit in a dirty bitmap.  This kernel scans the bitmap (one word per warp,
-// one slot per lane, grid-stride), visits the slots whose bits are set, converts each to a
+// bit in a dirty bitmap.  Every set bit is one record, so an exclusive scan
+// of the words' bit counts (word_scan_kernel per 2048-word block, then
+// block_scan_kernel over the blocks) gives each record its place in slot
+// order -- (series, segment, width) in the plan's layout -- and the total.
+// The finaliser then scans the bitmap (one word per warp, one slot per
+// lane, grid-stride), visits the slots whose bits are set, converts each to a
 // record, computes
 // ln p = ln Q(a, S) + ln n_trials (Bonferroni, capped at 0; a = w, or
 // H(H+1)/2 w for the H-harmonic sum of §2.3) and the
@@ -21,8 +25,75 @@ namespace ps {
 
 namespace {
 
+constexpr int kScanThreads = 256;
+constexpr int kWordsPerThread = 8;
+constexpr int kWordsPerBlock = kScanThreads * kWordsPerThread;
+
+// word_off[j] = set bits in the words before j within its 2048-word block;
+// block_tot[b] = set bits of block b.
+__global__ void __launch_bounds__(kScanThreads) word_scan_kernel(const uint32_t *__restrict__ dirty, int64_t n_words,
+                                                                  uint32_t *__restrict__ word_off,
+                                                                  uint32_t *__restrict__ block_tot) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  const int64_t j0 = blockIdx.x * static_cast<int64_t>(kWordsPerBlock) + threadIdx.x * kWordsPerThread;
+  uint32_t c[kWordsPerThread];
+  uint32_t mine = 0;
+#pragma unroll
+  for (int k = 0; k < kWordsPerThread; ++k) {
+    c[k] = (j0 + k < n_words) ? static_cast<uint32_t>(__popc(dirty[j0 + k])) : 0u;
+    mine += c[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint32_t base = incl - mine;
+  for (int v = 0; v < warp; ++v) base += wsum[v];
+#pragma unroll
+  for (int k = 0; k < kWordsPerThread; ++k) {
+    if (j0 + k < n_words) word_off[j0 + k] = base;
+    base += c[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) block_tot[blockIdx.x] = base;
+}
+
+// In-place exclusive scan of the block totals (one CTA); counters[1] = total.
+__global__ void __launch_bounds__(1024) block_scan_kernel(uint32_t *__restrict__ block_tot, int64_t n_blocks,
+                                                           uint32_t *__restrict__ counters) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t b0 = 0; b0 < n_blocks; b0 += blockDim.x) {
+    const int64_t b = b0 + threadIdx.x;
+    const uint32_t v = (b < n_blocks) ? block_tot[b] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t base = carry + incl - v;
+    for (int w = 0; w < warp; ++w) base += wsum[w];
+    if (b < n_blocks) block_tot[b] = base;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = base + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) counters[1] = carry;
+}
+
 __global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty,
-                                int64_t n_words, uint32_t *__restrict__ counters, int W,
+                                int64_t n_words, const uint32_t *__restrict__ word_off,
+                                const uint32_t *__restrict__ block_off, int W,
                                 const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
                                 int n_series, const double *__restrict__ ln_trials,
                                 const float *__restrict__ gtab,
@@ -39,11 +110,9 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t
     const bool mine = (bits >> lane) & 1u;
     const uint64_t idx = static_cast<uint64_t>(j) * 32u + static_cast<uint64_t>(lane);
     const unsigned long long key = mine ? slots[idx] : 0ull;
-    // one output reservation per warp (the word's set bits), not per record
-    const unsigned act = __ballot_sync(0xffffffffu, key != 0ull);
-    uint32_t base = 0;
-    if (lane == 0 && act) base = atomicAdd(counters + 1, static_cast<uint32_t>(__popc(act)));
-    base = __shfl_sync(0xffffffffu, base, 0);
+    // the word's place in slot order, from the scans
+    const unsigned act = bits;
+    const uint32_t base = block_off[j / kWordsPerBlock] + word_off[j];
     if (key == 0ull) continue;
     slots[idx] = 0ull;
     const int64_t gseg = static_cast<int64_t>(idx / static_cast<uint64_t>(W));
@@ -80,8 +149,14 @@ __global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t
 
 int launch_finalize(pulscan_plan p, cudaStream_t s) {
   const int64_t words = (p->total_seg * static_cast<int64_t>(p->z_max) + 31) / 32;
+  const int64_t blocks = (words + kWordsPerBlock - 1) / kWordsPerBlock;
+  word_scan_kernel<<<static_cast<unsigned>(blocks), kScanThreads, 0, s>>>(p->d_dirty, words, p->d_word_off,
+                                                                           p->d_block_off);
+  PS_CUDA(cudaGetLastError());
+  block_scan_kernel<<<1, 1024, 0, s>>>(p->d_block_off, blocks, p->d_counters);
+  PS_CUDA(cudaGetLastError());
   const int grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>((words + 7) / 8, 1), 2432));
-  finalize_kernel<<<grid, 256, 0, s>>>(p->d_slots, p->d_dirty, words, p->d_counters, p->z_max, p->d_series,
+  finalize_kernel<<<grid, 256, 0, s>>>(p->d_slots, p->d_dirty, words, p->d_word_off, p->d_block_off, p->z_max, p->d_series,
                                        p->d_seg_off, static_cast<int>(p->series.size()), p->d_ln_trials,
                                        p->d_gtab, p->d_cands, static_cast<uint32_t>(p->max_cands));
   PS_CUDA(cudaGetLastError());

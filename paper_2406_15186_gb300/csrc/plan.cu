@@ -117,7 +117,7 @@ static void free_plan(pulscan_plan p) {
   void *ptrs[] = {p->d_series, p->d_tile_off, p->d_seg_off, p->d_thresh, p->d_thresh_bound, p->d_ln_trials,
                   p->d_stats,  p->d_slots,    p->d_dirty,   p->d_counters, p->d_cands,     p->own_x,
                   p->own_spec, p->own_power, p->d_items, p->d_snaps,    p->d_gtab,     p->d_x_off,
-                  p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec,   p->d_ranges,  p->d_searched};
+                  p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec,   p->d_ranges,  p->d_searched, p->d_word_off, p->d_block_off};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (auto &e : p->ev)
@@ -267,6 +267,7 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
       ok(dalloc(&p->d_thresh, ns * z_max)) && ok(dalloc(&p->d_thresh_bound, ns * z_max)) &&
       ok(dalloc(&p->d_ln_trials, ns)) && ok(dalloc(&p->d_stats, 4 * sg)) &&
       ok(dalloc(&p->d_slots, total_slots)) && ok(dalloc(&p->d_dirty, dirty_words)) &&
+      ok(dalloc(&p->d_word_off, dirty_words)) && ok(dalloc(&p->d_block_off, dirty_words / 2048 + 1)) &&
       ok(dalloc(&p->d_counters, 4 + static_cast<size_t>(n_sm))) && ok(dalloc(&p->d_cands, p->max_cands)) &&
       ok(dalloc(&p->d_items, p->item_cap)) && ok(dalloc(&p->d_snaps, p->item_cap * kR * 32)) &&
       ok(dalloc(&p->d_gtab, static_cast<size_t>(numharm) * z_max)) && ok(dalloc(&p->d_x_off, ns)) &&
@@ -574,7 +575,9 @@ int pulscan_candidates(pulscan_plan p, pulscan_cand *h_out, int64_t cap, int64_t
                   static_cast<uint64_t>(seg),
               (static_cast<uint64_t>(c.width) << 32) | static_cast<uint64_t>(i)};
   }
-  std::sort(key.begin(), key.end());
+  // the finaliser writes slot order, which is this order whenever the
+  // layout keeps the caller's series order; sort only otherwise
+  if (!std::is_sorted(key.begin(), key.end())) std::sort(key.begin(), key.end());
   const int64_t ncopy = std::min<int64_t>(have, cap);
   for (int64_t i = 0; i < ncopy; ++i) {
     h_out[i] = tmp[key[i].second & 0xffffffffull];

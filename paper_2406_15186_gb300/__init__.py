@@ -56,6 +56,9 @@ _SIGS = {
     "pulscan_plan_set_widths": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "pulscan_plan_set_rblock": (ctypes.c_int, [_P, ctypes.c_int64]),
     "pulscan_plan_set_fidelity": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "pulscan_plan_autotune": (ctypes.c_int, [_P, _P, _P]),
+    "pulscan_plan_tiling": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "pulscan_plan_set_tiling": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "pulscan_plan_thresholds": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pulscan_rfft": (ctypes.c_int, [_P, _P, _P, _P]),
     "pulscan_power_normalise": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -199,6 +202,19 @@ class Plan:
     def set_fidelity(self, mode):
         """FIDELITY_EXACT (default) or FIDELITY_PAPER_GPU (median of medians + polynomial log p)."""
         _check(load().pulscan_plan_set_fidelity(self._h, int(mode)))
+
+    def autotune(self, d_power, stream=None):
+        """Pick the bank's warps per CTA and launch form by timing the search on d_power."""
+        _check(load().pulscan_plan_autotune(self._h, _ptr(d_power), _stream(stream)))
+        return self.tiling()
+
+    def set_tiling(self, warps, persistent=-1):
+        _check(load().pulscan_plan_set_tiling(self._h, int(warps), int(persistent)))
+
+    def tiling(self):
+        w, m = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().pulscan_plan_tiling(self._h, ctypes.byref(w), ctypes.byref(m)))
+        return w.value, m.value
 
     def set_rblock(self, block_width):
         """Report block indices floor(bin / block_width) instead of bins (0: exact bins)."""

@@ -685,7 +685,8 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
   // needs all its resident warps busy for full issue and a persistent grid
   // would run its last round with fewer CTAs per SM
   const int pg0 = p->persist_grid[search ? 0 : 1];
-  const int pg = (pg0 > 0 && p->total_tiles >= 3LL * pg0) ? pg0 : 0;
+  const bool persist = p->persist_mode < 0 ? p->total_tiles >= 3LL * pg0 : p->persist_mode > 0;
+  const int pg = (pg0 > 0 && persist) ? pg0 : 0;
   uint32_t *ctr = pg > 0 ? p->d_counters + 4 : nullptr;
   const dim3 grid(static_cast<unsigned>(pg > 0 ? std::min<int64_t>(p->total_tiles, pg) : p->total_tiles));
   const dim3 block(32 * p->search_warps);

@@ -138,11 +138,12 @@ struct pulscan_plan_s {
   uint32_t *d_dirty = nullptr;     // one bit per slot touched by the search, 0 at rest
   uint32_t *d_word_off = nullptr;  // per bitmap word: set bits before it in its 2048-word block
   uint32_t *d_block_off = nullptr; // per 2048-word block: set bits before it
-  uint32_t *d_counters = nullptr;  // [0] deferred items, [1] candidates, [2] error flags, [3] spare,
+  uint32_t *d_counters = nullptr;  // [0] deferred items, [1] candidates, [2] error flags, [3] finaliser scan,
                                    // [4, 4 + n_ranges) tile claim counters of the persistent bank
   int n_ranges = 1;                // tile ranges of the persistent bank (one per SM)
   int64_t *d_ranges = nullptr;     // their first tiles, n_ranges + 1 entries
   int persist_grid[2] = {0, 0};    // persistent bank grid: [0] search, [1] maxima (0: one CTA per tile)
+  int persist_mode = -1;           // -1: persistent for grids of >= 3 waves; 0: never; 1: always
   unsigned long long *d_items = nullptr;  // deferred boxcar blocks
   float *d_snaps = nullptr;        // their running-sum snapshots (33 x 32 floats each)
   int64_t item_cap = 0;           // deferred items in use (<= alloc_item_cap)

@@ -5,8 +5,8 @@
 // The search kernel leaves, for every (segment, width) whose maximum reached
 // T_w, a 64-bit key (power bits << 32 | ~bin) in its slot and sets the slot's
 // bit in a dirty bitmap.  Every set bit is one record, so an exclusive scan
-// of the words' bit counts (word_scan_kernel per 2048-word block, then
-// block_scan_kernel over the blocks) gives each record its place in slot
+// of the words' bit counts (word_scan_kernel: per 2048-word block, then the
+// last block over the block totals) gives each record its place in slot
 // order -- (series, segment, width) in the plan's layout -- and the total.
 // The finaliser then scans the bitmap (one word per warp, one slot per
 // lane, grid-stride), visits the slots whose bits are set, converts each to a
@@ -30,11 +30,16 @@ constexpr int kWordsPerThread = 8;
 constexpr int kWordsPerBlock = kScanThreads * kWordsPerThread;
 
 // word_off[j] = set bits in the words before j within its 2048-word block;
-// block_tot[b] = set bits of block b.
+// block_off[b] = set bits of the blocks before b.  Each CTA scans its block
+// and publishes its total; the CTA that finishes last (a counter, no
+// waiting) scans the totals in place and writes the record count to
+// counters[1], then resets the counter for the next search.
 __global__ void __launch_bounds__(kScanThreads) word_scan_kernel(const uint32_t *__restrict__ dirty, int64_t n_words,
                                                                   uint32_t *__restrict__ word_off,
-                                                                  uint32_t *__restrict__ block_tot) {
+                                                                  uint32_t *__restrict__ block_off,
+                                                                  uint32_t *__restrict__ counters) {
   __shared__ uint32_t wsum[kScanThreads / 32];
+  __shared__ uint32_t last;
   const int64_t j0 = blockIdx.x * static_cast<int64_t>(kWordsPerBlock) + threadIdx.x * kWordsPerThread;
   uint32_t c[kWordsPerThread];
   uint32_t mine = 0;
@@ -59,36 +64,41 @@ __global__ void __launch_bounds__(kScanThreads) word_scan_kernel(const uint32_t 
     if (j0 + k < n_words) word_off[j0 + k] = base;
     base += c[k];
   }
-  if (threadIdx.x == kScanThreads - 1) block_tot[blockIdx.x] = base;
-}
-
-// In-place exclusive scan of the block totals (one CTA); counters[1] = total.
-__global__ void __launch_bounds__(1024) block_scan_kernel(uint32_t *__restrict__ block_tot, int64_t n_blocks,
-                                                           uint32_t *__restrict__ counters) {
-  __shared__ uint32_t wsum[32];
+  if (threadIdx.x == kScanThreads - 1) {
+    block_off[blockIdx.x] = base;
+    __threadfence();
+    last = (atomicAdd(counters + 3, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  // the last CTA: exclusive scan of the block totals
+  __threadfence();
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0u;
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n_blocks = gridDim.x;
   for (int64_t b0 = 0; b0 < n_blocks; b0 += blockDim.x) {
-    const int64_t b = b0 + threadIdx.x;
-    const uint32_t v = (b < n_blocks) ? block_tot[b] : 0u;
-    uint32_t incl = v;
+    const int64_t bb = b0 + threadIdx.x;
+    const uint32_t v = (bb < n_blocks) ? __ldcg(block_off + bb) : 0u;
+    uint32_t in2 = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
+      const uint32_t u = __shfl_up_sync(0xffffffffu, in2, o);
+      if (lane >= o) in2 += u;
     }
-    if (lane == 31) wsum[warp] = incl;
+    if (lane == 31) wsum[warp] = in2;
     __syncthreads();
-    uint32_t base = carry + incl - v;
-    for (int w = 0; w < warp; ++w) base += wsum[w];
-    if (b < n_blocks) block_tot[b] = base;
+    uint32_t bs = carry + in2 - v;
+    for (int w = 0; w < warp; ++w) bs += wsum[w];
+    if (bb < n_blocks) block_off[bb] = bs;
     __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = base + v;
+    if (threadIdx.x == blockDim.x - 1) carry = bs + v;
     __syncthreads();
   }
-  if (threadIdx.x == 0) counters[1] = carry;
+  if (threadIdx.x == 0) {
+    counters[1] = carry;
+    counters[3] = 0u;
+  }
 }
 
 __global__ void finalize_kernel(unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty,
@@ -151,9 +161,7 @@ int launch_finalize(pulscan_plan p, cudaStream_t s) {
   const int64_t words = (p->total_seg * static_cast<int64_t>(p->z_max) + 31) / 32;
   const int64_t blocks = (words + kWordsPerBlock - 1) / kWordsPerBlock;
   word_scan_kernel<<<static_cast<unsigned>(blocks), kScanThreads, 0, s>>>(p->d_dirty, words, p->d_word_off,
-                                                                           p->d_block_off);
-  PS_CUDA(cudaGetLastError());
-  block_scan_kernel<<<1, 1024, 0, s>>>(p->d_block_off, blocks, p->d_counters);
+                                                                           p->d_block_off, p->d_counters);
   PS_CUDA(cudaGetLastError());
   const int grid = static_cast<int>(std::min<int64_t>(std::max<int64_t>((words + 7) / 8, 1), 2432));
   finalize_kernel<<<grid, 256, 0, s>>>(p->d_slots, p->d_dirty, words, p->d_word_off, p->d_block_off, p->z_max, p->d_series,

@@ -147,6 +147,50 @@ static int check_shape(int64_t n, int32_t z_max, int32_t seg_len, double sigma) 
   return PULSCAN_OK;
 }
 
+// Device copies of the series table, the tile offsets and the per-SM tile
+// ranges (after the layout or the tile width changed).
+static int upload_layout(pulscan_plan p) {
+  const size_t ns = p->series.size();
+  std::vector<SeriesDev> sd(ns);
+  std::vector<int64_t> to(ns + 1), so(ns + 1);
+  for (size_t i = 0; i < ns; ++i) {
+    const Series &s = p->series[i];
+    sd[i] = SeriesDev{s.m, s.n_seg, s.p_off, s.spec_off, s.seg_off, s.tile_off, s.user_index, s.harm};
+    to[i] = s.tile_off;
+    so[i] = s.seg_off;
+  }
+  to[ns] = p->total_tiles;
+  so[ns] = p->total_seg;
+  PS_CUDA(cudaMemcpy(p->d_series, sd.data(), ns * sizeof(SeriesDev), cudaMemcpyHostToDevice));
+  PS_CUDA(cudaMemcpy(p->d_tile_off, to.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  PS_CUDA(cudaMemcpy(p->d_seg_off, so.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  std::vector<int64_t> rl(static_cast<size_t>(p->n_ranges) + 1);
+  for (int r = 0; r <= p->n_ranges; ++r) rl[r] = p->total_tiles * r / p->n_ranges;   // equal ranges, one per SM
+  PS_CUDA(cudaMemcpy(p->d_ranges, rl.data(), rl.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  return PULSCAN_OK;
+}
+
+// Re-tile the bank with `warps` warps per CTA (tile = 1056 x warps bins).
+static int relayout_tiles(pulscan_plan p, int warps) {
+  p->search_warps = warps;
+  const int64_t tb = search_tile_bins(warps);
+  int64_t tl = 0;
+  for (auto &se : p->series) {
+    se.tile_off = tl;
+    tl += (se.m + tb - 1) / tb;
+  }
+  p->total_tiles = tl;
+  const int64_t nb = (p->z_max + kR - 1) / kR;
+  p->item_cap = std::min<int64_t>(std::min<int64_t>(tl * warps * nb, 65536), p->alloc_item_cap);
+  int rc = upload_layout(p);
+  if (!rc) rc = prepare_bank(p);
+  if (p->graph.exec) {
+    cudaGraphExecDestroy(p->graph.exec);
+    p->graph.exec = nullptr;
+  }
+  return rc;
+}
+
 static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_series, int32_t z_max,
                       int32_t seg_len, double sigma, int32_t numharm = 1) {
   if (!out) return fail(PULSCAN_ERR_INVALID_ARG, "null plan pointer");
@@ -273,17 +317,8 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
       ok(dalloc(&p->d_gtab, static_cast<size_t>(numharm) * z_max)) && ok(dalloc(&p->d_x_off, ns)) &&
       ok(dalloc(&p->d_x_len, ns)) &&
       ok(dalloc(&p->d_ranges, static_cast<size_t>(n_sm) + 1)) && ok(dalloc(&p->d_searched, z_max))) {
-    std::vector<SeriesDev> sd(ns);
-    std::vector<int64_t> to(ns + 1), so(ns + 1);
-    for (size_t i = 0; i < ns; ++i) {
-      const Series &s = p->series[i];
-      sd[i] = SeriesDev{s.m, s.n_seg, s.p_off, s.spec_off, s.seg_off, s.tile_off, s.user_index, s.harm};
-      to[i] = s.tile_off;
-      so[i] = s.seg_off;
-    }
-    to[ns] = tl;
-    so[ns] = sg;
-    ok(cuda_ok_or(cudaMemcpy(p->d_series, sd.data(), ns * sizeof(SeriesDev), cudaMemcpyHostToDevice)));
+    p->n_ranges = n_sm;
+    ok(upload_layout(p));
     std::vector<int64_t> xo(ns), xl(ns);
     for (size_t i = 0; i < ns; ++i) {
       xo[i] = p->series[i].x_off;
@@ -291,15 +326,9 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
     }
     ok(cuda_ok_or(cudaMemcpy(p->d_x_off, xo.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(cuda_ok_or(cudaMemcpy(p->d_x_len, xl.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice)));
-    ok(cuda_ok_or(cudaMemcpy(p->d_tile_off, to.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)));
-    ok(cuda_ok_or(cudaMemcpy(p->d_seg_off, so.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(cuda_ok_or(cudaMemset(p->d_slots, 0, total_slots * sizeof(unsigned long long))));
     ok(cuda_ok_or(cudaMemset(p->d_dirty, 0, dirty_words * sizeof(uint32_t))));
-    p->n_ranges = n_sm;
     ok(cuda_ok_or(cudaMemset(p->d_counters, 0, (4 + static_cast<size_t>(n_sm)) * sizeof(uint32_t))));
-    std::vector<int64_t> rl(static_cast<size_t>(n_sm) + 1);
-    for (int r = 0; r <= n_sm; ++r) rl[r] = tl * r / n_sm;   // equal contiguous tile ranges, one per SM
-    ok(cuda_ok_or(cudaMemcpy(p->d_ranges, rl.data(), rl.size() * sizeof(int64_t), cudaMemcpyHostToDevice)));
     ok(upload_thresholds(p));
     std::vector<float> gt(static_cast<size_t>(numharm) * z_max);
     for (int h = 1; h <= numharm; ++h)
@@ -450,6 +479,71 @@ int pulscan_plan_set_fidelity(pulscan_plan p, int32_t mode) {
     cudaGraphExecDestroy(p->graph.exec);
     p->graph.exec = nullptr;
   }
+  return PULSCAN_OK;
+}
+
+static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s);
+
+int pulscan_plan_autotune(pulscan_plan p, const float *d_power, pulscan_stream stream) {
+  if (!p || !d_power) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(d_power)) return fail(PULSCAN_ERR_INVALID_ARG, "power buffer must be 16-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool timing = p->timing;
+  p->timing = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PS_CUDA(cudaEventCreate(&e0));
+  PS_CUDA(cudaEventCreate(&e1));
+  float best = INFINITY;
+  int best_w = p->search_warps, best_m = p->persist_mode;
+  int rc = PULSCAN_OK;
+  for (int w : {1, 2, 4}) {
+    rc = relayout_tiles(p, w);
+    for (int mode : {0, 1}) {
+      if (rc) break;
+      p->persist_mode = mode;
+      rc = search_impl(p, d_power, s);   // warm-up (and the kernels' first-use costs)
+      float tot = 0.0f;
+      for (int r = 0; r < 3 && !rc; ++r) {
+        cudaEventRecord(e0, s);
+        rc = search_impl(p, d_power, s);
+        cudaEventRecord(e1, s);
+        float ms = 0.0f;
+        if (!rc && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+          tot += ms;
+        else if (!rc)
+          rc = fail(PULSCAN_ERR_CUDA, "event timing failed");
+      }
+      if (!rc && tot < best) {
+        best = tot;
+        best_w = w;
+        best_m = mode;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->persist_mode = best_m;
+  const int rc2 = relayout_tiles(p, best_w);
+  PS_CUDA(cudaMemsetAsync(p->d_counters, 0, (4 + static_cast<size_t>(p->n_ranges)) * sizeof(uint32_t), s));
+  PS_CUDA(cudaStreamSynchronize(s));
+  p->timing = timing;
+  return rc ? rc : rc2;
+}
+
+int pulscan_plan_set_tiling(pulscan_plan p, int32_t warps, int32_t persistent) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  if (warps != 1 && warps != 2 && warps != 4) return fail(PULSCAN_ERR_INVALID_ARG, "warps must be 1, 2 or 4");
+  if (persistent < -1 || persistent > 1) return fail(PULSCAN_ERR_INVALID_ARG, "persistent must be -1, 0 or 1");
+  PS_CUDA(cudaDeviceSynchronize());
+  p->persist_mode = persistent;
+  return relayout_tiles(p, warps);
+}
+
+int pulscan_plan_tiling(pulscan_plan p, int32_t *warps, int32_t *persistent) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  if (warps) *warps = p->search_warps;
+  if (persistent) *persistent = p->persist_mode;
   return PULSCAN_OK;
 }
 

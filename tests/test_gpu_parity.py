@@ -221,3 +221,34 @@ def test_rblock_reports_block_index(pkg):
     assert np.array_equal(approx["bin"], exact["bin"] // 1000)
     for f in ("series", "width", "power", "sigma"):
         assert np.array_equal(approx[f], exact[f])
+
+
+@pytest.mark.parametrize("warps,persistent", [(1, 1), (2, 1), (4, 1), (1, 0), (4, 0)])
+def test_launch_shapes_give_the_same_search(pkg, warps, persistent):
+    """Every tile width and both launch forms (one CTA per tile; persistent
+    per-SM tile ranges with stealing) against the oracle on one input."""
+    n, w_max, seg_len, sigma = 1 << 18, 48, 1024, 2.5
+    x = _series(n, seed=12)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    plan.set_tiling(warps, persistent)
+    assert plan.tiling() == (warps, persistent)
+    out = parity.run_gpu(plan, x)
+    m = n // 2 + 1
+    p64 = out["power"][:m].astype(np.float64)
+    mx_ref, am_ref = parity.check_maxima(p64, out["mx"], out["am"], w_max, seg_len)
+    parity.check_candidates(out["cands"], p64, mx_ref, am_ref, w_max, seg_len, sigma,
+                            parity.n_trials_of(m, w_max))
+
+
+def test_autotune_keeps_the_candidates(pkg):
+    n, w_max, seg_len, sigma = 1 << 18, 64, 1024, 3.0
+    x = _series(n, seed=13)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    before = parity.run_gpu(plan, x, maxima=False)
+    d_power = torch.from_numpy(before["power"]).cuda()
+    warps, persistent = plan.autotune(d_power)
+    assert warps in (1, 2, 4) and persistent in (0, 1)
+    after = parity.run_gpu(plan, x, maxima=False)
+    assert len(after["cands"]) == len(before["cands"]) > 0
+    for f in ("series", "width", "bin", "power", "sigma"):
+        assert np.array_equal(np.sort(after["cands"][f]), np.sort(before["cands"][f]))

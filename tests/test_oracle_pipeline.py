@@ -67,3 +67,17 @@ def test_rblock_reports_block_indices():
     for a, b in zip(exact, block):
         assert b["bin"] == a["bin"] // 100
         assert {k: v for k, v in a.items() if k != "bin"} == {k: v for k, v in b.items() if k != "bin"}
+
+
+def test_smoke_case_gives_candidates_clear_of_the_threshold():
+    """The smoke run compares GPU candidates with the oracle's: its input must
+    give candidates, most of them far above the threshold (CPU, FP64 FFT)."""
+    import __graft_entry__ as ge
+    from oracle import fft as offt
+    from oracle import normalise as onorm
+    x, n, w_max, seg_len, sigma = ge.smoke_input()
+    p, _, flags = onorm.normalise_power(offt.rfft(np.asarray(x, dtype=np.float64)), seg_len)
+    assert not flags.any()
+    ref = pipeline.search_power(p, w_max, seg_len, sigma)
+    assert len(ref) >= 20
+    assert max(r["sigma"] for r in ref) > 2 * sigma

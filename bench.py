@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-series batched measurement")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable 4096-binary measurement")
+    ap.add_argument("--tiling", default=None, metavar="WARPS,PERSISTENT",
+                    help="bank launch shape of the single-series plan instead of the autotuner (e.g. 4,0)")
     return ap.parse_args()
 
 
@@ -480,12 +482,18 @@ def run_ours(args, rank, world, local):
         plan.boxcar_search(d_power, stream=stream)
 
     step()
-    tiling = plan.autotune(d_power, stream=stream)     # launch shape of the bank, timed on this input
+    if args.tiling:
+        plan.set_tiling(*[int(v) for v in args.tiling.split(",")])
+        tiling, tiling_by = plan.tiling(), "--tiling"
+    else:
+        tiling = plan.autotune(d_power, stream=stream)     # launch shape of the bank, timed on this input
+        tiling_by = "pulscan_plan_autotune"
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
             flush.zero_()
         step()
     n_cands = len(plan.candidates(stream=stream))
+    n_deferred = plan.counters()[0]      # blocks the bank handed to the deferred kernel
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -579,12 +587,12 @@ def run_ours(args, rank, world, local):
             "config": {"workload": f"{WORKLOAD}: N=2^23 samples (M=4194305 bins), 8 drifting tones, "
                                    f"z_max=1024, segment_len=4096, sigma=6",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                       "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "by": "pulscan_plan_autotune"},
+                       "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "by": tiling_by},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "kernels_ms": {"rfft_cufft": statistics.mean(k_fft), "normalise": statistics.mean(k_norm),
                            "boxcar_search": statistics.mean(k_search), "deferred_blocks": statistics.mean(k_def),
                            "finalise": statistics.mean(k_fin)},
-            "candidates": n_cands,
+            "candidates": n_cands, "deferred_blocks": n_deferred,
             "width_sampling": dict(sampling, note="boxcar + deferred + finalise per step; all widths summed, "
                                                   "only the sampled ones compared (z mod 8 == 0; z a power of two)"),
             "harmonics": harmonic,

@@ -184,7 +184,7 @@ PULSCAN_API int pulscan_plan_set_fidelity(pulscan_plan plan, int32_t mode);
 
 /* Autotuner of the bank's launch shape: runs the search (bank, deferred
  * blocks, finaliser) on the caller's normalised power d_power three times for
- * each of 1, 2 and 4 warps per CTA (tile = 1056 x warps bins) with one CTA
+ * each of 1, 2, 3 and 4 warps per CTA (tile = 1056 x warps bins) with one CTA
  * per tile and with a persistent grid of per-SM tile ranges, and keeps the
  * fastest.  Segment length, widths and halo are fixed by the search itself,
  * so the candidates do not depend on the choice.  Synchronises `stream`,
@@ -193,7 +193,7 @@ PULSCAN_API int pulscan_plan_set_fidelity(pulscan_plan plan, int32_t mode);
  * automatic, the default; 0 one CTA per tile; 1 persistent). */
 PULSCAN_API int pulscan_plan_autotune(pulscan_plan plan, const float *d_power, pulscan_stream stream);
 PULSCAN_API int pulscan_plan_tiling(pulscan_plan plan, int32_t *warps, int32_t *persistent);
-/* Set the launch shape directly (warps 1, 2 or 4; persistent -1, 0 or 1).
+/* Set the launch shape directly (warps 1 to 4; persistent -1, 0 or 1).
  * Synchronises the device.  Errors: INVALID_ARG. */
 PULSCAN_API int pulscan_plan_set_tiling(pulscan_plan plan, int32_t warps, int32_t persistent);
 

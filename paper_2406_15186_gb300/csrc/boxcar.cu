@@ -1,7 +1,7 @@
 // Boxcar filter bank + per-(segment, width) maximum (paper §2.2.5 and
 // Algorithm 4), GB300 design.
 //
-// Work decomposition: a CTA of 1, 2 or 4 warps owns a tile of 1056 bins per
+// Work decomposition: a CTA of 1 to 4 warps owns a tile of 1056 bins per
 // warp (consecutive start bins of one series); lane l of warp v owns the
 // kR = 33 start bins k0 .. k0+32, k0 = tile + 33 (32 v + l).  The tile plus its halo
 // of z_max bins is staged into shared memory by one TMA bulk copy.  Each lane

@@ -496,7 +496,7 @@ int pulscan_plan_autotune(pulscan_plan p, const float *d_power, pulscan_stream s
   float best = INFINITY;
   int best_w = p->search_warps, best_m = p->persist_mode;
   int rc = PULSCAN_OK;
-  for (int w : {1, 2, 4}) {
+  for (int w : {1, 2, 3, 4}) {
     rc = relayout_tiles(p, w);
     for (int mode : {0, 1}) {
       if (rc) break;
@@ -533,7 +533,7 @@ int pulscan_plan_autotune(pulscan_plan p, const float *d_power, pulscan_stream s
 
 int pulscan_plan_set_tiling(pulscan_plan p, int32_t warps, int32_t persistent) {
   if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
-  if (warps != 1 && warps != 2 && warps != 4) return fail(PULSCAN_ERR_INVALID_ARG, "warps must be 1, 2 or 4");
+  if (warps < 1 || warps > 4) return fail(PULSCAN_ERR_INVALID_ARG, "warps must be 1, 2, 3 or 4");
   if (persistent < -1 || persistent > 1) return fail(PULSCAN_ERR_INVALID_ARG, "persistent must be -1, 0 or 1");
   PS_CUDA(cudaDeviceSynchronize());
   p->persist_mode = persistent;

@@ -449,22 +449,39 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
   }
 }
 
-// Deferred blocks, one CTA of four warps per work item.  The item is the
-// 32 x 33 x 33 block (lanes x bins x widths) one warp of the search kernel
-// left, with its 33 x 32 running sums saved in a snapshot.  Warp q takes bins
-// [kSplit[q], kSplit[q + 1]) of every lane's 33 (9 + 8 + 8 + 8), so each thread
-// carries at most 9 running sums through the block's remaining widths and the
-// serial chain per item is a quarter of one warp doing it all.  The P window
-// (32 x 33 bins plus the 66-bin reach of one block) is staged in shared
-// memory.  Phase 1: per step each thread forms the best key of its bins in
-// each segment part, and only when that reaches T_w (rare) merges it into
-// keys[part][lane][step] with a shared 64-bit max.  Phase 2: one thread per
-// width merges the 32 lanes' keys segment by segment and sends every maximum
-// to its slot.
+// Deferred blocks, one CTA of three warps per work item.  The item is the
+// block of 32 x 33 = 1056 consecutive start bins x 33 widths that one warp of
+// the search kernel left, with the 1056 running sums saved in a snapshot.
+// Thread t carries the sums of bins 11t .. 11t + 10 of the block through its
+// remaining widths -- the same adds in the same order as the search kernel,
+// so the sums are bit-identical -- and after each step stores the best of its
+// eleven sums (a max tree) and the first of its bins holding it; the window
+// values come from an 11-register ring (one shared-memory load per step), and
+// the step loop has no cross-thread work.  A thread whose bins straddle a
+// segment boundary keeps the two parts apart (a second best/bin pair); its
+// warp runs that variant, so no thread diverges.  Every 11 steps the three
+// warps merge the chunk's widths: lane l scans the three threads that cover
+// bins 33 l .. 33 l + 32 and keeps, per segment there (at most two), the
+// largest sum reaching T_w and its lowest bin; the second part moves to lane
+// l + 1 (whose segment it is), and the warp then reduces each segment it
+// holds with two 32-bit reductions (power bits, then bin) into one 64-bit
+// maximum per (segment, width).  A last pass sends every maximum to its slot.
+// The P window (1056 bins plus the 66-bin reach of one block) and the
+// snapshot are staged in shared memory.  Blocks at the very end of a series
+// (windows that leave the spectrum) take a plain per-step loop.
+constexpr int kDeferThreads = 96;
+constexpr int kDeferBins = 32 * kR / kDeferThreads;        // bins per thread (11)
+constexpr int kDeferWarps = kDeferThreads / 32;
+constexpr int kDeferChunk = 11;                             // steps per merge
 constexpr int kRegion = 32 * kR + 2 * kR;
-constexpr int kDeferWarps = 4;
-constexpr int kSubBins = 9;
-__constant__ int kSplit[kDeferWarps + 1] = {0, 9, 17, 25, 33};
+constexpr int kItemSegs = 32 * kR / (2 * kR) + 2;           // segments one item can touch (segment_len >= 66)
+static_assert(kDeferBins == 11 && kDeferChunk == 11, "the unrolled ring assumes 11 bins and 11 steps");
+static_assert(kDeferBins * kDeferThreads == 32 * kR, "the threads' bins cover the block");
+static_assert(kR % kDeferBins == 0 && kR / kDeferBins * 32 == kDeferThreads, "a lane's 33 bins are whole threads");
+constexpr int kThreadsPerLane = kR / kDeferBins;            // 3
+constexpr int kRegionLoads = (kRegion + kDeferThreads - 1) / kDeferThreads;
+constexpr int kSnapLoads = 32 * kR / kDeferThreads;
+static_assert(kSnapLoads * kDeferThreads == 32 * kR, "whole snapshot loads");
 
 __device__ __forceinline__ float max3f(float a, float b, float c) {
   float r;
@@ -472,44 +489,73 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
   return r;
 }
 
-// Key of the best of v[0..n) whose lane index i0 + j lies in [ia, ib), or 0
-// when that best is below T.  v[n..9) hold -1 (never a window sum).  In
-// deferred blocks most windows reach T, so the first-index search is a
-// branch-free equality mask.
-__device__ __forceinline__ unsigned long long sub_key(const float (&v)[kSubBins], int n, int i0, int ia, int ib,
-                                                      int64_t k0, float T) {
-  uint32_t in = 0x1ffu;   // bits j of v that lie in [ia, ib)
-  float m;
-  if (ia <= i0 && ib >= i0 + n) {
-    m = fmaxf(max3f(max3f(v[0], v[1], v[2]), max3f(v[3], v[4], v[5]), max3f(v[6], v[7], v[8])), -1.0f);
-  } else {
-    const int lo = max(ia - i0, 0), hi = min(ib - i0, n);
-    in = (hi > lo) ? (((1u << hi) - 1u) & ~((1u << lo) - 1u)) : 0u;
-    m = -1.0f;
-#pragma unroll
-    for (int j = 0; j < kSubBins; ++j) m = fmaxf(m, ((in >> j) & 1u) ? v[j] : -1.0f);
-  }
-  if (!(m >= T) || !(m >= 0.0f)) return 0ull;
-  uint32_t eq = 0u;
-#pragma unroll
-  for (int j = 0; j < kSubBins; ++j) eq |= (v[j] == m) ? (1u << j) : 0u;
-  eq &= in;
-  return slot_key(m, static_cast<uint32_t>(k0 + i0 + (__ffs(static_cast<int>(eq)) - 1)));
+__device__ __forceinline__ unsigned long long best_key(float v, uint32_t bin) {
+  return (static_cast<unsigned long long>(__float_as_uint(v)) << 32) |
+         static_cast<unsigned long long>(0xffffffffu - bin);
 }
 
-__global__ void __launch_bounds__(32 * kDeferWarps) deferred_kernel(
+__device__ __forceinline__ float max11(const float (&v)[kDeferBins]) {
+  return max3f(max3f(max3f(v[0], v[1], v[2]), max3f(v[3], v[4], v[5]), max3f(v[6], v[7], v[8])), v[9], v[10]);
+}
+
+// First j with v[j] == m (11 if none).
+__device__ __forceinline__ int first_of(const float (&v)[kDeferBins], float m) {
+  uint32_t eq = 0u;
+#pragma unroll
+  for (int j = 0; j < kDeferBins; ++j) eq |= (v[j] == m) ? (1u << j) : 0u;
+  return __ffs(static_cast<int>(eq | (1u << kDeferBins))) - 1;
+}
+
+struct DeferShared {
+  float region[kRegion];
+  float snap[kR * (32 + 1)];                    // [bin i][lane l], rows of 33
+  float cval[kDeferChunk][kDeferThreads];       // per step of the chunk: best sum of each thread (part A)
+  float cvalB[kDeferChunk][kDeferThreads];      // part B (bins past a segment boundary), -1 if none
+  uint8_t cidx[kDeferChunk][kDeferThreads];     // first bin within the thread holding it
+  uint8_t cidxB[kDeferChunk][kDeferThreads];
+  unsigned long long keys[kItemSegs][kR];
+  float tcache[kR];                             // T_w of the block's widths
+};
+
+// One chunk of 11 steps from the register ring rg (positions p of the chunk's
+// window rb[] in rg[p % 11]; on exit positions 11..21, i.e. the next chunk's
+// 0..10).  kSplit: bins from jc on form part B.
+template <bool kSplit>
+__device__ __forceinline__ void defer_chunk(float (&s)[kDeferBins], float (&rg)[kDeferBins],
+                                            const float *__restrict__ rb, int jc, DeferShared &sh, int t) {
+#pragma unroll
+  for (int u = 0; u < kDeferChunk; ++u) {
+#pragma unroll
+    for (int j = 0; j < kDeferBins; ++j) s[j] += rg[(u + j) % kDeferBins];
+    rg[u] = rb[u + kDeferBins];   // position u + 11 takes the slot of position u
+    if (!kSplit) {
+      const float best = max11(s);
+      sh.cval[u][t] = best;
+      sh.cidx[u][t] = static_cast<uint8_t>(first_of(s, best));
+    } else {
+      float va[kDeferBins], vb[kDeferBins];
+#pragma unroll
+      for (int j = 0; j < kDeferBins; ++j) {
+        va[j] = (j < jc) ? s[j] : -1.0f;
+        vb[j] = (j < jc) ? -1.0f : s[j];
+      }
+      const float ba = max11(va), bb = max11(vb);
+      sh.cval[u][t] = ba;
+      sh.cidx[u][t] = static_cast<uint8_t>(first_of(va, ba));
+      sh.cvalB[u][t] = bb;
+      sh.cidxB[u][t] = static_cast<uint8_t>(first_of(vb, bb));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kDeferThreads, 8) deferred_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
     int n_series, int W, int seg_len, const float *__restrict__ thr_all, unsigned long long *__restrict__ slots,
     uint32_t *__restrict__ dirty, const uint32_t *__restrict__ counters,
     const unsigned long long *__restrict__ items, const float *__restrict__ snaps, uint32_t item_cap,
     int tile_bins) {
-  __shared__ float region[kRegion];
-  // keys[part][lane][step]: lane-major so phase 2 reads are bank-conflict free
-  __shared__ unsigned long long keys[2][32][kR];
-  __shared__ long long segs[32];
-  __shared__ float tcache[kR];   // T_w of the block's widths
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = kSplit[warp], nb = kSplit[warp + 1] - i0;
+  __shared__ DeferShared sh;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t n_items = min(counters[0], item_cap);
   for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const unsigned long long item = items[it];
@@ -520,74 +566,154 @@ __global__ void __launch_bounds__(32 * kDeferWarps) deferred_kernel(
     const int si = series_of_tile(tile_off, n_series, tile);
     const SeriesDev S = series[si];
     const int64_t t0 = (tile - S.tile_off) * static_cast<int64_t>(tile_bins);
-    const int64_t r0 = t0 + wv * (32 * kR) + bi * kR + cx;   // first bin of the staged window
+    const int64_t k0 = t0 + wv * (32 * kR);             // first start bin of the block
+    const int64_t r0 = k0 + bi * kR + cx;               // first bin of the staged window
     const float *src = power + S.p_off;
-    __syncthreads();   // the previous item is finished with the shared arrays
-    for (int j = threadIdx.x; j < kRegion; j += blockDim.x) region[j] = (r0 + j < S.m) ? src[r0 + j] : 0.0f;
-    for (int j = threadIdx.x; j < 2 * 32 * kR; j += blockDim.x) (&keys[0][0][0])[j] = 0ull;
     const int nsteps = min(kR, W - bi * kR);
     const int wf = bi * kR + 1;
-    const float *thr = thr_all + static_cast<int64_t>(si) * W;
-    if (threadIdx.x < nsteps) tcache[threadIdx.x] = thr[wf - 1 + threadIdx.x];
-    const float *sp = snaps + static_cast<size_t>(it) * (kR * 32) + lane;
-    float v[kSubBins];
+    const int64_t seg_hi = S.n_seg - 1;
+    const int64_t g0 = min64(k0 / seg_len, seg_hi);     // series-relative segment of the first bin
+    const int n_segs = static_cast<int>(min64((k0 + 32 * kR - 1) / seg_len, seg_hi) - g0 + 1);
+    // all global loads of the item are issued before any is used (registers),
+    // so staging costs one memory latency, not one per loop trip
+    const float *sp = snaps + static_cast<size_t>(it) * (kR * 32);
+    float ld_r[kRegionLoads], ld_s[kSnapLoads];
 #pragma unroll
-    for (int j = 0; j < kSubBins; ++j) v[j] = (j < nb) ? sp[(i0 + j) * 32] : -1.0f;
-    const LaneCtx c = lane_ctx(S, t0, tile_bins, wv, lane, W, seg_len, slots, dirty);
-    if (warp == 0) segs[lane] = c.seg_a;
-    __syncthreads();
-    // lane_buf[w - 1 + i] addresses bin k0 + w - 1 + i of the window
-    const float *lane_buf = region + lane * kR - (bi * kR + cx);
-    const bool split = c.ib < kR;
-    // valid windows of the lane at width w: min(lim_tile, max(0, base - w))
-    const int base = static_cast<int>(min64(c.m + 1 - c.k0, static_cast<int64_t>(1) << 30));
-    for (int cc = cx; cc < nsteps; ++cc) {
-      const int w = wf + cc;
-      const float *pw = lane_buf + (w - 1) + i0;
-#pragma unroll
-      for (int j = 0; j < kSubBins - 1; ++j) v[j] += pw[j];
-      if (nb == kSubBins) v[kSubBins - 1] += pw[kSubBins - 1];
-      const int lim = min(c.lim_tile, max(0, base - w));
-      const float T = tcache[cc];
-      const unsigned long long ka = sub_key(v, nb, i0, 0, min(c.ib, lim), c.k0, T);
-      if (ka) atomicMax(&keys[0][lane][cc], ka);
-      if (split) {
-        const unsigned long long kb = sub_key(v, nb, i0, c.ib, lim, c.k0, T);
-        if (kb) atomicMax(&keys[1][lane][cc], kb);
-      }
+    for (int q = 0; q < kRegionLoads; ++q) {
+      const int j = t + q * kDeferThreads;
+      ld_r[q] = (j < kRegion && r0 + j < S.m) ? __ldg(src + r0 + j) : 0.0f;
     }
+#pragma unroll
+    for (int q = 0; q < kSnapLoads; ++q) ld_s[q] = sp[t + q * kDeferThreads];
+    const float thr_t = (t < nsteps) ? __ldg(thr_all + static_cast<int64_t>(si) * W + wf - 1 + t) : 0.0f;
+    __syncthreads();   // the previous item is finished with the shared arrays
+#pragma unroll
+    for (int q = 0; q < kRegionLoads; ++q) {
+      const int j = t + q * kDeferThreads;
+      if (j < kRegion) sh.region[j] = ld_r[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kSnapLoads; ++q) {
+      const int j = t + q * kDeferThreads;
+      sh.snap[(j >> 5) * 33 + (j & 31)] = ld_s[q];
+    }
+    for (int j = t; j < n_segs * kR; j += kDeferThreads) (&sh.keys[0][0])[j] = 0ull;
+#pragma unroll
+    for (int u = 0; u < kDeferChunk; ++u) sh.cvalB[u][t] = -1.0f;
+    if (t < nsteps) sh.tcache[t] = thr_t;
     __syncthreads();
-    // phase 2: thread -> width.  The lanes' segments are non-decreasing along
-    // (lane, part A, part B), so a running maximum is flushed whenever the
-    // segment changes.
-    const int cc = cx + static_cast<int>(threadIdx.x);
-    if (cc < nsteps) {
-      const int w = wf + cc;
-      int64_t cur = -1;
-      unsigned long long best = 0ull;
-      auto flush = [&]() {
-        if (best != 0ull) emit_slot<true>(slots, dirty, static_cast<uint64_t>(cur) * W + (w - 1), best);
-      };
-      for (int l = 0; l < 32; ++l) {
-        const int64_t sa = segs[l];
-        const unsigned long long ka = keys[0][l][cc];
-        if (sa != cur) {
-          flush();
-          cur = sa;
-          best = 0ull;
+
+    // this thread's bins b0 + j, b0 = 11 t (bin b of the block = lane b / 33's bin b % 33)
+    const int b0 = kDeferBins * t;
+    float s[kDeferBins];
+#pragma unroll
+    for (int j = 0; j < kDeferBins; ++j) s[j] = sh.snap[((b0 + j) % kR) * 33 + (b0 + j) / kR];
+    const int sg0 = static_cast<int>(min64((k0 + b0) / seg_len, seg_hi) - g0);
+    const int sg1 = static_cast<int>(min64((k0 + b0 + kDeferBins - 1) / seg_len, seg_hi) - g0);
+    // straddling thread: bins from jc on lie in segment sg1
+    const int jc = (sg1 != sg0) ? static_cast<int>((g0 + sg1) * seg_len - k0) - b0 : kDeferBins;
+    const bool split_warp = __any_sync(kFull, jc != kDeferBins);
+    // bin b has a whole window at width w iff b < base - w; all_valid: every
+    // bin of the block at every remaining width
+    const int64_t base = S.m + 1 - k0;
+    const bool all_valid = base - (wf + nsteps - 1) >= 32 * kR;
+    // merge lanes: lane l covers bins 33 l .. 33 l + 32, from segment segA on;
+    // bins from cut on lie in segA + 1
+    const int segA = static_cast<int>(min64((k0 + kR * lane) / seg_len, seg_hi) - g0);
+    const int cut = (g0 + segA < seg_hi) ? static_cast<int>((g0 + segA + 1) * seg_len - k0) : (1 << 30);
+
+    float rg[kDeferBins];
+    bool ring = false;
+    for (int c0 = cx; c0 < nsteps; c0 += kDeferChunk) {
+      const int c1 = min(c0 + kDeferChunk, nsteps);
+      if (all_valid && c1 - c0 == kDeferChunk) {
+        const float *rb = sh.region + (c0 - cx) + b0;
+        if (!ring) {
+#pragma unroll
+          for (int j = 0; j < kDeferBins; ++j) rg[j] = rb[j];
+          ring = true;
         }
-        best = max(best, ka);
-        const unsigned long long kb = keys[1][l][cc];
-        if (kb != 0ull) {
-          if (sa + 1 != cur) {
-            flush();
-            cur = sa + 1;
-            best = 0ull;
+        if (split_warp) defer_chunk<true>(s, rg, rb, jc, sh, t);
+        else defer_chunk<false>(s, rg, rb, jc, sh, t);
+      } else {
+        // windows leaving the spectrum (or a short last block): plain steps
+        for (int cc = c0; cc < c1; ++cc) {
+          const float *pw = sh.region + (cc - cx) + b0;
+          const int64_t lim = base - (wf + cc);
+          float va[kDeferBins], vb[kDeferBins];
+#pragma unroll
+          for (int j = 0; j < kDeferBins; ++j) {
+            s[j] += pw[j];
+            const bool ok = b0 + j < lim;
+            va[j] = (ok && j < jc) ? s[j] : -1.0f;
+            vb[j] = (ok && j >= jc) ? s[j] : -1.0f;
           }
-          best = max(best, kb);
+          const float ba = max11(va), bb = max11(vb);
+          sh.cval[cc - c0][t] = ba;
+          sh.cidx[cc - c0][t] = static_cast<uint8_t>(first_of(va, ba));
+          sh.cvalB[cc - c0][t] = bb;
+          sh.cidxB[cc - c0][t] = static_cast<uint8_t>(first_of(vb, bb));
         }
       }
-      flush();
+      __syncthreads();
+      for (int cc = c0 + warp; cc < c1; cc += kDeferWarps) {
+        const int u = cc - c0;
+        const float T = sh.tcache[cc];
+        // the lane's best per segment part, scanning its bins in order (a
+        // strict > keeps the lowest bin among equal sums)
+        float vA = -1.0f, vB = -1.0f;
+        int binA = 0, binB = 0;
+#pragma unroll
+        for (int q = 0; q < kThreadsPerLane; ++q) {
+          const int tt = kThreadsPerLane * lane + q;
+          const float v = sh.cval[u][tt];
+          if (v >= T && v >= 0.0f) {
+            const int bin = kDeferBins * tt + sh.cidx[u][tt];
+            if (bin < cut) {
+              if (v > vA) { vA = v; binA = bin; }
+            } else if (v > vB) {
+              vB = v;
+              binB = bin;
+            }
+          }
+          const float v2 = sh.cvalB[u][tt];
+          if (v2 >= T && v2 >= 0.0f) {
+            const int bin = kDeferBins * tt + sh.cidxB[u][tt];
+            if (v2 > vB) { vB = v2; binB = bin; }
+          }
+        }
+        // part B of lane l lies in segment segA + 1 = lane l + 1's segA (a
+        // segment of >= 66 bins covers the rest of lane l and all of lane l + 1);
+        // its bins come first there, so it wins ties
+        const float vP = __shfl_up_sync(kFull, vB, 1);
+        const int binP = __shfl_up_sync(kFull, binB, 1);
+        if (lane > 0 && vP >= 0.0f && vP >= vA) { vA = vP; binA = binP; }
+        if (lane == 31 && vB >= 0.0f) {
+          unsigned long long &kk = sh.keys[segA + 1][cc];
+          kk = max(kk, best_key(vB, static_cast<uint32_t>(k0 + binB)));
+        }
+        // each segment the warp holds: max power bits, then the lowest bin
+        unsigned todo = __ballot_sync(kFull, vA >= 0.0f);
+        while (todo != 0u) {
+          const int sgs = __shfl_sync(kFull, segA, __ffs(static_cast<int>(todo)) - 1);
+          const bool in = segA == sgs && vA >= 0.0f;
+          const uint32_t bits = in ? __float_as_uint(vA) : 0u;
+          const uint32_t mx = __reduce_max_sync(kFull, bits);
+          const uint32_t bn = (in && bits == mx) ? static_cast<uint32_t>(k0 + binA) : 0xffffffffu;
+          const uint32_t bmin = __reduce_min_sync(kFull, bn);
+          if (lane == 0) {
+            unsigned long long &kk = sh.keys[sgs][cc];
+            kk = max(kk, best_key(__uint_as_float(mx), bmin));
+          }
+          todo &= ~__ballot_sync(kFull, segA == sgs);
+        }
+      }
+      __syncthreads();   // the next chunk overwrites the chunk arrays
+    }
+    for (int j = t; j < n_segs * kR; j += kDeferThreads) {
+      const unsigned long long key = (&sh.keys[0][0])[j];
+      if (key != 0ull)
+        emit_slot<true>(slots, dirty, static_cast<uint64_t>(S.seg_off + g0 + j / kR) * W + (wf + j % kR - 1), key);
     }
   }
 }
@@ -704,7 +830,7 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
     record(p, 5, s);
     record(p, 6, s);
     if (p->seg_len >= 2 * kR)
-      deferred_kernel<<<p->defer_grid, 32 * kDeferWarps, 0, s>>>(
+      deferred_kernel<<<p->defer_grid, kDeferThreads, 0, s>>>(
           d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
           p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
     else

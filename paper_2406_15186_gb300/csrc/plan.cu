@@ -296,7 +296,7 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
   const int64_t nb = (z_max + kR - 1) / kR;
   p->item_cap = std::min<int64_t>(total_warps * nb, 65536);
   p->alloc_item_cap = p->item_cap;
-  p->defer_grid = 4 * n_sm;   // 4-warp CTAs, one item each at a time: 16 warps per SM
+  p->defer_grid = 8 * n_sm;   // 3-warp CTAs, one item each at a time: 24 warps per SM
   p->searched.assign(z_max, 1);
   for (auto &s : p->series) p->n_trials.push_back(static_cast<double>(s.m) * z_max);
   compute_thresholds(p);

@@ -459,13 +459,17 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
 // values come from an 11-register ring (one shared-memory load per step), and
 // the step loop has no cross-thread work.  A thread whose bins straddle a
 // segment boundary keeps the two parts apart (a second best/bin pair); its
-// warp runs that variant, so no thread diverges.  Every 11 steps the three
-// warps merge the chunk's widths: lane l scans the three threads that cover
-// bins 33 l .. 33 l + 32 and keeps, per segment there (at most two), the
-// largest sum reaching T_w and its lowest bin; the second part moves to lane
-// l + 1 (whose segment it is), and the warp then reduces each segment it
-// holds with two 32-bit reductions (power bits, then bin) into one 64-bit
-// maximum per (segment, width).  A last pass sends every maximum to its slot.
+// warp runs that variant, so no thread diverges.  Every 11 steps the chunk's
+// widths are merged into one 64-bit maximum per (segment, width): when the
+// block touches at most two segments (segment_len >= 1056, the usual case),
+// 8 threads per width each scan 12 threads' entries in bin order and a
+// 3-round shuffle combines them; otherwise lane l of a warp scans the three
+// threads that cover bins 33 l .. 33 l + 32 and keeps, per segment there (at
+// most two), the largest sum reaching T_w and its lowest bin, the second part
+// moves to lane l + 1 (whose segment it is), and the warp reduces each
+// segment it holds with two 32-bit reductions (power bits, then bin).  Each
+// key has one writer, so no atomics.  A last pass sends every maximum to its
+// slot.
 // The P window (1056 bins plus the 66-bin reach of one block) and the
 // snapshot are staged in shared memory.  Blocks at the very end of a series
 // (windows that leave the spectrum) take a plain per-step loop.
@@ -509,10 +513,11 @@ __device__ __forceinline__ int first_of(const float (&v)[kDeferBins], float m) {
 struct DeferShared {
   float region[kRegion];
   float snap[kR * (32 + 1)];                    // [bin i][lane l], rows of 33
-  float cval[kDeferChunk][kDeferThreads];       // per step of the chunk: best sum of each thread (part A)
-  float cvalB[kDeferChunk][kDeferThreads];      // part B (bins past a segment boundary), -1 if none
-  uint8_t cidx[kDeferChunk][kDeferThreads];     // first bin within the thread holding it
-  uint8_t cidxB[kDeferChunk][kDeferThreads];
+  float cval[kDeferChunk][kDeferThreads + 1];   // per step of the chunk: best sum of each thread (part A);
+  float cvalB[kDeferChunk][kDeferThreads + 1];  // part B (bins past a segment boundary), -1 if none; rows
+                                                // padded so the 8-thread merge reads are conflict-free
+  uint8_t cidx[kDeferChunk][kDeferThreads + 1];   // first bin within the thread holding it
+  uint8_t cidxB[kDeferChunk][kDeferThreads + 1];
   unsigned long long keys[kItemSegs][kR];
   float tcache[kR];                             // T_w of the block's widths
 };
@@ -621,6 +626,8 @@ __global__ void __launch_bounds__(kDeferThreads, 8) deferred_kernel(
     // bins from cut on lie in segA + 1
     const int segA = static_cast<int>(min64((k0 + kR * lane) / seg_len, seg_hi) - g0);
     const int cut = (g0 + segA < seg_hi) ? static_cast<int>((g0 + segA + 1) * seg_len - k0) : (1 << 30);
+    // with at most two segments: the block's first bin of the second one
+    const int bcut = (n_segs == 2) ? static_cast<int>((g0 + 1) * seg_len - k0) : (1 << 30);
 
     float rg[kDeferBins];
     bool ring = false;
@@ -656,7 +663,40 @@ __global__ void __launch_bounds__(kDeferThreads, 8) deferred_kernel(
         }
       }
       __syncthreads();
-      for (int cc = c0 + warp; cc < c1; cc += kDeferWarps) {
+      if (n_segs <= 2) {
+        // at most one segment boundary (bcut) in the block: 8 threads per
+        // width of the chunk, each scanning 12 threads' entries in bin order,
+        // then a 3-round shuffle over the 8; no atomics (one writer per key)
+        const int mw = t >> 3, q = t & 7;
+        const int u = mw;
+        unsigned long long kk0 = 0ull, kk1 = 0ull;
+        if (c0 + mw < c1) {
+          const float T = sh.tcache[c0 + mw];
+#pragma unroll
+          for (int e = 0; e < kDeferThreads / 8; ++e) {
+            const int tt = (kDeferThreads / 8) * q + e;
+            const float v = sh.cval[u][tt];
+            if (v >= T && v >= 0.0f) {
+              const int bin = kDeferBins * tt + sh.cidx[u][tt];
+              const unsigned long long key = best_key(v, static_cast<uint32_t>(k0 + bin));
+              if (bin < bcut) kk0 = max(kk0, key);
+              else kk1 = max(kk1, key);
+            }
+            const float v2 = sh.cvalB[u][tt];   // part B: past the boundary
+            if (v2 >= T && v2 >= 0.0f)
+              kk1 = max(kk1, best_key(v2, static_cast<uint32_t>(k0 + kDeferBins * tt + sh.cidxB[u][tt])));
+          }
+        }
+#pragma unroll
+        for (int d = 4; d >= 1; d >>= 1) {
+          kk0 = max(kk0, __shfl_xor_sync(kFull, kk0, d));
+          kk1 = max(kk1, __shfl_xor_sync(kFull, kk1, d));
+        }
+        if (q == 0 && c0 + mw < c1) {
+          if (kk0 != 0ull) sh.keys[0][c0 + mw] = max(sh.keys[0][c0 + mw], kk0);
+          if (kk1 != 0ull) sh.keys[1][c0 + mw] = max(sh.keys[1][c0 + mw], kk1);
+        }
+      } else for (int cc = c0 + warp; cc < c1; cc += kDeferWarps) {
         const int u = cc - c0;
         const float T = sh.tcache[cc];
         // the lane's best per segment part, scanning its bins in order (a

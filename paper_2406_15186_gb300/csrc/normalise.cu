@@ -209,8 +209,8 @@ __device__ __forceinline__ void split_pair(Sh &sh, const bool (&split)[2], float
 // Multi-level select (the general path): get(e, v0, v1) gives element e's
 // two component values; level 0 starts from the whole block.
 template <class Get>
-__device__ void select_levels(SelShared &sh, Get get, int n, uint32_t rank, bool pair, float (&out_lo)[2],
-                              float (&out_hi)[2]) {
+__device__ void select_levels(SelShared &sh, Get get, int n, uint32_t rank, bool pair,
+                                           float (&out_lo)[2], float (&out_hi)[2]) {
   if (threadIdx.x < 2) {
     sh.rank[threadIdx.x] = rank;
     sh.done[threadIdx.x] = 0;
@@ -758,37 +758,43 @@ __global__ void __launch_bounds__(kNormThreads, reg_min_blocks(K)) normalise_reg
 
   const bool even = (n % 2) == 0;
   const uint32_t rank = even ? static_cast<uint32_t>(n / 2 - 1) : static_cast<uint32_t>(n / 2);
-  float lo_v[2], hi_v[2];
-  if (!reg_select<K>(rs, [&](int j) { return v[j]; }, nv, rank, even, mn0, mn1, mx0, mx1, lo_v, hi_v))
-    select_levels(sh, [&](int e, float &v0, float &v1) {
-      const float2 f = gval(e);
-      v0 = f.x;
-      v1 = f.y;
-    }, n, rank, even, lo_v, hi_v);
-  float med_re, med_im;
-  bcast_mid(rs.mm, lo_v, hi_v, even, med_re, med_im);
-  if (sel != nullptr && t == 0) {
-    sel[8 * g + 0] = lo_v[0];
-    sel[8 * g + 1] = hi_v[0];
-    sel[8 * g + 4] = lo_v[1];
-    sel[8 * g + 5] = hi_v[1];
-  }
-  const float dh0 = fmaxf(fabsf(mx0 - med_re), fabsf(med_re - mn0));
-  const float dh1 = fmaxf(fabsf(mx1 - med_im), fabsf(med_im - mn1));
-  if (!reg_select<K>(rs, [&](int j) { return make_float2(fabsf(v[j].x - med_re), fabsf(v[j].y - med_im)); }, nv,
-                     rank, even, 0.0f, 0.0f, dh0, dh1, lo_v, hi_v))
-    select_levels(sh, [&](int e, float &v0, float &v1) {
-      const float2 f = gval(e);
-      v0 = fabsf(f.x - med_re);
-      v1 = fabsf(f.y - med_im);
-    }, n, rank, even, lo_v, hi_v);
-  float mad_re, mad_im;
-  bcast_mid(rs.mm, lo_v, hi_v, even, mad_re, mad_im);
-  if (sel != nullptr && t == 0) {
-    sel[8 * g + 2] = lo_v[0];
-    sel[8 * g + 3] = hi_v[0];
-    sel[8 * g + 6] = lo_v[1];
-    sel[8 * g + 7] = hi_v[1];
+  // Two passes through ONE copy of the select code (a smaller kernel keeps
+  // the instruction cache warm): pass 0 selects the median of the values,
+  // pass 1 the median of their absolute deviations from it (the MAD).
+  float med_re = 0.0f, med_im = 0.0f, mad_re = 0.0f, mad_im = 0.0f;
+  float lo0 = mn0, lo1 = mn1, hi0 = mx0, hi1 = mx1;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const float c0 = med_re, c1 = med_im;
+    float lo_v[2], hi_v[2];
+    if (!reg_select<K>(rs, [&](int j) {
+          return pass ? make_float2(fabsf(v[j].x - c0), fabsf(v[j].y - c1)) : v[j];
+        }, nv, rank, even, lo0, lo1, hi0, hi1, lo_v, hi_v))
+      select_levels(sh, [&](int e, float &v0, float &v1) {
+        const float2 f = gval(e);
+        v0 = pass ? fabsf(f.x - c0) : f.x;
+        v1 = pass ? fabsf(f.y - c1) : f.y;
+      }, n, rank, even, lo_v, hi_v);
+    float a, b;
+    bcast_mid(rs.mm, lo_v, hi_v, even, a, b);
+    if (sel != nullptr && t == 0) {
+      sel[8 * g + 2 * pass + 0] = lo_v[0];
+      sel[8 * g + 2 * pass + 1] = hi_v[0];
+      sel[8 * g + 2 * pass + 4] = lo_v[1];
+      sel[8 * g + 2 * pass + 5] = hi_v[1];
+    }
+    if (pass == 0) {
+      med_re = a;
+      med_im = b;
+      // the deviations lie in [0, max distance of the block's range from the median]
+      lo0 = 0.0f;
+      lo1 = 0.0f;
+      hi0 = fmaxf(fabsf(mx0 - med_re), fabsf(med_re - mn0));
+      hi1 = fmaxf(fabsf(mx1 - med_im), fabsf(med_im - mn1));
+    } else {
+      mad_re = a;
+      mad_im = b;
+    }
   }
   float inv_re, inv_im;
   bcast_inv(rs.mm, mad_re, mad_im, inv_re, inv_im);

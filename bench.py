@@ -52,6 +52,23 @@ def dist_env():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself without a process group): every
+    rank's step time is the slowest rank's, as the job ends with the last."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, ms):
+    """Whole-job throughput in G units/s: each of `world` replicas processes
+    units_per_rank in the slowest rank's ms."""
+    return world * units_per_rank / (ms * 1e-3) / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -520,12 +537,8 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * m * w_max / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(statistics.mean(step_ms), dist, dev)
+    value = job_value(world, m * w_max, ms)
 
     # searched-width subsets (every width still summed): the same step with
     # the z mod 8 and log2 z samplings
@@ -561,11 +574,7 @@ def run_ours(args, rank, world, local):
         c = plan.search_host(x_pin, use_graph=True, stream=stream)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         nc = len(c)
-    e2e_ms_mean = statistics.mean(e2e_ms)
-    if dist:
-        tt = torch.tensor([e2e_ms_mean], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms_mean = float(tt.item())
+    e2e_ms_mean = max_over_ranks(statistics.mean(e2e_ms), dist, dev)
 
     peaks, peak_kind = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -598,7 +607,7 @@ def run_ours(args, rank, world, local):
             "harmonics": harmonic,
             "paper_gpu_fidelity": fidelity,
             "roofline": roofline,
-            "e2e": {"value": world * m * w_max / (e2e_ms_mean * 1e-3) / 1e9, "unit": UNIT,
+            "e2e": {"value": job_value(world, m * w_max, e2e_ms_mean), "unit": UNIT,
                     "ms_per_step": e2e_ms_mean, "h2d_bytes_per_step": 4 * n,
                     "d2h_bytes_per_step": 16 + 32 * nc},
             "gpu_launches": 4 * args.steps,

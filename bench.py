@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-series batched measurement")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable 4096-binary measurement")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the step's stages one by one instead of as one CUDA graph")
     ap.add_argument("--tiling", default=None, metavar="WARPS,PERSISTENT",
                     help="bank launch shape of the single-series plan instead of the autotuner (e.g. 4,0)")
     return ap.parse_args()
@@ -494,9 +496,14 @@ def run_ours(args, rank, world, local):
     plan.enable_timing(True)
 
     def step():
-        plan.rfft(d_x, d_spec, stream=stream)
-        plan.power_normalise(d_spec, d_power, stream=stream)
-        plan.boxcar_search(d_power, stream=stream)
+        if args.no_graph:
+            plan.rfft(d_x, d_spec, stream=stream)
+            plan.power_normalise(d_spec, d_power, stream=stream)
+            plan.boxcar_search(d_power, stream=stream)
+        else:
+            # the whole path as one CUDA graph launch (pulscan_search), its
+            # per-stage timing events captured inside the graph
+            plan.search(d_x, d_spec, d_power, use_graph=True, stream=stream)
 
     step()
     if args.tiling:

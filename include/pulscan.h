@@ -322,7 +322,10 @@ PULSCAN_API int pulscan_amplitude_grad(pulscan_plan plan, const float *d_gx, con
  * or disable recording; pulscan_plan_timings then writes the milliseconds of
  * the most recent launch of [rfft, normalise, boxcar search kernel,
  * deferred-block kernel, candidate finalise, segment-maxima kernel, harmonic
- * sums] (-1 where not run) to h_ms[0..min(n,7)-1].  Synchronises the events. */
+ * sums] (-1 where not run) to h_ms[0..min(n,7)-1].  Synchronises the events.
+ * With timing on, pulscan_search(use_graph = 1) captures the events into its
+ * graph, and every launch of the graph records them again; changing the
+ * setting drops the plan's captured graph (the next call captures anew). */
 PULSCAN_API int pulscan_plan_enable_timing(pulscan_plan plan, int on);
 PULSCAN_API int pulscan_plan_timings(pulscan_plan plan, float *h_ms, int32_t n);
 

@@ -35,7 +35,13 @@ static int cufft_fail(cufftResult r, const char *what) {
 
 void record(pulscan_plan p, int idx, cudaStream_t s) {
   if (p->timing) {
-    cudaEventRecord(p->ev[idx], s);
+    // inside a stream capture the record becomes a node of the graph (an
+    // external event record), re-recorded by every launch
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(p->ev[idx], s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(p->ev[idx], s);
     p->ran[idx / 2] = true;
   }
 }
@@ -709,8 +715,8 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
       g.exec = nullptr;
     }
     if (!g.capture) PS_CUDA(cudaStreamCreateWithFlags(&g.capture, cudaStreamNonBlocking));
-    const bool timing = p->timing;
-    p->timing = false;
+    // with timing on, the stage events are captured as event-record nodes and
+    // re-recorded by every launch of the graph
     const pulscan_stream cs = reinterpret_cast<pulscan_stream>(g.capture);
     PS_CUDA(cudaStreamBeginCapture(g.capture, cudaStreamCaptureModeThreadLocal));
     int rc = pulscan_rfft(p, d_x, d_spec, cs);
@@ -718,7 +724,6 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
     if (!rc) rc = pulscan_boxcar_search(p, d_power, cs);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(g.capture, &graph);
-    p->timing = timing;
     if (rc) {
       if (graph) cudaGraphDestroy(graph);
       return rc;
@@ -793,6 +798,12 @@ int pulscan_plan_enable_timing(pulscan_plan p, int on) {
   }
   p->timing = on != 0;
   for (bool &r : p->ran) r = false;
+  // a captured graph holds the event records of the setting it was captured
+  // with: the next pulscan_search captures anew (an in-flight launch finishes)
+  if (p->graph.exec) {
+    cudaGraphExecDestroy(p->graph.exec);
+    p->graph.exec = nullptr;
+  }
   return PULSCAN_OK;
 }
 

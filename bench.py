@@ -617,7 +617,9 @@ def run_ours(args, rank, world, local):
             "e2e": {"value": job_value(world, m * w_max, e2e_ms_mean), "unit": UNIT,
                     "ms_per_step": e2e_ms_mean, "h2d_bytes_per_step": 4 * n,
                     "d2h_bytes_per_step": 16 + 32 * nc},
-            "gpu_launches": 4 * args.steps,
+            # this library's kernels per step: normalise, bank, deferred
+            # blocks, word scan, finaliser (cuFFT's own kernels not counted)
+            "gpu_launches": 5 * args.steps,
             "clocks": clocks}
     if not args.no_batched:
         plan.close()

@@ -711,8 +711,10 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
 }
 
 // Blocks per SM the register budget must allow: all values of a thread plus
-// one bucket word per value stay in registers; small K fits four blocks.
-constexpr int reg_min_blocks(int k) { return k <= 9 ? 4 : (k <= 17 ? 3 : 1); }
+// one bucket word per value stay in registers.  Up to K = 17 four blocks per
+// SM (64 registers; K = 17 spills ~90 bytes to L1, which costs less than a
+// third round of CTAs on 1024-block grids).
+constexpr int reg_min_blocks(int k) { return k <= 17 ? 4 : 1; }
 
 template <int K>
 __global__ void __launch_bounds__(kNormThreads, reg_min_blocks(K)) normalise_reg_kernel(

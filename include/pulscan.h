@@ -318,8 +318,10 @@ PULSCAN_API int pulscan_inject(pulscan_plan plan, const float *d_noise, const fl
 PULSCAN_API int pulscan_amplitude_grad(pulscan_plan plan, const float *d_gx, const float *d_template,
                                        float *d_gamp, pulscan_stream stream);
 
-/* Per-kernel timing with CUDA events on the launch stream: enable (on != 0)
- * or disable recording; pulscan_plan_timings then writes the milliseconds of
+/* Per-kernel timing with CUDA events on the launch stream: on = 1 records
+ * every stage, on = 2 only the boxcar search kernel (each event between two
+ * kernels costs a few microseconds of pipeline drain), 0 disables recording;
+ * pulscan_plan_timings then writes the milliseconds of
  * the most recent launch of [rfft, normalise, boxcar search kernel,
  * deferred-block kernel, candidate finalise, segment-maxima kernel, harmonic
  * sums] (-1 where not run) to h_ms[0..min(n,7)-1].  Synchronises the events.

@@ -270,7 +270,8 @@ class Plan:
 
     # -- timing
     def enable_timing(self, on=True):
-        _check(load().pulscan_plan_enable_timing(self._h, int(bool(on))))
+        """on: True/1 every stage's events, 2 the boxcar search kernel's only, False/0 none."""
+        _check(load().pulscan_plan_enable_timing(self._h, 2 if on == 2 else int(bool(on))))
 
     def timings(self):
         """ms of the last [rfft, normalise, boxcar kernel, deferred blocks, finalise, segment maxima,

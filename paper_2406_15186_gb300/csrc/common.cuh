@@ -159,7 +159,7 @@ struct pulscan_plan_s {
   float *d_gspec = nullptr;        // C2R input (spectrum layout)
   std::vector<ps::FftClass> ifft;  // C2R plans per length class
   // timing
-  bool timing = false;
+  int timing = 0;                  // 0 off, 1 every stage's events, 2 the bank kernel's pair only
   cudaEvent_t ev[14] = {};
   bool ran[7] = {};
   ps::GraphCache graph;

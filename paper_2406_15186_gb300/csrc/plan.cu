@@ -34,7 +34,9 @@ static int cufft_fail(cufftResult r, const char *what) {
 }
 
 void record(pulscan_plan p, int idx, cudaStream_t s) {
-  if (p->timing) {
+  // mode 2 keeps only the bank kernel's pair (4, 5): every event between
+  // kernels costs a few microseconds of pipeline drain
+  if (p->timing == 1 || (p->timing == 2 && (idx == 4 || idx == 5))) {
     // inside a stream capture the record becomes a node of the graph (an
     // external event record), re-recorded by every launch
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -494,8 +496,8 @@ int pulscan_plan_autotune(pulscan_plan p, const float *d_power, pulscan_stream s
   if (!p || !d_power) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   if (!aligned16(d_power)) return fail(PULSCAN_ERR_INVALID_ARG, "power buffer must be 16-byte aligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const bool timing = p->timing;
-  p->timing = false;
+  const int timing = p->timing;
+  p->timing = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   PS_CUDA(cudaEventCreate(&e0));
   PS_CUDA(cudaEventCreate(&e1));
@@ -796,7 +798,7 @@ int pulscan_plan_enable_timing(pulscan_plan p, int on) {
     for (auto &e : p->ev)
       if (!e) PS_CUDA(cudaEventCreate(&e));
   }
-  p->timing = on != 0;
+  p->timing = (on == 2) ? 2 : (on != 0 ? 1 : 0);
   for (bool &r : p->ran) r = false;
   // a captured graph holds the event records of the setting it was captured
   // with: the next pulscan_search captures anew (an in-flight launch finishes)

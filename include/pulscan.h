@@ -278,6 +278,16 @@ PULSCAN_API int pulscan_search(pulscan_plan plan, const float *d_x, float *d_spe
 PULSCAN_API int pulscan_search_host(pulscan_plan plan, const float *h_x, pulscan_cand *h_out, int64_t cap,
                                     int64_t *n_out, int use_graph, pulscan_stream stream);
 
+/* The first half of pulscan_search_host, asynchronous: enqueues on `stream`
+ * the copy of h_x (float[x_floats]) into the plan's own device buffers and
+ * pulscan_search on them, and returns without waiting.  h_x must stay valid
+ * and unchanged until the copy has run (pinned memory lets it overlap with
+ * other work); collect the candidates with pulscan_candidates on the same
+ * stream.  Two plans used in turn on two streams pipeline a stream of series:
+ * one series' copy runs while the other's search does.  Errors as
+ * pulscan_search; NOMEM for the first call's buffers. */
+PULSCAN_API int pulscan_search_host_async(pulscan_plan plan, const float *h_x, int use_graph, pulscan_stream stream);
+
 /* Differentiable extension (a smooth relaxation of Algorithm 4's per-chunk
  * maximum; the paper has no gradient): for every segment s and width w,
  *   Y[s, w] = tau * log sum_{k in s, k <= M - w} exp(S_w[k] / tau),

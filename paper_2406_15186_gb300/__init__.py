@@ -69,6 +69,7 @@ _SIGS = {
                                                       _P]),
     "pulscan_search": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
     "pulscan_search_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _I64P, ctypes.c_int, _P]),
+    "pulscan_search_host_async": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     "pulscan_lse_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, _P]),
     "pulscan_lse_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float, _P]),
     "pulscan_inject": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -254,6 +255,12 @@ class Plan:
     def search(self, d_x, d_spec, d_power, use_graph=False, stream=None):
         _check(load().pulscan_search(self._h, _ptr(d_x), _ptr(d_spec), _ptr(d_power), int(bool(use_graph)),
                                      _stream(stream)))
+
+    def search_host_async(self, h_x, use_graph=True, stream=None):
+        """Enqueue the copy of h_x (pinned tensor or numpy array, kept alive by
+        the caller until the copy has run) and the search; no wait.  Collect
+        with candidates(stream=...)."""
+        _check(load().pulscan_search_host_async(self._h, _ptr(h_x), int(bool(use_graph)), _stream(stream)))
 
     def search_host(self, h_x, use_graph=True, cap=None, stream=None):
         """Whole path from host memory (numpy array or pinned CPU tensor); returns candidates."""

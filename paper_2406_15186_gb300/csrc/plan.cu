@@ -742,9 +742,8 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
   return PULSCAN_OK;
 }
 
-int pulscan_search_host(pulscan_plan p, const float *h_x, pulscan_cand *h_out, int64_t cap, int64_t *n_out,
-                        int use_graph, pulscan_stream stream) {
-  if (!p || !h_x || !n_out) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+int pulscan_search_host_async(pulscan_plan p, const float *h_x, int use_graph, pulscan_stream stream) {
+  if (!p || !h_x) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   if (!p->own_x) {
     int rc = dalloc(&p->own_x, p->x_floats);
     if (!rc) rc = dalloc(&p->own_spec, 2 * p->spec_bins);
@@ -753,7 +752,13 @@ int pulscan_search_host(pulscan_plan p, const float *h_x, pulscan_cand *h_out, i
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   PS_CUDA(cudaMemcpyAsync(p->own_x, h_x, p->x_floats * sizeof(float), cudaMemcpyHostToDevice, s));
-  const int rc = pulscan_search(p, p->own_x, p->own_spec, p->own_power, use_graph, stream);
+  return pulscan_search(p, p->own_x, p->own_spec, p->own_power, use_graph, stream);
+}
+
+int pulscan_search_host(pulscan_plan p, const float *h_x, pulscan_cand *h_out, int64_t cap, int64_t *n_out,
+                        int use_graph, pulscan_stream stream) {
+  if (!p || !h_x || !n_out) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  const int rc = pulscan_search_host_async(p, h_x, use_graph, stream);
   if (rc) return rc;
   return pulscan_candidates(p, h_out, cap, n_out, stream);
 }

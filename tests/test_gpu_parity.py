@@ -252,3 +252,32 @@ def test_autotune_keeps_the_candidates(pkg):
     assert len(after["cands"]) == len(before["cands"]) > 0
     for f in ("series", "width", "bin", "power", "sigma"):
         assert np.array_equal(np.sort(after["cands"][f]), np.sort(before["cands"][f]))
+
+
+def test_host_entry_points_match_the_device_path(pkg):
+    """pulscan_search_host and pulscan_search_host_async (two plans in turn on
+    two streams, as a pipelined stream of series) give exactly the records of
+    the device-buffer path on the same series."""
+    n, w_max, seg_len, sigma = 1 << 16, 64, 1024, 4.0
+    xs = [synth.inject(synth.noise(n, 40 + i), [dict(amp=0.15, r0=0.2 * n / 2 + 300 * i, z=30.0, w=0.0, phi0=0.3)])
+          for i in range(4)]
+    ref = []
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    d_x, d_spec, d_power = plan.buffers("cuda")
+    for x in xs:
+        d_x.copy_(torch.from_numpy(x))
+        plan.search(d_x, d_spec, d_power)
+        ref.append(plan.candidates())
+    assert all(len(r) > 0 for r in ref)
+    for i, x in enumerate(xs):
+        got = plan.search_host(torch.from_numpy(x).pin_memory(), use_graph=bool(i % 2))
+        assert np.array_equal(got, ref[i])
+    plans = [plan, pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pins = [torch.from_numpy(x).pin_memory() for x in xs]
+    plans[0].search_host_async(pins[0], stream=streams[0])
+    for i in range(len(xs)):
+        if i + 1 < len(xs):
+            plans[(i + 1) % 2].search_host_async(pins[i + 1], stream=streams[(i + 1) % 2])
+        got = plans[i % 2].candidates(stream=streams[i % 2])
+        assert np.array_equal(got, ref[i]), i

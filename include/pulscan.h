@@ -209,6 +209,15 @@ PULSCAN_API int pulscan_plan_set_rblock(pulscan_plan plan, int64_t block_width);
  * Host-synchronous. */
 PULSCAN_API int pulscan_plan_thresholds(pulscan_plan plan, int32_t series, float *h_thresh);
 
+/* The same threshold for one width, on the host only (no CUDA call, no plan;
+ * §2.2.3 Eq. 9 with the Bonferroni count of §2.2.3): *t_out = the smallest
+ * float T with ln Q(shape, T) + ln n_trials <= ln Phi_c(sigma_thr), where
+ * Q is the regularised upper incomplete gamma function and shape the gamma
+ * shape of the sum (w for a width-w sum of the power, H(H+1)/2 w for the
+ * H-harmonic sum of §2.3).  Errors: INVALID_ARG (shape <= 0, n_trials < 1, sigma_thr < 0 or not
+ * finite, null t_out). */
+PULSCAN_API int pulscan_threshold_power(double shape, double n_trials, double sigma_thr, float *t_out);
+
 /* R2C FFT of every series (cuFFT, unnormalised, e^{-2 pi i k n/N}): d_x
  * float[x_floats] -> d_spec float[spec_floats] as (re, im) pairs. */
 PULSCAN_API int pulscan_rfft(pulscan_plan plan, const float *d_x, float *d_spec, pulscan_stream stream);

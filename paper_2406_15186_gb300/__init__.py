@@ -60,6 +60,8 @@ _SIGS = {
     "pulscan_plan_tiling": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "pulscan_plan_set_tiling": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "pulscan_plan_thresholds": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
+    "pulscan_threshold_power": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.POINTER(ctypes.c_float)]),
     "pulscan_rfft": (ctypes.c_int, [_P, _P, _P, _P]),
     "pulscan_power_normalise": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pulscan_boxcar_search": (ctypes.c_int, [_P, _P, _P]),
@@ -103,6 +105,13 @@ def load():
 def _check(rc):
     if rc != 0:
         raise PulscanError(rc, _LIB.pulscan_last_error().decode())
+
+
+def threshold_power(shape, n_trials, sigma_thr):
+    """pulscan_threshold_power: the FP32 power threshold of one width (host only)."""
+    t = ctypes.c_float(0.0)
+    _check(load().pulscan_threshold_power(float(shape), float(n_trials), float(sigma_thr), ctypes.byref(t)))
+    return t.value
 
 
 def _ptr(a):

@@ -580,6 +580,14 @@ int pulscan_plan_stage_offsets(pulscan_plan p, int32_t harmonics, int64_t *h_pow
   return PULSCAN_OK;
 }
 
+int pulscan_threshold_power(double shape, double n_trials, double sigma_thr, float *t_out) {
+  if (!t_out || !(shape > 0.0) || !(n_trials >= 1.0) || !(sigma_thr >= 0.0) || !std::isfinite(sigma_thr) ||
+      !std::isfinite(shape) || !std::isfinite(n_trials))
+    return fail(PULSCAN_ERR_INVALID_ARG, "shape > 0, n_trials >= 1 and a finite sigma_thr >= 0 are required");
+  *t_out = threshold_for(shape, host_log_sf_normal(sigma_thr) - std::log(n_trials));
+  return PULSCAN_OK;
+}
+
 int pulscan_plan_thresholds(pulscan_plan p, int32_t series, float *h_thresh) {
   if (!p || !h_thresh) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   if (series < 0 || series >= static_cast<int32_t>(p->n_base))

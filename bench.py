@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-series batched measurement")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable 4096-binary measurement")
+    ap.add_argument("--diff-binaries", type=int, default=None,
+                    help="run the differentiable measurement on its first N binaries only (profiling)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the step's stages one by one instead of as one CUDA graph")
     ap.add_argument("--tiling", default=None, metavar="WARPS,PERSISTENT",
@@ -406,11 +408,14 @@ def run_fidelity(torch, pkg, plan, step, stream, steps, flush):
                     "maximum), the fitted polynomial log p per maximum"}
 
 
-def run_diff(torch, pkg, synth, dev, stream, steps):
+def run_diff(torch, pkg, synth, dev, stream, steps, n_binaries=None):
     """Differentiable batch: logsumexp forward and hand-written backward over
-    4096 binaries of 2^20 samples (widths 1..512, L = 2048, tau = 0.1)."""
+    4096 binaries of 2^20 samples (widths 1..512, L = 2048, tau = 0.1); the
+    first n_binaries of them only when given (a reduced case for profiling)."""
     cfg = synth.WORKLOADS["diff_4096"]
     n, n_series, w_max, seg_len, tau = cfg["n"], cfg["n_series"], cfg["z_max"], cfg["segment_len"], cfg["tau"]
+    if n_binaries:
+        n_series = min(n_series, int(n_binaries))
     m = n // 2 + 1
     lib = pkg.load()
     plan = pkg.Plan(lengths=[n] * n_series, z_max=w_max, segment_len=seg_len, threshold_sigma=6.0)
@@ -465,7 +470,7 @@ def run_diff(torch, pkg, synth, dev, stream, steps):
             "finite_gradients": ok,
             "forward": "rfft + normalise (order statistics kept) + logsumexp of the boxcar bank",
             "backward": "softmax-weighted boxcar scatter + median/MAD adjoint + C2R + amplitude reduction",
-            "l2": "inputs (17 GB) far larger than L2"}
+            "l2": f"inputs ({4 * n * n_series / 1e9:.2f} GB) larger than L2"}
 
 
 def run_ours(args, rank, world, local):
@@ -677,7 +682,7 @@ def run_ours(args, rank, world, local):
         plan.close()
         d_x = d_spec = d_power = None
         torch.cuda.empty_cache()
-        line["differentiable"] = run_diff(torch, pkg, synth, dev, stream, 3)
+        line["differentiable"] = run_diff(torch, pkg, synth, dev, stream, 3, args.diff_binaries)
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         spec, t_fft = oracle_fft(x)

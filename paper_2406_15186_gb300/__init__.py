@@ -5,6 +5,24 @@ The binding only marshals arguments: every step of the search runs in the
 library's CUDA kernels (and cuFFT for the transform).  PyTorch is used, when
 given, for device memory and streams only.  There is no CPU fallback: if the
 library has not been built, ``load()`` raises.
+
+Typical use (one series of n float32 samples already on the GPU)::
+
+    import paper_2406_15186_gb300 as ps
+    from paper_2406_15186_gb300 import build
+    build.build()                                   # in-tree libpulscan.so, sm_103a
+    plan = ps.Plan(n=n, z_max=1024, segment_len=4096, threshold_sigma=6.0)
+    d_x, d_spec, d_power = plan.buffers("cuda")     # torch tensors sized for the plan
+    d_x.copy_(x)
+    plan.search(d_x, d_spec, d_power, use_graph=True)   # FFT, normalise, bank, threshold
+    cands = plan.candidates()                       # numpy records (CAND_DTYPE)
+    plan.autotune(d_power)                          # optional, once: the bank's launch shape
+
+From host memory: ``plan.search_host(x_pinned)``; a stream of series:
+``search_host_async`` on two plans in turn, then ``candidates``.  Batches
+of uneven lengths: ``Plan(lengths=[...], ...)``; harmonic sums:
+``Plan(..., numharm=H)``; the logsumexp statistic and its gradient:
+``paper_2406_15186_gb300.lse``.
 """
 import ctypes
 import os

@@ -1,12 +1,16 @@
 """Benchmark of the GB300 boxcar search (one JSON line on stdout, rank 0).
 
-Workload: the SPOTLIGHT-scale single series -- N = 2^23 float32 samples of
-Gaussian noise with 8 injected drifting tones, boxcar widths 1..1024, segments
-of 4096 bins, threshold 6 sigma (synthetic stand-in for the paper's `.fft`
-inputs).  One step = the whole path: R2C FFT (cuFFT), per-segment median/MAD
-normalisation, the boxcar bank over every width at every bin, and the
-per-(segment, width) maximum / threshold / significance.  The metric is
-boxcar bins x widths per second, M * W / step time, summed over ranks.
+Headline workload: the large single series -- N = 2^27 float32 samples of
+Gaussian noise with 32 injected drifting tones, boxcar widths 1..4096,
+segments of 16384 bins, threshold 7 sigma (synthetic stand-in for the
+paper's `.fft` inputs), the largest single-series workload.  One step = the
+whole path: R2C FFT (cuFFT), per-segment median/MAD normalisation, the
+boxcar bank over every width at every bin, and the per-(segment, width)
+maximum / threshold / significance.  The metric is boxcar bins x widths per
+second, M * W / step time, summed over ranks.  The other single-series
+workloads (2^23 samples, widths 1..1024; 2^20 samples, widths 1..256), the
+512-series batch and the differentiable batch are reported under their own
+keys.
 
 --impl reference times the FP64 CPU oracle instead (the repository's own
 reference implementation of the method), on a bounded sample of the same
@@ -15,6 +19,7 @@ workload scaled to the same unit.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -27,10 +32,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "single_2p23"
+WORKLOAD = "single_2p27"
+EXTRA_SINGLE = ("single_2p23", "single_2p20")
 METRIC = "boxcar bins x widths per second"
 UNIT = "G bin-widths/s"
 L2_FLUSH_BYTES = 512 << 20      # > 129 MB of L2
+FFT_PREFIX = 1 << 24            # oracle FFT sample of the 2^27-sample series
 
 
 def parse():
@@ -39,9 +46,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["single_2p27", "single_2p23", "single_2p20"],
+                    help="headline single-series workload (profiling of a smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-series batched measurement")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable 4096-binary measurement")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="skip every section after the headline's timed steps (profiling)")
     ap.add_argument("--diff-binaries", type=int, default=None,
                     help="run the differentiable measurement on its first N binaries only (profiling)")
     ap.add_argument("--no-graph", action="store_true",
@@ -134,9 +145,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profile_traffic(kernel_src):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the kernel source."""
-    path = os.path.join(ROOT, "profiles", "boxcar_search_single_2p23.md")
+def profile_traffic(kernel_src, workload):
+    """DRAM bytes per launch of the bank kernel from the committed ncu summary
+    of this workload, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"boxcar_search_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -152,20 +164,35 @@ def profile_traffic(kernel_src):
 
 
 # ------------------------------------------------------------------ oracle arm
-def oracle_fft(x):
-    """The oracle's FFT of the whole series, with its time (s)."""
+def oracle_fft_sample(name):
+    """The oracle's FFT timed on a bounded sample of the workload's series: the
+    whole series when it has at most FFT_PREFIX samples, else its first
+    FFT_PREFIX samples, with the time scaled by N log2 N (the radix-2 FFT does
+    log2 N stages of N / 2 butterflies).  Returns (spectrum of the sample, the
+    scaled seconds for the whole series, description)."""
     from oracle import fft as offt
+    from paper_2406_15186_gb300 import synth
+    n = synth.WORKLOADS[name]["n"]
+    n_p = min(n, FFT_PREFIX)
+    x = synth.single_series_prefix(name, n_p)
     t0 = time.perf_counter()
     spec = offt.rfft(x.astype(np.float64))
-    return spec, time.perf_counter() - t0
+    t = time.perf_counter() - t0
+    scale = (n * math.log2(n)) / (n_p * math.log2(n_p))
+    if n_p == n:
+        desc = f"oracle FFT of the whole 2^{int(math.log2(n))}-sample series ({t:.1f} s, timed once, one core)"
+    else:
+        desc = (f"oracle FFT of the series' first 2^{int(math.log2(n_p))} samples ({t:.1f} s, one core), "
+                f"scaled by N log2 N to 2^{int(math.log2(n))} ({t * scale:.1f} s)")
+    return spec, t * scale, desc
 
 
-def oracle_sample(spec, t_fft, cfg, n_seg_sample):
-    """Time the FP64 oracle on a bounded sample; returns (G bin-widths/s, seconds, description).
+def oracle_sample(spec, t_fft, fft_desc, cfg, n_seg_sample):
+    """Time the FP64 oracle on a bounded sample, one core; returns (G bin-widths/s, seconds, description).
 
-    The FFT is timed once on the whole series (t_fft); normalisation and the
-    boxcar stage are linear in segments, so they are timed on the first
-    n_seg_sample segments and scaled to the whole series.
+    Normalisation and the boxcar stage are linear in segments, so they are
+    timed on the first n_seg_sample segments of the sampled spectrum and
+    scaled to the whole series; the FFT time is added (t_fft).
     """
     from oracle import boxcar as obox
     from oracle import normalise as onorm
@@ -182,8 +209,8 @@ def oracle_sample(spec, t_fft, cfg, n_seg_sample):
     t3 = time.perf_counter()
     frac = n_seg_sample / n_seg
     t_full = t_fft + (t3 - t1) / frac
-    desc = (f"oracle FFT of the full 2^{n.bit_length() - 1}-sample series ({t_fft:.1f} s, timed once) + "
-            f"normalise/boxcar/search of {n_seg_sample}/{n_seg} segments, scaled linearly to all segments")
+    desc = (f"{fft_desc} + normalise/boxcar/search of {n_seg_sample} of its segments on one core, scaled "
+            f"linearly to the {n_seg} segments of the series")
     return m * w_max / t_full / 1e9, (t3 - t1), desc
 
 
@@ -207,73 +234,87 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def oracle_parallel(spec, t_fft, cfg, seg_per_proc, procs):
+def oracle_parallel(spec, t_fft, fft_desc, cfg, seg_per_proc, procs):
     """The oracle on all host cores: processes (spawned, so no CUDA state is
     inherited) each run normalise + maxima + candidates on their own run of
-    seg_per_proc segments; wall time of the parallel pass, the FFT (one core,
-    timed once) added, scaled linearly to all segments."""
+    seg_per_proc segments of the sampled spectrum; wall time of the parallel
+    pass, scaled linearly to all segments of the series, plus the FFT time."""
     import multiprocessing as mp
     n, w_max, seg_len, sigma = cfg["n"], cfg["z_max"], cfg["segment_len"], cfg["sigma"]
     m = n // 2 + 1
     n_seg = m // seg_len
-    procs = max(1, min(procs, n_seg // seg_per_proc))
+    avail = (len(spec) - w_max) // seg_len
+    procs = max(1, min(procs, avail // seg_per_proc))
     nt = float(m) * w_max
     jobs = [(spec[i * seg_per_proc * seg_len: (i + 1) * seg_per_proc * seg_len + w_max], w_max, seg_len, sigma, nt,
              seg_per_proc) for i in range(procs)]
     with mp.get_context("spawn").Pool(procs) as pool:
-        pool.map(_oracle_segments, [(j[0][: 2 * seg_len + w_max], w_max, seg_len, sigma, nt, 1) for j in jobs])
+        pool.map(_oracle_segments, [(j[0][: seg_len + w_max], w_max, seg_len, sigma, nt, 1) for j in jobs])
         t0 = time.perf_counter()
         pool.map(_oracle_segments, jobs)
         t = time.perf_counter() - t0
     frac = procs * seg_per_proc / n_seg
     t_full = t_fft + t / frac
-    desc = (f"oracle FFT of the full series on one core ({t_fft:.1f} s, timed once) + normalise/boxcar/search "
-            f"of {procs * seg_per_proc}/{n_seg} segments on {procs} processes ({seg_per_proc} each, "
-            f"{t:.1f} s wall), scaled linearly to all segments")
+    desc = (f"{fft_desc} + normalise/boxcar/search of {procs * seg_per_proc} of its segments on {procs} "
+            f"processes ({seg_per_proc} each, {t:.1f} s wall), scaled linearly to the {n_seg} segments of the "
+            f"series")
     return m * w_max / t_full / 1e9, t, desc, procs
 
 
 def run_reference(args, rank, world):
     """The oracle on the host cores: each step is one bounded sample of the
-    workload -- normalise + maxima + candidates of 2 segments per process over
-    a spawned pool of all host cores -- with the FFT of the whole series
-    (one core, timed once) added and the sample scaled to the series."""
+    workload -- normalise + maxima + candidates of one segment per process
+    over a spawned pool of all host cores -- with the oracle FFT time (a
+    sample scaled by N log2 N, timed once) added and the sample scaled to the
+    series."""
     if rank != 0:
         return
     import multiprocessing as mp
     from paper_2406_15186_gb300 import synth
-    cfg = synth.WORKLOADS[WORKLOAD]
-    x, _ = synth.single_series(WORKLOAD)
+    name = args.workload
+    cfg = synth.WORKLOADS[name]
     n, w_max, seg_len, sigma = cfg["n"], cfg["z_max"], cfg["segment_len"], cfg["sigma"]
     m = n // 2 + 1
     n_seg = m // seg_len
-    spec, t_fft = oracle_fft(x)
-    procs = max(1, min(host_cores(), n_seg // 2))
-    per = 2
+    spec, t_fft, fft_desc = oracle_fft_sample(name)
+    per = 1
+    procs = max(1, min(host_cores(), (len(spec) - w_max) // seg_len))
     nt = float(m) * w_max
     jobs = [(spec[i * per * seg_len: (i + 1) * per * seg_len + w_max], w_max, seg_len, sigma, nt, per)
             for i in range(procs)]
-    vals = []
+    # one step = the sample: procs * per segments (their bins x widths), in
+    # the wall time of the pool pass plus the same fraction of the FFT time
+    frac = procs * per / n_seg
+    step_s = []
     with mp.get_context("spawn").Pool(procs) as pool:
         for i in range(args.warmup + args.steps):
             t0 = time.perf_counter()
             pool.map(_oracle_segments, jobs)
             t = time.perf_counter() - t0
             if i >= args.warmup:
-                t_full = t_fft + t / (procs * per / n_seg)
-                vals.append(m * w_max / t_full / 1e9)
-    value = statistics.mean(vals)
-    desc = (f"oracle FFT of the full series on one core ({t_fft:.1f} s, timed once) + normalise/boxcar/search of "
-            f"{procs * per}/{n_seg} segments per step on {procs} processes, scaled linearly to all segments")
-    ms = m * w_max / (value * 1e9) * 1e3
+                step_s.append(t + t_fft * frac)
+    ms = statistics.mean(step_s) * 1e3
+    value = frac * m * w_max / (ms * 1e-3) / 1e9
+    desc = (f"{fft_desc} + normalise/boxcar/search of {procs * per} of its segments per step on {procs} "
+            f"processes; a step is those segments' share ({frac:.3g}) of the series' bins x widths, in the pool "
+            f"pass's wall time plus the same share of the FFT time")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: N=2^23, z_max=1024, segment_len=4096, sigma=6",
-                       "sample": desc, "l2": "n/a (CPU)"},
+            "config": {"workload": workload_text(name), "sample": desc, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def workload_text(name):
+    from paper_2406_15186_gb300 import synth
+    cfg = synth.WORKLOADS[name]
+    n = cfg["n"]
+    tones = {"single_2p27": "32 drifting tones", "single_2p23": "8 drifting tones",
+             "single_2p20": "one drifting tone"}[name]
+    return (f"{name}: N=2^{int(math.log2(n))} samples (M={n // 2 + 1} bins), {tones}, z_max={cfg['z_max']}, "
+            f"segment_len={cfg['segment_len']}, sigma={cfg['sigma']:g}")
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -334,7 +375,7 @@ def run_batched(torch, pkg, synth, dev, stream, steps):
             "l2": "inputs (8.2 GB) far larger than L2"}
 
 
-def run_harmonic(torch, pkg, synth, dev, stream, x, cfg, steps, flush):
+def run_harmonic(torch, pkg, synth, dev, stream, x_dev, cfg, steps, flush):
     """The bench series searched with harmonic summing up to 4 harmonics (§2.3;
     numharm = 4 is the paper's setting in its timing runs)."""
     n, w_max, seg_len, sigma = cfg["n"], cfg["z_max"], cfg["segment_len"], cfg["sigma"]
@@ -342,7 +383,7 @@ def run_harmonic(torch, pkg, synth, dev, stream, x, cfg, steps, flush):
     plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma, numharm=numharm)
     with torch.cuda.stream(stream):
         d_x, d_spec, d_power = plan.buffers(dev)
-        d_x.copy_(torch.from_numpy(x))
+        d_x.copy_(x_dev)
     torch.cuda.synchronize()
     plan.enable_timing(True)
 
@@ -473,6 +514,124 @@ def run_diff(torch, pkg, synth, dev, stream, steps, n_binaries=None):
             "l2": f"inputs ({4 * n * n_series / 1e9:.2f} GB) larger than L2"}
 
 
+def time_single(torch, pkg, synth, dev, stream, flush, name, args, steps, warmup, around=None):
+    """One single-series workload: the whole path as one CUDA graph per step
+    (or its stages one by one with --no-graph), the bank's launch shape by the
+    autotuner (or --tiling), `warmup` untimed steps, then `steps` timed steps
+    with the L2 flushed before each (outside the events); the bank kernel's
+    own event pair is recorded inside every timed step.  around = (start,
+    stop) callables bracketing the timed region (clock sampling, barriers).
+    Then extra steps with every stage's events give the per-stage breakdown.
+    Returns (result dict, plan, (d_x, d_spec, d_power))."""
+    cfg = synth.WORKLOADS[name]
+    n, w_max, seg_len, sigma = cfg["n"], cfg["z_max"], cfg["segment_len"], cfg["sigma"]
+    m = n // 2 + 1
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    with torch.cuda.stream(stream):
+        d_x, d_spec, d_power = plan.buffers(dev)
+        synth.single_series_device(name, d_x)
+    torch.cuda.synchronize()
+    # the timed steps record only the bank kernel's event pair (the roofline's
+    # live kernel time): every event between two kernels drains the pipeline
+    # and adds a few microseconds
+    plan.enable_timing(2)
+
+    def step():
+        if args.no_graph:
+            plan.rfft(d_x, d_spec, stream=stream)
+            plan.power_normalise(d_spec, d_power, stream=stream)
+            plan.boxcar_search(d_power, stream=stream)
+        else:
+            plan.search(d_x, d_spec, d_power, use_graph=True, stream=stream)
+
+    step()
+    if args.tiling:
+        plan.set_tiling(*[int(v) for v in args.tiling.split(",")])
+        tiling, tiling_by = plan.tiling(), "--tiling"
+    else:
+        tiling = plan.autotune(d_power, stream=stream)     # launch shape of the bank, timed on this input
+        tiling_by = "pulscan_plan_autotune"
+    for _ in range(warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        step()
+    n_cands = len(plan.candidates(stream=stream))
+    n_deferred = plan.counters()[0]
+    extra = around[0]() if around else None
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    k_bank_live = []
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # L2 flushed between timed steps (outside the events)
+            ev[i][0].record(stream)
+        step()
+        with torch.cuda.stream(stream):
+            ev[i][1].record(stream)
+        k_bank_live.append(plan.timings()[2])  # the bank kernel's events in this step (same stream)
+    torch.cuda.synchronize()
+    clocks = around[1](extra) if around else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+
+    plan.enable_timing(True)
+    step()
+    n_break = max(5, steps // 2)
+    k = {key: [] for key in ("rfft_cufft", "normalise", "boxcar_search", "deferred_blocks", "finalise")}
+    break_ms = []
+    for _ in range(n_break):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        step()
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        t = plan.timings()
+        for key, idx in zip(k, (0, 1, 2, 3, 4)):
+            k[key].append(t[idx])
+        torch.cuda.synchronize()
+        break_ms.append(e0.elapsed_time(e1))
+    plan.enable_timing(False)
+    kernels = {key: statistics.mean(v) for key, v in k.items()}
+    kernels["boxcar_search_live"] = statistics.mean(k_bank_live)
+    kernels["note"] = (f"per-stage events from {n_break} extra steps recording every stage "
+                       f"({statistics.mean(break_ms):.4f} ms per step with those events); boxcar_search_live: "
+                       "the bank's own event pair inside the timed steps (the roofline's time)")
+    res = {"workload": workload_text(name), "m": m, "w_max": w_max, "step_ms": step_ms,
+           "ms_per_step": statistics.mean(step_ms), "kernels_ms": kernels, "candidates": n_cands,
+           "deferred_blocks": n_deferred, "clocks": clocks,
+           "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "by": tiling_by}}
+    return res, plan, (d_x, d_spec, d_power)
+
+
+def rooflines(res, peak, n_sm, sm_max, name):
+    """roofline (the bank kernel alone, its live events) and roofline_search
+    (bank + deferred blocks + finaliser, the per-stage events) against the
+    FP32 add rate measured in this run; the derived rate (SMs x 128 FP32
+    lanes x the maximum SM clock) is reported beside it."""
+    m, w_max = res["m"], res["w_max"]
+    adds = m * (w_max - 1)                  # sum_{w=2}^{W} (M - w + 1) ~ M (W - 1): one add per bin and width
+    kn = res["kernels_ms"]
+    p = peak["packed_adds_per_s"] / 1e12
+    derived = n_sm * 128 * sm_max * 1e6 / 1e12
+    ach = adds / (kn["boxcar_search_live"] * 1e-3) / 1e12
+    t_search = kn["boxcar_search"] + kn["deferred_blocks"] + kn["finalise"]
+    ach_s = adds / (t_search * 1e-3) / 1e12
+    src = os.path.join(ROOT, "paper_2406_15186_gb300", "csrc", "boxcar.cu")
+    bank = {"bound": "alu", "achieved": ach, "peak": p, "unit": "TFLOP/s", "frac": ach / p,
+            "traffic": profile_traffic(src, name), "kernel": "boxcar_kernel<search>",
+            "algorithmic": f"M (W - 1) = {adds:.4g} FP32 adds per launch, 4 M = {4 * m:.4g} bytes read",
+            "peak_source": (f"pulscan_measure_add_peak in this run: packed f32x2 adds at "
+                            f"{peak['packed_sm_mhz']:.0f} MHz (scalar adds: "
+                            f"{peak['scalar_adds_per_s'] / 1e12:.2f} T/s)"),
+            "peak_derived": derived, "frac_of_derived": ach / derived,
+            "peak_derived_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (sm_max_mhz)"}
+    search = {"bound": "alu", "achieved": ach_s, "peak": p, "unit": "TFLOP/s", "frac": ach_s / p,
+              "kernels": "boxcar_kernel<search> + deferred_kernel + word_scan_kernel + finalize_kernel",
+              "time_ms": t_search, "time_source": "per-stage events of the breakdown steps"}
+    return bank, search
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2406_15186_gb300 as pkg
@@ -487,207 +646,163 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    cfg = synth.WORKLOADS[WORKLOAD]
+    name = args.workload
+    cfg = synth.WORKLOADS[name]
     n, w_max, seg_len, sigma = cfg["n"], cfg["z_max"], cfg["segment_len"], cfg["sigma"]
     m = n // 2 + 1
-    x, _ = synth.single_series(WORKLOAD)
-    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    with torch.cuda.stream(stream):
-        d_x, d_spec, d_power = plan.buffers(dev)
-        d_x.copy_(torch.from_numpy(x))
-    torch.cuda.synchronize()
-    # the timed steps record only the bank kernel's event pair (the roofline's
-    # live kernel time): every event between two kernels drains the pipeline
-    # and adds a few microseconds; the per-stage breakdown comes from extra
-    # steps with every stage's events, after the timed region
-    plan.enable_timing(2)
-
-    def step():
-        if args.no_graph:
-            plan.rfft(d_x, d_spec, stream=stream)
-            plan.power_normalise(d_spec, d_power, stream=stream)
-            plan.boxcar_search(d_power, stream=stream)
-        else:
-            # the whole path as one CUDA graph launch (pulscan_search), its
-            # timing events captured inside the graph
-            plan.search(d_x, d_spec, d_power, use_graph=True, stream=stream)
-
-    step()
-    if args.tiling:
-        plan.set_tiling(*[int(v) for v in args.tiling.split(",")])
-        tiling, tiling_by = plan.tiling(), "--tiling"
-    else:
-        tiling = plan.autotune(d_power, stream=stream)     # launch shape of the bank, timed on this input
-        tiling_by = "pulscan_plan_autotune"
-    for _ in range(args.warmup):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        step()
-    n_cands = len(plan.candidates(stream=stream))
-    n_deferred = plan.counters()[0]      # blocks the bank handed to the deferred kernel
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    k_search = []
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()                       # L2 flushed between timed steps (outside the events)
-            ev[i][0].record(stream)
-        step()
-        with torch.cuda.stream(stream):
-            ev[i][1].record(stream)
-        k_search.append(plan.timings()[2])     # the bank kernel's events in this step (same stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = max_over_ranks(statistics.mean(step_ms), dist, dev)
-    value = job_value(world, m * w_max, ms)
-
-    # per-stage breakdown: extra steps with every stage's events
-    plan.enable_timing(True)
-    step()
-    n_break = max(5, args.steps // 2)
-    k_fft, k_norm, k_bank, k_def, k_fin, break_ms = [], [], [], [], [], []
-    for _ in range(n_break):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        step()
-        with torch.cuda.stream(stream):
-            e1.record(stream)
-        t = plan.timings()
-        k_fft.append(t[0])
-        k_norm.append(t[1])
-        k_bank.append(t[2])
-        k_def.append(t[3])
-        k_fin.append(t[4])
-        torch.cuda.synchronize()
-        break_ms.append(e0.elapsed_time(e1))
-
-    # searched-width subsets (every width still summed): the same step with
-    # the z mod 8 and log2 z samplings
-    sampling = {}
-    for name, mode, stp in (("step8", 1, 8), ("log2", 2, 1)):
-        plan.set_widths(mode, stp)
-        step()
-        ts = []
-        for _ in range(max(3, args.steps // 2)):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            step()
-            t = plan.timings()
-            ts.append(t[2] + t[3] + t[4])
-        sampling[name] = {"search_ms": statistics.mean(ts), "candidates": len(plan.candidates(stream=stream))}
-    plan.set_widths(0, 1)
-    harmonic = run_harmonic(torch, pkg, synth, dev, stream, x, cfg, max(3, args.steps // 2), flush)
-    fidelity = run_fidelity(torch, pkg, plan, step, stream, max(3, args.steps // 2), flush)
-    sampling["all"] = {"search_ms": statistics.mean(k_bank) + statistics.mean(k_def) + statistics.mean(k_fin),
-                       "candidates": n_cands}
-
-    # end to end through the host-buffer entry points, as a stream of series:
-    # two plans in turn on two streams (double buffering), so one series'
-    # copy to the device runs while the previous one's search does.  Every
-    # step has its own L2 flush (on its stream, before its copy), its H2D
-    # copy of the series from pinned memory and its D2H read of candidates.
-    plan.enable_timing(False)
-    plan_b = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
-    plan_b.set_tiling(*tiling)
-    plans, streams = [plan, plan_b], [stream, torch.cuda.Stream(device=dev)]
-    x_pin = [torch.from_numpy(x).pin_memory(), torch.from_numpy(x.copy()).pin_memory()]
-    cap = min(plan.max_candidates, 1 << 16)
-
-    def issue(i):
-        k = i % 2
-        with torch.cuda.stream(streams[k]):
-            flush.zero_()
-        plans[k].search_host_async(x_pin[k], use_graph=True, stream=streams[k])
-
-    for i in range(2):                          # warm-up: both plans capture their graphs
-        issue(i)
-        plans[i].candidates(cap=cap, stream=streams[i])
-    torch.cuda.synchronize()
-    n_e2e = max(4, args.steps)
-    nc = 0
-    t0 = time.perf_counter()
-    issue(0)
-    for i in range(n_e2e):
-        if i + 1 < n_e2e:
-            issue(i + 1)
-        nc = len(plans[i % 2].candidates(cap=cap, stream=streams[i % 2]))   # waits for step i
-    e2e_ms_mean = max_over_ranks((time.perf_counter() - t0) * 1e3 / n_e2e, dist, dev)
-    plan_b.close()
-
-    peaks, peak_kind = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
+    peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
-    p_add = props.multi_processor_count * 128 * sm_max * 1e6          # FP32 adds/s
-    t_search = statistics.mean(k_search) * 1e-3
-    adds = m * (w_max - 1)
-    achieved = adds / t_search / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": p_add / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / (p_add / 1e12),
-                "traffic": profile_traffic(os.path.join(ROOT, "paper_2406_15186_gb300", "csrc", "boxcar.cu")),
-                "kernel": "boxcar_kernel<search>",
-                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
-                               f"({peak_kind} sm_max_mhz)"}
+
+    # the FP32 add rate of this GPU, measured now (the bank's roofline)
+    add_peak = pkg.measure_add_peak(reps=5, stream=stream)
+    sampler = ClockSampler(local)
+
+    def start():
+        sampler.start()
+        time.sleep(0.3)
+        if dist:
+            dist.barrier()
+
+    def stop(_):
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return sampler.stop()
+
+    head, plan, (d_x, d_spec, d_power) = time_single(torch, pkg, synth, dev, stream, flush, name, args, args.steps,
+                                                     args.warmup, around=(start, stop))
+    ms = max_over_ranks(head["ms_per_step"], dist, dev)
+    value = job_value(world, m * w_max, ms)
+    roof, roof_search = rooflines(head, add_peak, props.multi_processor_count, sm_max, name)
+    tiling = (head["bank_tiling"]["warps_per_cta"], head["bank_tiling"]["persistent"])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: N=2^23 samples (M=4194305 bins), 8 drifting tones, "
-                                   f"z_max=1024, segment_len=4096, sigma=6",
+            "config": {"workload": head["workload"],
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                       "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "by": tiling_by},
+                       "bank_tiling": head["bank_tiling"],
+                       "input": "noise from torch's seeded device generator plus the workload's tones (FP64 "
+                                "phase), drawn on the device",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "kernels_ms": {"rfft_cufft": statistics.mean(k_fft), "normalise": statistics.mean(k_norm),
-                           "boxcar_search": statistics.mean(k_bank), "deferred_blocks": statistics.mean(k_def),
-                           "finalise": statistics.mean(k_fin),
-                           "boxcar_search_live": statistics.mean(k_search),
-                           "note": f"per-stage events from {n_break} extra steps recording every stage "
-                                   f"({statistics.mean(break_ms):.4f} ms per step with those events); "
-                                   "boxcar_search_live: the bank's own event pair inside the timed steps "
-                                   "(the roofline's time)"},
-            "candidates": n_cands, "deferred_blocks": n_deferred,
-            "width_sampling": dict(sampling, note="boxcar + deferred + finalise per step; all widths summed, "
-                                                  "only the sampled ones compared (z mod 8 == 0; z a power of two)"),
-            "harmonics": harmonic,
-            "paper_gpu_fidelity": fidelity,
-            "roofline": roofline,
-            "e2e": {"value": job_value(world, m * w_max, e2e_ms_mean), "unit": UNIT,
-                    "ms_per_step": e2e_ms_mean, "h2d_bytes_per_step": 4 * n,
-                    "d2h_bytes_per_step": 16 + 32 * nc, "steps": n_e2e,
-                    "pipeline": "pulscan_search_host_async + pulscan_candidates on two plans and two "
-                                "streams in turn (a series' copy overlaps the previous search); each step "
-                                "flushes L2 on its stream before its copy; wall clock over all steps"},
+            "kernels_ms": head["kernels_ms"], "candidates": head["candidates"],
+            "deferred_blocks": head["deferred_blocks"],
+            "roofline": roof, "roofline_search": roof_search,
+            "fp32_add_peak": {"packed_T_per_s": add_peak["packed_adds_per_s"] / 1e12,
+                              "scalar_T_per_s": add_peak["scalar_adds_per_s"] / 1e12,
+                              "packed_sm_mhz": add_peak["packed_sm_mhz"], "scalar_sm_mhz": add_peak["scalar_sm_mhz"],
+                              "derived_T_per_s": props.multi_processor_count * 128 * sm_max * 1e6 / 1e12,
+                              "sm_max_mhz_source": peak_kind},
             # this library's kernels per step: normalise, bank, deferred
             # blocks, word scan, finaliser (cuFFT's own kernels not counted)
             "gpu_launches": 5 * args.steps,
-            "clocks": clocks}
-    if not args.no_batched:
-        plan.close()
-        del d_x, d_spec, d_power
-        torch.cuda.empty_cache()
+            "clocks": head["clocks"]}
+
+    if not args.only_headline:
+        # end to end through the host-buffer entry points, as a stream of
+        # series: two plans in turn on two streams (double buffering), so one
+        # series' copy to the device runs while the previous one's search
+        # does.  Every step has its own L2 flush (on its stream, before its
+        # copy), its H2D copy of the series from pinned memory and its D2H
+        # read of candidates.
+        x_host = d_x.cpu()
+        plan_b = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+        plan_b.set_tiling(*tiling)
+        plans, streams = [plan, plan_b], [stream, torch.cuda.Stream(device=dev)]
+        x_pin = [x_host.pin_memory(), x_host.clone().pin_memory()]
+        cap = min(plan.max_candidates, 1 << 20)
+
+        def issue(i):
+            k = i % 2
+            with torch.cuda.stream(streams[k]):
+                flush.zero_()
+            plans[k].search_host_async(x_pin[k], use_graph=True, stream=streams[k])
+
+        for i in range(2):                          # warm-up: both plans capture their graphs
+            issue(i)
+            plans[i].candidates(cap=cap, stream=streams[i])
+        torch.cuda.synchronize()
+        n_e2e = max(4, args.steps)
+        nc = 0
+        t0 = time.perf_counter()
+        issue(0)
+        for i in range(n_e2e):
+            if i + 1 < n_e2e:
+                issue(i + 1)
+            nc = len(plans[i % 2].candidates(cap=cap, stream=streams[i % 2]))   # waits for step i
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / n_e2e, dist, dev)
+        plan_b.close()
+        del x_pin, x_host
+        line["e2e"] = {"value": job_value(world, m * w_max, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
+                       "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 16 + 32 * nc, "steps": n_e2e,
+                       "pipeline": "pulscan_search_host_async + pulscan_candidates on two plans and two streams "
+                                   "in turn (a series' copy overlaps the previous search); each step flushes L2 on "
+                                   "its stream before its copy; wall clock over all steps"}
+    plan.close()
+    del d_x, d_spec, d_power
+    torch.cuda.empty_cache()
+
+    if not args.only_headline:
+        # the other single-series workloads, each with its own roofline
+        for other in EXTRA_SINGLE:
+            if other == name:
+                continue
+            r, p2, bufs = time_single(torch, pkg, synth, dev, stream, flush, other, args, args.steps, args.warmup)
+            b, sr = rooflines(r, add_peak, props.multi_processor_count, sm_max, other)
+            om = r["m"] * r["w_max"]
+            line[other] = {"workload": r["workload"], "value": om / (r["ms_per_step"] * 1e-3) / 1e9, "unit": UNIT,
+                           "ms_per_step": r["ms_per_step"], "kernels_ms": r["kernels_ms"],
+                           "candidates": r["candidates"], "deferred_blocks": r["deferred_blocks"],
+                           "bank_tiling": r["bank_tiling"], "roofline": b, "roofline_search": sr}
+            if other == "single_2p23":
+                # f1-f3 on this series: harmonic sums, the paper-GPU fidelity
+                # mode, and the searched-width subsets
+                d_x2 = bufs[0]
+                sub_steps = max(3, args.steps // 2)
+                ocfg = synth.WORKLOADS[other]
+                p2.enable_timing(True)
+
+                def step2():
+                    p2.search(*bufs, use_graph=True, stream=stream)
+
+                sampling = {}
+                for sname, mode, stp in (("step8", 1, 8), ("log2", 2, 1)):
+                    p2.set_widths(mode, stp)
+                    step2()
+                    ts = []
+                    for _ in range(sub_steps):
+                        with torch.cuda.stream(stream):
+                            flush.zero_()
+                        step2()
+                        t = p2.timings()
+                        ts.append(t[2] + t[3] + t[4])
+                    sampling[sname] = {"search_ms": statistics.mean(ts),
+                                       "candidates": len(p2.candidates(stream=stream))}
+                p2.set_widths(0, 1)
+                kn = r["kernels_ms"]
+                sampling["all"] = {"search_ms": kn["boxcar_search"] + kn["deferred_blocks"] + kn["finalise"],
+                                   "candidates": r["candidates"]}
+                line["width_sampling"] = dict(sampling, workload=other,
+                                              note="boxcar + deferred + finalise per step; all widths summed, only "
+                                                   "the sampled ones compared (z mod 8 == 0; z a power of two)")
+                line["harmonics"] = run_harmonic(torch, pkg, synth, dev, stream, d_x2, ocfg, sub_steps, flush)
+                line["paper_gpu_fidelity"] = run_fidelity(torch, pkg, p2, step2, stream, sub_steps, flush)
+            p2.close()
+            del bufs
+            torch.cuda.empty_cache()
+    if not args.no_batched and not args.only_headline:
         line["batched"] = run_batched(torch, pkg, synth, dev, stream, max(3, args.steps // 4))
         torch.cuda.empty_cache()
-    if not args.no_diff:
-        plan.close()
-        d_x = d_spec = d_power = None
-        torch.cuda.empty_cache()
+    if not args.no_diff and not args.only_headline:
         line["differentiable"] = run_diff(torch, pkg, synth, dev, stream, 3, args.diff_binaries)
         torch.cuda.empty_cache()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        spec, t_fft = oracle_fft(x)
-        v1, secs, desc1 = oracle_sample(spec, t_fft, cfg, 64)
-        vp, secs_p, desc_p, procs = oracle_parallel(spec, t_fft, cfg, 32, host_cores())
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.only_headline:
+        spec, t_fft, fft_desc = oracle_fft_sample(name)
+        v1, secs, desc1 = oracle_sample(spec, t_fft, fft_desc, cfg, 4)
+        vp, secs_p, desc_p, procs = oracle_parallel(spec, t_fft, fft_desc, cfg, 2, host_cores())
         line["cpu_baseline"] = {"value": vp, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": desc_p,
                                 "seconds": secs_p + t_fft,
                                 "single_core": {"value": v1, "cores": 1, "sample": desc1, "seconds": secs + t_fft}}

@@ -88,6 +88,8 @@ typedef struct {
  * Validation (PULSCAN_ERR_INVALID_ARG, nothing allocated): n >= 2 and even;
  * z_max >= 1; z_max <= segment_len <= M = n/2 + 1 (a window's halo then comes
  * from at most one neighbouring segment); threshold_sigma finite and >= 0.
+ * n < 2^33, else PULSCAN_ERR_UNSUPPORTED (start bins are 32-bit in the
+ * per-(segment, width) merge keys).
  * The Bonferroni trial count is M * z_max (reading of §2.2.3: every bin times
  * every searched width).  Allocates device scratch on the current device. */
 PULSCAN_API int pulscan_plan_create(pulscan_plan *out, int64_t n, int32_t z_max, int32_t segment_len,
@@ -265,8 +267,9 @@ PULSCAN_API int pulscan_segment_maxima(pulscan_plan plan, const float *d_power, 
  * uint64[n_seg * z_max] with the layout of pulscan_segment_maxima.  Scratch
  * is one library-owned static device array of 8 MiB (plus a small header)
  * that each GPU loading the library keeps until exit; the call itself
- * allocates nothing.  Limits: n_seg * z_max <= 2^20 and z_max <= 4096, else
- * PULSCAN_ERR_UNSUPPORTED.  The first call on a device sets up (looks up the
+ * allocates nothing.  Limits: n_seg * z_max <= 2^20, z_max <= 4096 and
+ * n < 2^33, else PULSCAN_ERR_UNSUPPORTED; all size checks come before any
+ * CUDA call.  The first call on a device sets up (looks up the
  * array's device address, raises the kernel's shared-memory limit): make it
  * before any stream capture.  All calls share the array, so calls that
  * overlap on the GPU race; serialise them. */
@@ -362,6 +365,18 @@ PULSCAN_API int pulscan_plan_counters(pulscan_plan plan, int64_t *h_out, int32_t
  * reallocates the list (4.2 KB per item; synchronises the device and drops
  * the plan's captured graph).  Errors: INVALID_ARG, NOMEM. */
 PULSCAN_API int pulscan_plan_set_defer_capacity(pulscan_plan plan, int64_t cap);
+
+/* The FP32 add rate of the current GPU, the ceiling of the boxcar bank
+ * (§2.2.5: one add per bin and width), measured rather than derived: a
+ * kernel of independent adds on every SM (8 CTAs of 256 threads per SM,
+ * 32 running sums per thread), timed with CUDA events on `stream`, best of
+ * `reps` launches after two untimed ones.  h_out[0] = adds/s with packed
+ * pairs (add.rn.f32x2), h_out[1] = adds/s with scalar adds, h_out[2], h_out[3]
+ * = the SM clock in MHz during each (clock64 ticks per globaltimer ns of the
+ * first CTA); the first min(n, 4) entries are written.  Allocates and frees
+ * a small device buffer; synchronises `stream`.  Errors: INVALID_ARG, NOMEM,
+ * CUDA. */
+PULSCAN_API int pulscan_measure_add_peak(double *h_out, int32_t n, int32_t reps, pulscan_stream stream);
 
 /* Message of the last error on this thread ("" if none). */
 PULSCAN_API const char *pulscan_last_error(void);

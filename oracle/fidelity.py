@@ -93,22 +93,6 @@ def log_p_adjusted_poly(shape, s, n_trials):
     return np.minimum(0.0, poly_logp(2.0 * np.asarray(s, dtype=np.float64), 2.0 * shape) + np.log(float(n_trials)))
 
 
-def threshold_power_poly(shape, sigma_thr, n_trials):
-    """Smallest S whose polynomial significance reaches sigma_thr (bisection;
-    the polynomial log p falls monotonically with S over its fitted range)."""
-    target = float(significance.log_sf_normal(sigma_thr)) - np.log(float(n_trials))
-    lo, hi = 0.0, 2.0 * shape + 100.0
-    while poly_logp(2.0 * hi, 2.0 * shape) > target:
-        hi *= 2.0
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        if poly_logp(2.0 * mid, 2.0 * shape) > target:
-            lo = mid
-        else:
-            hi = mid
-    return hi
-
-
 def search_power_poly(p, w_max, seg_len, sigma_thr, n_trials):
     """Candidates with the polynomial significance (same maxima as the exact
     search; only the emission rule and sigma change)."""

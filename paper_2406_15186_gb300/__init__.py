@@ -98,6 +98,7 @@ _SIGS = {
     "pulscan_plan_counters": (ctypes.c_int, [_P, _I64P, ctypes.c_int32]),
     "pulscan_plan_set_defer_capacity": (ctypes.c_int, [_P, ctypes.c_int64]),
     "pulscan_plan_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
+    "pulscan_measure_add_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, _P]),
     "pulscan_last_error": (ctypes.c_char_p, []),
     "pulscan_version": (ctypes.c_int, []),
 }
@@ -130,6 +131,16 @@ def threshold_power(shape, n_trials, sigma_thr):
     t = ctypes.c_float(0.0)
     _check(load().pulscan_threshold_power(float(shape), float(n_trials), float(sigma_thr), ctypes.byref(t)))
     return t.value
+
+
+def measure_add_peak(reps=5, stream=None):
+    """The GPU's FP32 add rate (pulscan_measure_add_peak): adds/s with packed
+    pairs and with scalar adds, and the SM clock (MHz) during each."""
+    lib = load()
+    out = (ctypes.c_double * 4)()
+    _check(lib.pulscan_measure_add_peak(out, 4, int(reps), _stream(stream)))
+    return {"packed_adds_per_s": out[0], "scalar_adds_per_s": out[1], "packed_sm_mhz": out[2],
+            "scalar_sm_mhz": out[3]}
 
 
 def _ptr(a):

@@ -78,7 +78,8 @@ extern "C" int pulscan_segment_maxima_noalloc(const float *d_power, int64_t n, i
   if ((reinterpret_cast<uintptr_t>(d_power) & 15u) != 0u)
     return fail(PULSCAN_ERR_INVALID_ARG, "power buffer must be 16-byte aligned");
   if (n < 2 || (n & 1)) return fail(PULSCAN_ERR_INVALID_ARG, "series length must be even and >= 2");
-  if (n > (int64_t(1) << 33)) return fail(PULSCAN_ERR_UNSUPPORTED, "series longer than 2^33 samples");
+  // bins are 32-bit in the (power, bin) merge keys: M = n/2 + 1 <= 2^32
+  if (n >= (int64_t(1) << 33)) return fail(PULSCAN_ERR_UNSUPPORTED, "series of 2^33 samples or more");
   const int64_t m = n / 2 + 1;
   if (z_max < 1 || segment_len < z_max || segment_len > m)
     return fail(PULSCAN_ERR_INVALID_ARG, "need 1 <= z_max <= segment_len <= n/2 + 1");

@@ -145,7 +145,8 @@ static int dalloc(T **out, size_t count) {
 
 static int check_shape(int64_t n, int32_t z_max, int32_t seg_len, double sigma) {
   if (n < 2 || (n & 1)) return fail(PULSCAN_ERR_INVALID_ARG, "series length must be even and >= 2");
-  if (n > (int64_t(1) << 33)) return fail(PULSCAN_ERR_UNSUPPORTED, "series longer than 2^33 samples");
+  // bins are 32-bit in the (power, bin) merge keys: M = n/2 + 1 <= 2^32
+  if (n >= (int64_t(1) << 33)) return fail(PULSCAN_ERR_UNSUPPORTED, "series of 2^33 samples or more");
   const int64_t m = n / 2 + 1;
   if (z_max < 1) return fail(PULSCAN_ERR_INVALID_ARG, "z_max must be >= 1");
   if (seg_len < z_max) return fail(PULSCAN_ERR_INVALID_ARG, "segment_len must be >= z_max");

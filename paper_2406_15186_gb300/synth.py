@@ -70,6 +70,21 @@ def inject(x, tones):
     return acc.astype(np.float32)
 
 
+def single_tones(name, n=None):
+    """The injected tones of one of the single-series workloads."""
+    cfg = WORKLOADS[name]
+    n = int(cfg["n"] if n is None else n)
+    rng = np.random.default_rng(seed_of(cfg["id"]) + 500_000)
+    if name == "single_2p20":
+        return [dict(amp=0.05, r0=min(100000.0, 0.4 * n), z=50.0, w=0.0,
+                     phi0=float(rng.uniform(0.0, 2.0 * np.pi)))]
+    if name == "single_2p23":
+        return tone_params(rng, n, 8, 800.0)
+    if name == "single_2p27":
+        return tone_params(rng, n, 32, 4000.0)
+    raise KeyError(name)
+
+
 def single_series(name, n=None):
     """(x, tones) for one of the single-series workloads.
 
@@ -77,18 +92,22 @@ def single_series(name, n=None):
     """
     cfg = WORKLOADS[name]
     n = int(cfg["n"] if n is None else n)
-    seed = seed_of(cfg["id"])
-    rng = np.random.default_rng(seed + 500_000)
-    if name == "single_2p20":
-        tones = [dict(amp=0.05, r0=min(100000.0, 0.4 * n), z=50.0, w=0.0,
-                      phi0=float(rng.uniform(0.0, 2.0 * np.pi)))]
-    elif name == "single_2p23":
-        tones = tone_params(rng, n, 8, 800.0)
-    elif name == "single_2p27":
-        tones = tone_params(rng, n, 32, 4000.0)
-    else:
-        raise KeyError(name)
-    return inject(noise(n, seed), tones), tones
+    tones = single_tones(name, n)
+    return inject(noise(n, seed_of(cfg["id"])), tones), tones
+
+
+def single_series_prefix(name, n_prefix):
+    """The first n_prefix samples of a single-series workload drawn on the
+    host (noise of the workload's seed, tones with u = n / N of the full
+    length N), for timing samples of a series too long to draw whole."""
+    cfg = WORKLOADS[name]
+    n = int(cfg["n"])
+    u = np.arange(int(n_prefix), dtype=np.float64) / float(n)
+    acc = noise(n_prefix, seed_of(cfg["id"])).astype(np.float64)
+    for t in single_tones(name):
+        ph = t["r0"] * u + 0.5 * t["z"] * u * u + (t.get("w", 0.0) / 6.0) * u * u * u
+        acc += t["amp"] * np.cos(2.0 * np.pi * ph + t.get("phi0", 0.0))
+    return acc.astype(np.float32)
 
 
 def batch_lengths(n_series=512, lengths=(1 << 20, 1 << 21, 1 << 22, 1 << 23), seed=None):
@@ -151,6 +170,15 @@ def device_inject(x, tones):
         acc += t["amp"] * torch.cos(2.0 * np.pi * ph + t.get("phi0", 0.0))
     x.copy_(acc.to(torch.float32))
     return x
+
+
+def single_series_device(name, x):
+    """Fill x (device, float32[N]) with a single-series workload: noise from
+    the device generator seeded with the workload's seed, plus the
+    workload's tones (the same draws as single_series)."""
+    cfg = WORKLOADS[name]
+    x.copy_(device_noise(int(cfg["n"]), seed_of(cfg["id"]), device=x.device))
+    return device_inject(x, single_tones(name))
 
 
 def batch_device(x_all, offsets, lengths, tone_mask, workload_id=3):

@@ -77,3 +77,22 @@ def test_candidate_record_layout():
     import paper_2406_15186_gb300 as pkg
     assert pkg.CAND_DTYPE.itemsize == 32
     assert [pkg.CAND_DTYPE.fields[k][1] for k in ("series", "width", "bin", "power", "sigma")] == [0, 4, 8, 16, 20]
+
+
+def test_noalloc_refuses_before_any_cuda_call(lib):
+    """pulscan_segment_maxima_noalloc checks every size against the static
+    array before it touches CUDA, so refusals need no GPU: the pointers here
+    are aligned stand-ins that are never dereferenced."""
+    fake = ctypes.c_void_p(1 << 12)
+    f = lib.pulscan_segment_maxima_noalloc
+    assert f(fake, 1 << 22, 64, 64, fake, fake, None) == -6        # 2^21 segments x 64 widths > 2^20 slots
+    assert f(fake, (1 << 21) + 1024, 256, 256, fake, fake, None) == -6   # 4098 segments x 256 > 2^20
+    assert f(fake, 1 << 24, 5000, 8192, fake, fake, None) == -6     # z_max above 4096
+    assert f(fake, 1 << 33, 4, 16, fake, fake, None) == -6          # bins would not fit 32 bits
+    assert f(fake, 1023, 4, 16, fake, fake, None) == -1             # odd n
+    assert f(fake, 1024, 32, 16, fake, fake, None) == -1            # segment_len < z_max
+    assert f(ctypes.c_void_p((1 << 12) + 4), 1024, 4, 16, fake, fake, None) == -1   # unaligned power
+    assert f(None, 1024, 4, 16, fake, fake, None) == -1
+    assert lib.pulscan_last_error()
+    h = ctypes.c_void_p()
+    assert lib.pulscan_plan_create(ctypes.byref(h), 1 << 33, 4, 16, 6.0) == -6

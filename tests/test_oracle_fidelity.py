@@ -90,3 +90,47 @@ def test_mom_normalisation_of_noise():
     assert not flags.any()
     assert abs(p.mean() - 1.0) < 0.1
     assert np.all(np.abs(st[:, [1, 3]] * fidelity.MOM_SCALE - 1.0) < 0.15)
+
+
+def test_mom_last_block_uses_the_statistics_of_its_first_4k_bins():
+    """Hand case of the reading taken for §2.5's median of medians: blocks of
+    4 bins (4^1), M = 9, so the last block holds bins 4..8 and its fifth bin
+    is normalised with the statistics of bins 4..7.  Re(4..7) = 1, 2, 3, 4:
+    median lm(1, 2, 3, 4) = 2.5, deviations 1.5, 0.5, 0.5, 1.5, MAD 1.  Im(4..7)
+    = 1, -1, 2, -2: median (1 + -1) / 2 = 0, deviations 1, 1, 2, 2, MAD 1.5.
+    Bin 8 = 10 + 5i: a = 7.5 / 1.4826, b = 5 / (1.4826 * 1.5)."""
+    spec = np.zeros(9, dtype=complex)
+    spec[0:4] = [7.0 + 7.0j, 1.0 - 2.0j, -3.0 + 0.5j, 2.0 + 1.0j]
+    spec[4:9] = [1.0 + 1.0j, 2.0 - 1.0j, 3.0 + 2.0j, 4.0 - 2.0j, 10.0 + 5.0j]
+    p, st, flags = fidelity.normalise_power_mom(spec, 4)
+    assert not flags.any() and st.shape == (2, 4)
+    assert tuple(st[1]) == (2.5, 1.0, 0.0, 1.5)
+    a, b = 7.5 / 1.4826, 5.0 / (1.4826 * 1.5)
+    assert p[8] == pytest.approx(0.5 * (a * a + b * b), rel=1e-15)
+    # bins 4..7 with the same statistics
+    re, im = np.array([1.0, 2.0, 3.0, 4.0]), np.array([1.0, -1.0, 2.0, -2.0])
+    want = 0.5 * (((re - 2.5) / 1.4826) ** 2 + (im / (1.4826 * 1.5)) ** 2)
+    assert np.allclose(p[4:8], want, rtol=1e-15, atol=0)
+    # the first block: DC taken as 0, so Re = 0, 1, -3, 2 -> lm = (0 + 1) / 2
+    assert st[0, 0] == 0.5
+    # had bin 8 entered the statistics, the median of Re would differ
+    assert np.median(np.array([1.0, 2.0, 3.0, 4.0, 10.0])) != st[1, 0]
+
+
+def test_polynomial_log_p_equals_eqs_10_to_12_by_polyval():
+    """Eqs. 10-12 evaluated independently: numpy.polyval on the golden
+    coefficients, x = A1 dof / pow, log p = pow f(x) / A1; zero from the
+    1.05 cutoff on."""
+    vals = {}
+    for ln in open(os.path.join(HERE, "golden", "logp_polynomial.txt")):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        k, v = ln.split()
+        vals[k] = float(v)
+    coeffs = [vals[f"c{i}"] for i in range(16, -1, -1)]
+    for pow_, dof in ((2048.0, 512.0), (1200.0, 200.0), (4096.0, 2048.0), (300.0, 64.0), (150.0, 140.0)):
+        x = vals["A1"] * dof / pow_
+        want = pow_ * np.polyval(coeffs, x) / vals["A1"]
+        assert float(fidelity.poly_logp(pow_, dof)) == pytest.approx(want, rel=1e-12, abs=1e-12)
+    assert float(fidelity.poly_logp(100.0, 105.0)) == 0.0           # dof = 1.05 pow: cut off
+    assert float(fidelity.poly_logp(100.0, 104.9)) != 0.0

@@ -51,3 +51,8 @@ def test_workload_sizes():
     assert (w["batch_512"]["n_series"], w["batch_512"]["z_max"], w["batch_512"]["segment_len"]) == (512, 512, 2048)
     assert (w["diff_4096"]["n_series"], w["diff_4096"]["n"], w["diff_4096"]["tau"]) == (4096, 1 << 20, 0.1)
     assert (w["single_2p27"]["n"], w["single_2p27"]["z_max"], w["single_2p27"]["sigma"]) == (1 << 27, 4096, 7.0)
+
+
+def test_prefix_draw_is_the_prefix_of_the_whole_series():
+    x, _ = synth.single_series("single_2p20")
+    assert np.array_equal(synth.single_series_prefix("single_2p20", 1 << 12), x[: 1 << 12])

@@ -57,8 +57,9 @@ def parse():
                     help="run the differentiable measurement on its first N binaries only (profiling)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the step's stages one by one instead of as one CUDA graph")
-    ap.add_argument("--tiling", default=None, metavar="WARPS,PERSISTENT",
-                    help="bank launch shape of the single-series plan instead of the autotuner (e.g. 4,0)")
+    ap.add_argument("--tiling", default=None, metavar="WARPS,PERSISTENT,PACKED",
+                    help="bank launch shape of the single-series plan instead of the autotuner (e.g. 4,0,1: 4 warps "
+                         "per CTA, one CTA per tile, packed adds)")
     return ap.parse_args()
 
 
@@ -369,7 +370,8 @@ def run_batched(torch, pkg, synth, dev, stream, steps):
             "dm_trials_per_s": len(lengths) / (t_b * 1e-3), "ms_per_batch": t_b,
             "per_series_dm_trials_per_s": len(lengths) / (t_s * 1e-3), "ms_per_series_loop": t_s,
             "ratio_batched_vs_per_series": t_s / t_b, "bin_widths_per_s": bins * w_max / (t_b * 1e-3) / 1e9,
-            "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "by": "pulscan_plan_autotune"},
+            "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "packed": tiling[2],
+                            "by": "pulscan_plan_autotune"},
             "unit": "G bin-widths/s", "candidates": n_cands, "graph": True,
             "per_series": "the same kernels launched per series on one stream (no graph), one plan per length",
             "l2": "inputs (8.2 GB) far larger than L2"}
@@ -475,17 +477,18 @@ def run_diff(torch, pkg, synth, dev, stream, steps, n_binaries=None):
     stats = torch.empty(4 * plan.total_segments, **f32)
     sel = torch.empty(8 * plan.total_segments, **f32)
     y = torch.empty(plan.total_segments * w_max, **f32)
+    ylo = torch.empty_like(y)
     gy = torch.ones_like(y)
     gx = torch.empty(plan.x_floats, **f32)
     gamp = torch.empty(n_series, **f32)
 
     def fwd():
         return lib.pulscan_lse_forward(plan._h, x.data_ptr(), spec.data_ptr(), power.data_ptr(), stats.data_ptr(),
-                                       sel.data_ptr(), y.data_ptr(), tau, sp)
+                                       sel.data_ptr(), y.data_ptr(), ylo.data_ptr(), tau, sp)
 
     def bwd():
         rc = lib.pulscan_lse_backward(plan._h, spec.data_ptr(), power.data_ptr(), stats.data_ptr(), sel.data_ptr(),
-                                      y.data_ptr(), gy.data_ptr(), gx.data_ptr(), tau, sp)
+                                      y.data_ptr(), ylo.data_ptr(), gy.data_ptr(), gx.data_ptr(), tau, sp)
         return rc or lib.pulscan_amplitude_grad(plan._h, gx.data_ptr(), tmpl.data_ptr(), gamp.data_ptr(), sp)
 
     def timed(fn, reps):
@@ -600,7 +603,7 @@ def time_single(torch, pkg, synth, dev, stream, flush, name, args, steps, warmup
     res = {"workload": workload_text(name), "m": m, "w_max": w_max, "step_ms": step_ms,
            "ms_per_step": statistics.mean(step_ms), "kernels_ms": kernels, "candidates": n_cands,
            "deferred_blocks": n_deferred, "clocks": clocks,
-           "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "by": tiling_by}}
+           "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "packed": tiling[2], "by": tiling_by}}
     return res, plan, (d_x, d_spec, d_power)
 
 
@@ -677,7 +680,7 @@ def run_ours(args, rank, world, local):
     ms = max_over_ranks(head["ms_per_step"], dist, dev)
     value = job_value(world, m * w_max, ms)
     roof, roof_search = rooflines(head, add_peak, props.multi_processor_count, sm_max, name)
-    tiling = (head["bank_tiling"]["warps_per_cta"], head["bank_tiling"]["persistent"])
+    tiling = (head["bank_tiling"]["warps_per_cta"], head["bank_tiling"]["persistent"], head["bank_tiling"]["packed"])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -186,18 +186,31 @@ PULSCAN_API int pulscan_plan_set_fidelity(pulscan_plan plan, int32_t mode);
 
 /* Autotuner of the bank's launch shape: runs the search (bank, deferred
  * blocks, finaliser) on the caller's normalised power d_power three times for
- * each of 1, 2, 3 and 4 warps per CTA (tile = 1056 x warps bins) with one CTA
- * per tile and with a persistent grid of per-SM tile ranges, and keeps the
- * fastest.  Segment length, widths and halo are fixed by the search itself,
- * so the candidates do not depend on the choice.  Synchronises `stream`,
- * discards the candidates of the trial runs and drops the plan's captured
- * graph.  pulscan_plan_tiling reports the current choice (persistent: -1
- * automatic, the default; 0 one CTA per tile; 1 persistent). */
+ * each of 1, 2, 3 and 4 warps per CTA, in the scalar form (a warp owns 1056
+ * start bins, tile = 1056 x warps) and the packed form (a warp owns two 1056-
+ * bin slices and adds them pairwise with add.f32x2, tile = 2112 x warps),
+ * each with one CTA per tile and with a persistent grid of per-SM tile
+ * ranges, and keeps the fastest.  Segment length, widths and halo are fixed
+ * by the search itself, and the two forms perform the same FP32 adds in the
+ * same order, so the candidates do not depend on the choice.  Synchronises
+ * `stream`, discards the candidates of the trial runs and drops the plan's
+ * captured graph.  pulscan_plan_tiling reports the current choice
+ * (persistent: -1 automatic, the default; 0 one CTA per tile; 1 persistent;
+ * packed: 0 scalar, 1 packed). */
 PULSCAN_API int pulscan_plan_autotune(pulscan_plan plan, const float *d_power, pulscan_stream stream);
-PULSCAN_API int pulscan_plan_tiling(pulscan_plan plan, int32_t *warps, int32_t *persistent);
-/* Set the launch shape directly (warps 1 to 4; persistent -1, 0 or 1).
- * Synchronises the device.  Errors: INVALID_ARG. */
-PULSCAN_API int pulscan_plan_set_tiling(pulscan_plan plan, int32_t warps, int32_t persistent);
+PULSCAN_API int pulscan_plan_tiling(pulscan_plan plan, int32_t *warps, int32_t *persistent, int32_t *packed);
+/* Set the launch shape directly (warps 1 to 4; persistent -1, 0 or 1;
+ * packed 0 or 1).  Synchronises the device.  Errors: INVALID_ARG. */
+PULSCAN_API int pulscan_plan_set_tiling(pulscan_plan plan, int32_t warps, int32_t persistent, int32_t packed);
+
+/* A test of the search's bounded-wait path that faults nothing: arms the
+ * plan's next boxcar search so that its bank kernel issues no copy into
+ * its staging buffer and waits on that copy's barrier for limit_us
+ * microseconds (1..1000), then flags the timeout and exits, with nothing in
+ * flight; pulscan_candidates of that search returns PULSCAN_ERR_TIMEOUT (and
+ * no candidates), and the search after it runs normally.  pulscan_search
+ * runs an armed search outside its CUDA graph.  Errors: INVALID_ARG. */
+PULSCAN_API int pulscan_plan_test_wait_timeout(pulscan_plan plan, int32_t limit_us);
 
 /* Approximate r-bin output (§2.4, "Pulscan R-Block"): with block_width > 0,
  * pulscan_candidates / pulscan_search_host report in `bin` the block index
@@ -309,14 +322,18 @@ PULSCAN_API int pulscan_search_host_async(pulscan_plan plan, const float *h_x, i
  * float[4 * total_segments] and d_sel float[8 * total_segments] (the
  * selected order statistics the adjoint needs) are written and must be kept
  * for pulscan_lse_backward; d_y float[total_segments * z_max] (row = segment,
- * column = w - 1).  Terms more than tau ln(2^24 L) below the segment maximum
+ * column = w - 1) and d_ylo (same layout): Y's FP32 rounding error, so that
+ * d_y + d_ylo carries Y well below FP32 resolution (the adjoint's softmax
+ * weights exp((S - Y) / tau) amplify an error in Y by 1 / tau); keep it for
+ * pulscan_lse_backward.  Terms more than tau ln(2^24 L) below the segment maximum
  * are skipped: they are below FP32 resolution of the sum.  tau > 0.
  * Segments must be at most 4224 bins (else PULSCAN_ERR_UNSUPPORTED). */
 PULSCAN_API int pulscan_lse_forward(pulscan_plan plan, const float *d_x, float *d_spec, float *d_power,
-                                    float *d_stats, float *d_sel, float *d_y, float tau, pulscan_stream stream);
+                                    float *d_stats, float *d_sel, float *d_y, float *d_ylo, float tau,
+                                    pulscan_stream stream);
 
 /* Adjoint of pulscan_lse_forward: given d_gy = dL/dY (same layout as d_y)
- * and the forward's d_spec, d_power, d_stats, d_sel, d_y, writes
+ * and the forward's d_spec, d_power, d_stats, d_sel, d_y, d_ylo, writes
  * d_gx = dL/dx float[x_floats].  The chain: softmax weights; the boxcar
  * scatter dL/dP[j] = sum_w sum_{k=j-w+1..j} dL/dS_w[k]; P = (a^2 + b^2)/2;
  * the median / MAD normalisation with its almost-everywhere derivatives at
@@ -325,8 +342,9 @@ PULSCAN_API int pulscan_lse_forward(pulscan_plan plan, const float *d_x, float *
  * use (dL/dP, the segment tails, the C2R input); overlapping backward calls
  * on one plan race. */
 PULSCAN_API int pulscan_lse_backward(pulscan_plan plan, const float *d_spec, const float *d_power,
-                                     const float *d_stats, const float *d_sel, const float *d_y, const float *d_gy,
-                                     float *d_gx, float tau, pulscan_stream stream);
+                                     const float *d_stats, const float *d_sel, const float *d_y,
+                                     const float *d_ylo, const float *d_gy, float *d_gx, float tau,
+                                     pulscan_stream stream);
 
 /* Synthetic signal model of the differentiable workload (§2.1, Eq. 1):
  * d_x = d_noise + amp[i] * d_template for every series i (all

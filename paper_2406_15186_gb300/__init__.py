@@ -75,8 +75,10 @@ _SIGS = {
     "pulscan_plan_set_rblock": (ctypes.c_int, [_P, ctypes.c_int64]),
     "pulscan_plan_set_fidelity": (ctypes.c_int, [_P, ctypes.c_int32]),
     "pulscan_plan_autotune": (ctypes.c_int, [_P, _P, _P]),
-    "pulscan_plan_tiling": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
-    "pulscan_plan_set_tiling": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "pulscan_plan_tiling": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    "pulscan_plan_set_tiling": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "pulscan_plan_test_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int32]),
     "pulscan_plan_thresholds": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pulscan_threshold_power": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                ctypes.POINTER(ctypes.c_float)]),
@@ -90,8 +92,8 @@ _SIGS = {
     "pulscan_search": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
     "pulscan_search_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _I64P, ctypes.c_int, _P]),
     "pulscan_search_host_async": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
-    "pulscan_lse_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, _P]),
-    "pulscan_lse_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float, _P]),
+    "pulscan_lse_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float, _P]),
+    "pulscan_lse_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float, _P]),
     "pulscan_inject": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "pulscan_amplitude_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pulscan_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -247,13 +249,18 @@ class Plan:
         _check(load().pulscan_plan_autotune(self._h, _ptr(d_power), _stream(stream)))
         return self.tiling()
 
-    def set_tiling(self, warps, persistent=-1):
-        _check(load().pulscan_plan_set_tiling(self._h, int(warps), int(persistent)))
+    def set_tiling(self, warps, persistent=-1, packed=0):
+        _check(load().pulscan_plan_set_tiling(self._h, int(warps), int(persistent), int(packed)))
 
     def tiling(self):
-        w, m = ctypes.c_int32(0), ctypes.c_int32(0)
-        _check(load().pulscan_plan_tiling(self._h, ctypes.byref(w), ctypes.byref(m)))
-        return w.value, m.value
+        """(warps per CTA, persistent, packed) of the bank's launch shape."""
+        w, m, k = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().pulscan_plan_tiling(self._h, ctypes.byref(w), ctypes.byref(m), ctypes.byref(k)))
+        return w.value, m.value, k.value
+
+    def test_wait_timeout(self, limit_us=20):
+        """Arm the next search to exercise its timeout path (pulscan_plan_test_wait_timeout)."""
+        _check(load().pulscan_plan_test_wait_timeout(self._h, int(limit_us)))
 
     def set_rblock(self, block_width):
         """Report block indices floor(bin / block_width) instead of bins (0: exact bins)."""

@@ -208,10 +208,12 @@ __device__ __forceinline__ int series_of_tile(const int64_t *__restrict__ tile_o
   return lo;
 }
 
-// Deferred block: (tile, warp, block, first step) packed in 64 bits.
+// Deferred block: (tile, virtual warp, block, first step) packed in 64 bits:
+// tile in bits 0-39, the virtual warp (the 1056-bin slice of the tile, 0..7)
+// in 40-42, the 33-width block in 43-55, the first step in 56-63.
 __device__ __forceinline__ unsigned long long pack_item(int64_t tile, int warp, int bi, int cx) {
   return static_cast<unsigned long long>(tile) | (static_cast<unsigned long long>(warp) << 40) |
-         (static_cast<unsigned long long>(bi) << 42) | (static_cast<unsigned long long>(cx) << 56);
+         (static_cast<unsigned long long>(bi) << 43) | (static_cast<unsigned long long>(cx) << 56);
 }
 
 // Defer the rest of block bi (steps cx..) of this warp: append a work item
@@ -232,15 +234,178 @@ __device__ __forceinline__ bool defer_block(const float (&s)[kR], unsigned long 
   return true;
 }
 
+// Two adds in one instruction: (a, b) += (x, y) by add.rn.f32x2, the packed
+// FP32 add of sm_100 and later.  Each half rounds exactly as a scalar
+// add.rn.f32 would, so the sums are bit-identical to the scalar bank's.
+__device__ __forceinline__ void add_pair(float &a, float &b, float x, float y) {
+  asm("{\n\t.reg .b64 s, v;\n\t"
+      "mov.b64 s, {%0, %1};\n\t"
+      "mov.b64 v, {%2, %3};\n\t"
+      "add.rn.f32x2 s, s, v;\n\t"
+      "mov.b64 {%0, %1}, s;\n\t}"
+      : "+f"(a), "+f"(b)
+      : "f"(x), "f"(y));
+}
+
+// Packed form of fast_steps: a lane carries two 33-bin groups (A and B, 1056
+// bins apart) with one ring each, and adds them pairwise.
+template <int C0, int NC>
+__device__ __forceinline__ void fast_steps2(float (&sA)[kR], float (&sB)[kR], float (&bA)[kR], float (&bB)[kR],
+                                            const float *__restrict__ pA, const float *__restrict__ pB) {
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc) {
+    const int c = C0 + cc;
+    bA[(c + kR - 1) % kR] = pA[c + kR - 1];
+    bB[(c + kR - 1) % kR] = pB[c + kR - 1];
+#pragma unroll
+    for (int i = 0; i < kR; ++i) add_pair(sA[i], sB[i], bA[(i + c) % kR], bB[(i + c) % kR]);
+  }
+}
+
+// The search over one staged tile with packed adds (two virtual warps per
+// warp).  The block logic is the scalar one's, once per group: a group whose
+// bound reaches the threshold is deferred (its own item and snapshot) while
+// both groups go on with packed adds; if the item list is full, the rest of
+// that block runs in scalar code for both groups (the flagged one exactly).
+// The lane contexts are only needed on that rare path and are formed there
+// (from the series descriptor in global memory), so they hold no registers
+// in the packed loop.
+__device__ __forceinline__ void packed_bank(const float *__restrict__ buf, const float *__restrict__ q11,
+                                         const float *__restrict__ q33, const SeriesDev &S0, int si, int64_t tile,
+                                         int64_t t0, int tile_bins, int W, int seg_len, const float *__restrict__ thr,
+                                         const float *__restrict__ thrb, unsigned long long *__restrict__ slots,
+                                         uint32_t *__restrict__ dirty, uint32_t *__restrict__ counters,
+                                         unsigned long long *__restrict__ items, float *__restrict__ snaps,
+                                         uint32_t item_cap, const SeriesDev *__restrict__ series) {
+  (void)S0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int vA = 2 * warp, vB = 2 * warp + 1;
+  const int xA = vA * (32 * kR) + lane * kR, xB = xA + 32 * kR;
+  const float *lA = buf + xA, *lB = buf + xB;
+  float sA[kR], sB[kR], bA[kR], bB[kR];
+#pragma unroll
+  for (int i = 0; i < kR; ++i) {
+    sA[i] = 0.0f;
+    sB[i] = 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < kR - 1; ++j) {
+    bA[j] = lA[j];
+    bB[j] = lB[j];
+  }
+  bA[kR - 1] = 0.0f;
+  bB[kR - 1] = 0.0f;
+  const int nb = (W + kR - 1) / kR;
+  const int qbA = xA / kSub, qcA = xA / kR, qbB = xB / kSub, qcB = xB / kR;
+  // the rest of block bi from step cb in scalar code; a group flagged ex
+  // runs exactly (every window compared), the other one plain adds
+  auto finish_scalar = [&](int bi, int cb, int nsteps, bool exA, bool exB) {
+    const SeriesDev S = series[si];
+    const int wf = bi * kR + 1;
+    if (exA) {
+      const LaneCtx c = lane_ctx(S, t0, tile_bins, vA, lane, W, seg_len, slots, dirty);
+      exact_steps<true>(sA, lA, wf, cb, nsteps, thr, c);
+    } else {
+      tail_steps(sA, lA, wf + cb, wf + nsteps);
+    }
+    if (exB) {
+      const LaneCtx c = lane_ctx(S, t0, tile_bins, vB, lane, W, seg_len, slots, dirty);
+      exact_steps<true>(sB, lB, wf, cb, nsteps, thr, c);
+    } else {
+      tail_steps(sB, lB, wf + cb, wf + nsteps);
+    }
+    reload_ring<kR>(bA, lA + bi * kR);
+    reload_ring<kR>(bB, lB + bi * kR);
+  };
+  for (int bi = 0; bi < nb; ++bi) {
+    const float *pA = lA + bi * kR, *pB = lB + bi * kR;
+    const int wf = bi * kR + 1;
+    const int nsteps = min(kR, W - bi * kR);
+    const bool early = bi < kEarlyBlocks;
+    bool defA = false, defB = false, exA = false, exB = false;
+    {
+      const float tb = thrb[wf - 1];
+      const bool hA = early ? early_bound(sA, q11, qbA + 3 * bi, tb)
+                            : (sA[0] + q33[qcA + bi] + q33[qcA + bi + 1] >= tb);
+      const bool hB = early ? early_bound(sB, q11, qbB + 3 * bi, tb)
+                            : (sB[0] + q33[qcB + bi] + q33[qcB + bi + 1] >= tb);
+      if (__any_sync(kFull, hA)) {
+        if (defer_block(sA, items, snaps, counters, item_cap, tile, vA, bi, 0)) defA = true;
+        else exA = true;
+      }
+      if (__any_sync(kFull, hB)) {
+        if (defer_block(sB, items, snaps, counters, item_cap, tile, vB, bi, 0)) defB = true;
+        else exB = true;
+      }
+    }
+    if (exA || exB) {
+      finish_scalar(bi, 0, nsteps, exA, exB);
+      continue;
+    }
+    if (nsteps < kSub) {
+      tail_steps(sA, lA, wf, wf + nsteps);
+      tail_steps(sB, lB, wf, wf + nsteps);
+      continue;
+    }
+    fast_steps2<0, kSub>(sA, sB, bA, bB, pA, pB);
+    if (early && nsteps > kSub) {
+      const float tb = thrb[wf + kSub - 1];
+      if (!defA && __any_sync(kFull, early_bound(sA, q11, qbA + 3 * bi + 1, tb))) {
+        if (defer_block(sA, items, snaps, counters, item_cap, tile, vA, bi, kSub)) defA = true;
+        else exA = true;
+      }
+      if (!defB && __any_sync(kFull, early_bound(sB, q11, qbB + 3 * bi + 1, tb))) {
+        if (defer_block(sB, items, snaps, counters, item_cap, tile, vB, bi, kSub)) defB = true;
+        else exB = true;
+      }
+      if (exA || exB) {
+        finish_scalar(bi, kSub, nsteps, exA, exB);
+        continue;
+      }
+    }
+    if (nsteps < 2 * kSub) {
+      tail_steps(sA, lA, wf + kSub, wf + nsteps);
+      tail_steps(sB, lB, wf + kSub, wf + nsteps);
+      continue;
+    }
+    fast_steps2<kSub, kSub>(sA, sB, bA, bB, pA, pB);
+    if (early && nsteps > 2 * kSub) {
+      const float tb = thrb[wf + 2 * kSub - 1];
+      if (!defA && __any_sync(kFull, early_bound(sA, q11, qbA + 3 * bi + 2, tb))) {
+        if (!defer_block(sA, items, snaps, counters, item_cap, tile, vA, bi, 2 * kSub)) exA = true;
+      }
+      if (!defB && __any_sync(kFull, early_bound(sB, q11, qbB + 3 * bi + 2, tb))) {
+        if (!defer_block(sB, items, snaps, counters, item_cap, tile, vB, bi, 2 * kSub)) exB = true;
+      }
+      if (exA || exB) {
+        finish_scalar(bi, 2 * kSub, nsteps, exA, exB);
+        continue;
+      }
+    }
+    if (nsteps < kR) {
+      tail_steps(sA, lA, wf + 2 * kSub, wf + nsteps);
+      tail_steps(sB, lB, wf + 2 * kSub, wf + nsteps);
+      continue;
+    }
+    fast_steps2<2 * kSub, kSub>(sA, sB, bA, bB, pA, pB);
+  }
+}
+
 // One tile: stage P[t0, t0 + buf_len) by a TMA bulk copy, form the bound
 // sums, run the bank.  Returns false when the copy timed out (flagged).
-template <bool kSearch>
+// groups = 1: warp v owns bins [1056 v, 1056 (v + 1)) of the tile, a lane 33
+// of them.  groups = 2 (tiles twice as wide): warp v owns the two slices
+// ("virtual warps") 2v and 2v + 1; in search mode (kPacked) each lane carries
+// one 33-bin group of each and adds both with packed instructions, in dump
+// mode the warp runs the two slices one after the other.  A virtual warp is
+// the unit of the deferred-block items either way.
+template <bool kSearch, bool kPacked>
 __device__ __forceinline__ bool boxcar_tile(
     int64_t tile, unsigned char *smem_raw, const float *__restrict__ power, const SeriesDev *__restrict__ series,
     const int64_t *__restrict__ tile_off, int n_series, int W, int seg_len, const float *__restrict__ thr_all,
     const float *__restrict__ thrb_all, unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty,
     uint32_t *__restrict__ counters, unsigned long long *__restrict__ items, float *__restrict__ snaps,
-    uint32_t item_cap, int tile_bins, int buf_len) {
+    uint32_t item_cap, int tile_bins, int buf_len, int groups, uint32_t wait_test) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
   const int nq33 = buf_len / kR;        // 33-bin block sums
@@ -260,13 +425,18 @@ __device__ __forceinline__ bool boxcar_tile(
 
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
-  if (threadIdx.x == 0 && n_tma > 0) {
+  // wait_test != 0 (a test of the timeout path): no copy is issued, so the
+  // barrier never completes and the bounded wait below gives up after
+  // wait_test microseconds with nothing in flight
+  if (threadIdx.x == 0 && n_tma > 0 && wait_test == 0u) {
     mbar_arrive_expect_tx(bar, static_cast<uint32_t>(n_tma) * 4u);
     tma_load_1d(buf, src, static_cast<uint32_t>(n_tma) * 4u, bar);
   }
   for (int i = n_tma + threadIdx.x; i < buf_len; i += nthreads) buf[i] = (i < avail) ? src[i] : 0.0f;
   // one thread waits on the copy (bounded); the others sleep in the barrier
-  if (threadIdx.x == 0) q33[0] = (n_tma == 0 || mbar_wait_bounded(bar, 0, 2000000000ull)) ? 1.0f : 0.0f;
+  const uint64_t limit_ns = wait_test ? 1000ull * wait_test : 2000000000ull;
+  if (threadIdx.x == 0)
+    q33[0] = ((n_tma == 0 && wait_test == 0u) || mbar_wait_bounded(bar, 0, limit_ns)) ? 1.0f : 0.0f;
   __syncthreads();
   if (q33[0] == 0.0f) {
     if (threadIdx.x == 0) atomicOr(counters + 2, kErrTimeout);
@@ -288,20 +458,33 @@ __device__ __forceinline__ bool boxcar_tile(
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int x0 = warp * (32 * kR) + lane * kR;   // buffer-relative first bin
-  const LaneCtx c = lane_ctx(S, t0, tile_bins, warp, lane, W, seg_len, slots, dirty);
   const float *thr = thr_all + static_cast<int64_t>(si) * W;
   const float *thrb = thrb_all + static_cast<int64_t>(si) * W;
 
+  if (!kSearch) {
+    // every (segment, width) maximum: each of the warp's slices in turn
+    for (int g = 0; g < groups; ++g) {
+      const int vw = warp * groups + g;
+      const LaneCtx c = lane_ctx(S, t0, tile_bins, vw, lane, W, seg_len, slots, dirty);
+      float s[kR];
+#pragma unroll
+      for (int i = 0; i < kR; ++i) s[i] = 0.0f;
+      exact_steps<false>(s, buf + vw * (32 * kR) + lane * kR, 1, 0, W, thr, c);
+    }
+    return true;
+  }
+  if (kPacked) {
+    packed_bank(buf, q11, q33, S, si, tile, t0, tile_bins, W, seg_len, thr, thrb, slots, dirty, counters, items,
+                snaps, item_cap, series);
+    return true;
+  }
+
+  const int x0 = warp * (32 * kR) + lane * kR;   // buffer-relative first bin
+  const LaneCtx c = lane_ctx(S, t0, tile_bins, warp, lane, W, seg_len, slots, dirty);
   float s[kR], b[kR];
 #pragma unroll
   for (int i = 0; i < kR; ++i) s[i] = 0.0f;
   const float *lane_buf = buf + x0;
-
-  if (!kSearch) {
-    exact_steps<false>(s, lane_buf, 1, 0, W, thr, c);
-    return true;
-  }
 
 #pragma unroll
   for (int j = 0; j < kR - 1; ++j) b[j] = lane_buf[j];
@@ -388,17 +571,21 @@ __device__ __forceinline__ uint32_t sm_id() {
 // places the CTAs, and no tile is left while any CTA runs.  (A
 // one-CTA-per-tile grid refills the SMs that free their slots first, which
 // leaves a partial last wave on some SMs only.)
-template <bool kSearch>
-__global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
+// kPacked (search mode only): two virtual warps per warp with packed adds,
+// at most 170 registers per thread (three 4-warp CTAs per SM).
+template <bool kSearch, bool kPacked>
+__global__ void __launch_bounds__(kMaxThreads, kPacked ? 3 : kMinBlocks) boxcar_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
     int n_series, int W, int seg_len, const float *__restrict__ thr_all, const float *__restrict__ thrb_all,
     unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty, uint32_t *__restrict__ counters,
     unsigned long long *__restrict__ items, float *__restrict__ snaps, uint32_t item_cap, int tile_bins,
-    int buf_len, uint32_t *__restrict__ tile_ctr, const int64_t *__restrict__ range_lo, int n_ranges) {
+    int buf_len, uint32_t *__restrict__ tile_ctr, const int64_t *__restrict__ range_lo, int n_ranges, int groups,
+    uint32_t wait_test) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (tile_ctr == nullptr) {
-    boxcar_tile<kSearch>(blockIdx.x, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all, thrb_all,
-                         slots, dirty, counters, items, snaps, item_cap, tile_bins, buf_len);
+    boxcar_tile<kSearch, kPacked>(blockIdx.x, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all,
+                                  thrb_all, slots, dirty, counters, items, snaps, item_cap, tile_bins, buf_len, groups,
+                                  wait_test);
     return;
   }
   int64_t *claim = reinterpret_cast<int64_t *>(smem_raw + 64);
@@ -442,8 +629,9 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks) boxcar_kernel(
     __syncthreads();
     if (tile < 0) return;
     if (threadIdx.x == 0) mine = claim_home();
-    if (!boxcar_tile<kSearch>(tile, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all, thrb_all,
-                              slots, dirty, counters, items, snaps, item_cap, tile_bins, buf_len))
+    if (!boxcar_tile<kSearch, kPacked>(tile, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all,
+                                       thrb_all, slots, dirty, counters, items, snaps, item_cap, tile_bins, buf_len,
+                                       groups, wait_test))
       return;
     __syncthreads();   // the tile's shared memory is free for the next one
   }
@@ -565,8 +753,8 @@ __global__ void __launch_bounds__(kDeferThreads, 8) deferred_kernel(
   for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const unsigned long long item = items[it];
     const int64_t tile = static_cast<int64_t>(item & 0xffffffffffull);
-    const int wv = static_cast<int>((item >> 40) & 3ull);
-    const int bi = static_cast<int>((item >> 42) & 0x3fffull);
+    const int wv = static_cast<int>((item >> 40) & 7ull);
+    const int bi = static_cast<int>((item >> 43) & 0x1fffull);
     const int cx = static_cast<int>((item >> 56) & 0xffull);
     const int si = series_of_tile(tile_off, n_series, tile);
     const SeriesDev S = series[si];
@@ -774,8 +962,8 @@ __global__ void __launch_bounds__(128) deferred_small_kernel(
   for (uint32_t it = blockIdx.x * 4 + warp; it < n_items; it += gridDim.x * 4) {
     const unsigned long long item = items[it];
     const int64_t tile = static_cast<int64_t>(item & 0xffffffffffull);
-    const int wv = static_cast<int>((item >> 40) & 3ull);
-    const int bi = static_cast<int>((item >> 42) & 0x3fffull);
+    const int wv = static_cast<int>((item >> 40) & 7ull);
+    const int bi = static_cast<int>((item >> 43) & 0x1fffull);
     const int cx = static_cast<int>((item >> 56) & 0xffull);
     const int si = series_of_tile(tile_off, n_series, tile);
     const SeriesDev S = series[si];
@@ -814,29 +1002,35 @@ __global__ void unpack_kernel(unsigned long long *__restrict__ slots, int64_t n,
 
 }  // namespace
 
-int search_tile_bins(int warps) { return 32 * kR * warps; }
+int search_tile_bins(int warps, int groups) { return 32 * kR * warps * groups; }
 
-int search_smem_bytes(int W, int warps, int *buf_len_out) {
+int search_smem_bytes(int W, int warps, int groups, int *buf_len_out) {
   const int nb = (W + kR - 1) / kR;
-  int buf_len = search_tile_bins(warps) + nb * kR + 3 * kR;
+  int buf_len = search_tile_bins(warps, groups) + nb * kR + 3 * kR;
   buf_len = (buf_len + 3) & ~3;
   const int nq33 = buf_len / kR, nq11 = buf_len / kSub;
   if (buf_len_out) *buf_len_out = buf_len;
   return 128 + 4 * (buf_len + nq33 + 1 + nq11 + 1);
 }
 
-SmemLimit g_lim_search, g_lim_dump;
+SmemLimit g_lim_search, g_lim_search2, g_lim_dump;
 
 int prepare_bank(pulscan_plan p) {
-  const int smem = search_smem_bytes(p->z_max, p->search_warps, nullptr);
+  const int smem = search_smem_bytes(p->z_max, p->search_warps, p->search_groups, nullptr);
   if (smem > 220 * 1024) return fail(PULSCAN_ERR_UNSUPPORTED, "z_max too large for the shared-memory tile");
-  int rc = ensure_smem(boxcar_kernel<true>, smem, g_lim_search);
-  if (!rc) rc = ensure_smem(boxcar_kernel<false>, smem, g_lim_dump);
+  int rc = p->search_groups == 2 ? ensure_smem(boxcar_kernel<true, true>, smem, g_lim_search2)
+                                 : ensure_smem(boxcar_kernel<true, false>, smem, g_lim_search);
+  if (!rc) rc = ensure_smem(boxcar_kernel<false, false>, smem, g_lim_dump);
   if (rc) return rc;
   // persistent grid: as many CTAs as fit on the GPU at once
   int b0 = 0, b1 = 0;
-  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, boxcar_kernel<true>, 32 * p->search_warps, smem));
-  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, boxcar_kernel<false>, 32 * p->search_warps, smem));
+  if (p->search_groups == 2)
+    PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, boxcar_kernel<true, true>, 32 * p->search_warps, smem));
+  else
+    PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, boxcar_kernel<true, false>, 32 * p->search_warps,
+                                                          smem));
+  PS_CUDA(
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, boxcar_kernel<false, false>, 32 * p->search_warps, smem));
   p->persist_grid[0] = b0 * p->n_ranges;
   p->persist_grid[1] = b1 * p->n_ranges;
   return PULSCAN_OK;
@@ -844,7 +1038,8 @@ int prepare_bank(pulscan_plan p) {
 
 static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaStream_t s) {
   int buf_len = 0;
-  const int smem = search_smem_bytes(p->z_max, p->search_warps, &buf_len);
+  const int groups = p->search_groups;
+  const int smem = search_smem_bytes(p->z_max, p->search_warps, groups, &buf_len);
   if (p->total_tiles > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many search tiles");
   // persistent for grids of three or more full waves (claim counters zeroed
   // by the caller); a smaller grid keeps one CTA per tile, since each SM
@@ -856,16 +1051,27 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
   uint32_t *ctr = pg > 0 ? p->d_counters + 4 : nullptr;
   const dim3 grid(static_cast<unsigned>(pg > 0 ? std::min<int64_t>(p->total_tiles, pg) : p->total_tiles));
   const dim3 block(32 * p->search_warps);
-  const int tile_bins = search_tile_bins(p->search_warps);
+  const int tile_bins = search_tile_bins(p->search_warps, groups);
   const uint32_t cap = static_cast<uint32_t>(p->item_cap);
-  const int rc = search ? ensure_smem(boxcar_kernel<true>, smem, g_lim_search)
-                        : ensure_smem(boxcar_kernel<false>, smem, g_lim_dump);
+  // a timeout test applies to the next search only
+  const uint32_t wait_test = search ? p->wait_test_us : 0u;
+  if (search) p->wait_test_us = 0u;
+  int rc = PULSCAN_OK;
+  if (!search) rc = ensure_smem(boxcar_kernel<false, false>, smem, g_lim_dump);
+  else if (groups == 2) rc = ensure_smem(boxcar_kernel<true, true>, smem, g_lim_search2);
+  else rc = ensure_smem(boxcar_kernel<true, false>, smem, g_lim_search);
   if (rc) return rc;
   if (search) {
-    boxcar_kernel<true><<<grid, block, smem, s>>>(
-        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
-        p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
-        tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges);
+    if (groups == 2)
+      boxcar_kernel<true, true><<<grid, block, smem, s>>>(
+          d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+          p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
+          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test);
+    else
+      boxcar_kernel<true, false><<<grid, block, smem, s>>>(
+          d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+          p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
+          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test);
     PS_CUDA(cudaGetLastError());
     record(p, 5, s);
     record(p, 6, s);
@@ -880,10 +1086,10 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
     PS_CUDA(cudaGetLastError());
     record(p, 7, s);
   } else {
-    boxcar_kernel<false><<<grid, block, smem, s>>>(
+    boxcar_kernel<false, false><<<grid, block, smem, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
         p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, 0u,
-        tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges);
+        tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, 0u);
   }
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
@@ -892,19 +1098,19 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
 // Dump-mode launch with caller-supplied descriptor and scratch pointers
 // (used by the allocation-free entry point; no plan involved).
 int prepare_bank_raw(int W, int warps) {
-  return ensure_smem(boxcar_kernel<false>, search_smem_bytes(W, warps, nullptr), g_lim_dump);
+  return ensure_smem(boxcar_kernel<false, false>, search_smem_bytes(W, warps, 1, nullptr), g_lim_dump);
 }
 
 int launch_segmax_raw(const float *d_power, const SeriesDev *d_series, const int64_t *d_tile_off, int64_t tiles,
                       int warps, int W, int seg_len, unsigned long long *d_slots, uint32_t *d_counters,
                       int64_t n_slots, float *d_max, uint64_t *d_argmax, cudaStream_t s) {
   int buf_len = 0;
-  const int smem = search_smem_bytes(W, warps, &buf_len);
-  const int rc = ensure_smem(boxcar_kernel<false>, smem, g_lim_dump);
+  const int smem = search_smem_bytes(W, warps, 1, &buf_len);
+  const int rc = ensure_smem(boxcar_kernel<false, false>, smem, g_lim_dump);
   if (rc) return rc;
-  boxcar_kernel<false><<<static_cast<unsigned>(tiles), 32 * warps, smem, s>>>(
+  boxcar_kernel<false, false><<<static_cast<unsigned>(tiles), 32 * warps, smem, s>>>(
       d_power, d_series, d_tile_off, 1, W, seg_len, nullptr, nullptr, d_slots, nullptr, d_counters, nullptr,
-      nullptr, 0u, search_tile_bins(warps), buf_len, nullptr, nullptr, 1);
+      nullptr, 0u, search_tile_bins(warps, 1), buf_len, nullptr, nullptr, 1, 1, 0u);
   PS_CUDA(cudaGetLastError());
   unpack_kernel<<<1024, 256, 0, s>>>(d_slots, n_slots, d_max, d_argmax);
   PS_CUDA(cudaGetLastError());

@@ -124,7 +124,9 @@ struct pulscan_plan_s {
   std::vector<float> h_thresh;      // n_series * z_max, layout order
   int64_t x_floats = 0, spec_bins = 0, p_floats = 0, total_seg = 0, total_tiles = 0;
   int64_t max_cands = 0;
-  int search_warps = 4;            // warps per boxcar CTA (tile = 1056 * warps bins)
+  int search_warps = 4;            // warps per boxcar CTA
+  int search_groups = 1;           // 1056-bin slices per warp: 1 scalar adds, 2 packed (tile = 1056 * warps * groups)
+  uint32_t wait_test_us = 0;       // > 0: the next search tests its timeout path (no copy issued; limit in us)
   // device scratch
   ps::SeriesDev *d_series = nullptr;
   int64_t *d_tile_off = nullptr;   // n_series + 1, for tile -> series search
@@ -185,8 +187,8 @@ double host_log_sf_normal(double s);   // ln Phi_c(s), FP64 on the host
 int launch_segmax(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax,
                   cudaStream_t s);
 void record(pulscan_plan p, int idx, cudaStream_t s);  // timing event helper
-int search_smem_bytes(int W, int warps, int *buf_len_out);
-int search_tile_bins(int warps);
+int search_smem_bytes(int W, int warps, int groups, int *buf_len_out);
+int search_tile_bins(int warps, int groups = 1);
 int prepare_bank(pulscan_plan p);       // one-time kernel attributes (before any capture)
 int prepare_bank_raw(int W, int warps);
 int launch_segmax_raw(const float *d_power, const SeriesDev *d_series, const int64_t *d_tile_off, int64_t tiles,

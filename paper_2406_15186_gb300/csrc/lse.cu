@@ -32,8 +32,13 @@
 //   w terms of size S carries up to ~ w * 2^-24 * S.  Each picked window's S
 //   is recomputed as F[k + w] - F[k] from a per-segment exclusive prefix sum
 //   F held in shared memory as an unevaluated pair of floats (hi + lo, built
-//   with error-free additions, carried between threads in FP64), which is
-//   accurate to about one rounding of S;
+//   with error-free additions, carried between threads in FP64) and kept as
+//   a pair: even one rounding of S (half an ulp, 2.4e-4 at S = 4096) would
+//   move a weight by 2.4e-3 at tau = 0.1.  S - M is taken as (hi - M) + lo,
+//   whose first difference is exact;
+// * Y leaves the forward as a pair too (d_y and its rounding error d_ylo),
+//   and the backward's weights use (hi - Y) + (lo - Ylo): an FP32 Y alone
+//   would scale every weight of a (segment, width) by exp(dY / tau);
 // * normalise_backward_kernel: dL/dP -> dL/d(Re, Im) through Eq. 8, written
 //   as the input of a cuFFT C2R transform with the Hermitian weights (DC 0,
 //   interior halved, Nyquist real), whose output is dL/dx;
@@ -108,11 +113,17 @@ __device__ void build_prefix(const float *__restrict__ buf, int n, float *__rest
   __syncthreads();
 }
 
-// sum buf[a..b) = F[b] - F[a], to about one rounding.
-__device__ __forceinline__ float window_sum(const float *__restrict__ fh, const __half *__restrict__ fl, int a, int b) {
+// sum buf[a..b) = F[b] - F[a] as an unevaluated pair hi + lo: hi = fh[b] -
+// fh[a] rounded, lo = its rounding error plus the difference of the low
+// parts, so hi + lo carries about 2^-12 ulp of F of error (not one rounding
+// of S).  Callers subtract a nearby reference from hi first (exact by
+// Sterbenz's lemma when the two are within a factor of two) and add lo after.
+__device__ __forceinline__ float window_sum2(const float *__restrict__ fh, const __half *__restrict__ fl, int a, int b,
+                                             float &lo) {
   float e;
   const float d = two_sum(fh[b], -fh[a], e);
-  return __fadd_rn(d, __fadd_rn(e, __fsub_rn(__half2float(fl[b]), __half2float(fl[a]))));
+  lo = __fadd_rn(e, __fsub_rn(__half2float(fl[b]), __half2float(fl[a])));
+  return d;
 }
 
 // Ring steps C0..C0+NC-1 with a per-step callback cb(c) after the adds.
@@ -270,7 +281,8 @@ __device__ __forceinline__ float lane_groups(const float (&s)[kR], int lim, floa
 // Works off one width's events of this warp: the 11-bin groups flagged by
 // their lanes (grp: this lane's 3-bit mask, zero if not flagged), their
 // windows packed over the warp's lanes; every window whose exact sum lies
-// above thr calls f(k, S) with k the local start bin.  A window is first
+// above thr calls f(k, hi, lo) with k the local start bin and S = hi + lo
+// (window_sum2).  A window is first
 // screened with the high parts of the prefix alone: each is within half an
 // ulp of F, so fh[b] - fh[a] is within 1.5 ulp of S; the margin is 4 ulp of
 // F[b].  my_lim: the calling lane's valid window count at w; evl: this warp's
@@ -296,8 +308,9 @@ __device__ __forceinline__ void for_event_windows(uint32_t grp, int warp, int la
       const int k = warp * (32 * kR) + (ev & 31) * kR + i;
       const float hb = fh[k + w];
       if (hb - fh[k] > thr - 4.8e-7f * fabsf(hb)) {
-        const float sw = window_sum(fh, fl, k, k + w);
-        if (sw > thr) f(k, sw);
+        float lo;
+        const float hi = window_sum2(fh, fl, k, k + w, lo);
+        if (__fadd_rn(__fsub_rn(hi, thr), lo) > 0.0f) f(k, hi, lo);
       }
     }
   }
@@ -306,8 +319,8 @@ __device__ __forceinline__ void for_event_windows(uint32_t grp, int warp, int la
 
 __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
-    int n_series, int W, int seg_len, float tau, float cut, float *__restrict__ y, uint32_t *__restrict__ counters,
-    int buf_len) {
+    int n_series, int W, int seg_len, float tau, float cut, float *__restrict__ y, float *__restrict__ ylo,
+    uint32_t *__restrict__ counters, int buf_len) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   double *wtot = reinterpret_cast<double *>(smem_raw + 32);
@@ -372,29 +385,40 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
           const int w = bi * kR + c + 1;
           const uint32_t grp = hot ? kgrp[(warp * kR + c) * 32 + lane] : 0u;
           for_event_windows(grp, warp, lane, ll.at(w), w, thr, fh, fl, evl + warp * 96,
-                            [&](int, float sw) { acc += expf((sw - mw) * inv_tau); });
+                            [&](int, float hi, float lo) {
+                              acc += expf(__fadd_rn(__fsub_rn(hi, mw), lo) * inv_tau);
+                            });
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
           if (lane == 0) atomicAdd(&lsb[c], acc);
         }
         __syncthreads();
-        for (int c = threadIdx.x; c < nsteps; c += blockDim.x)
-          y[t.seg_g * static_cast<int64_t>(W) + bi * kR + c] = mblk[c] + tau * logf(lsb[c]);
+        // Y = M + tau log(sum) as a pair: the FP32 value and its exact
+        // rounding error (the backward's weights exp((S - Y) / tau) need Y to
+        // better than FP32 resolution: an error dY moves them all by dY / tau)
+        for (int c = threadIdx.x; c < nsteps; c += blockDim.x) {
+          float e;
+          const float yh = two_sum(mblk[c], tau * logf(lsb[c]), e);
+          const int64_t o = t.seg_g * static_cast<int64_t>(W) + bi * kR + c;
+          y[o] = yh;
+          ylo[o] = e;
+        }
       });
 }
 
 __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
     int n_series, int W, int seg_len, float tau, float cut, const float *__restrict__ y,
-    const float *__restrict__ gy, float *__restrict__ dp, float *__restrict__ tail, uint32_t *__restrict__ counters,
-    int buf_len, int d_len) {
+    const float *__restrict__ ylo, const float *__restrict__ gy, float *__restrict__ dp, float *__restrict__ tail,
+    uint32_t *__restrict__ counters, int buf_len, int d_len) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   double *wtot = reinterpret_cast<double *>(smem_raw + 32);
   uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
   float *yrow = buf + buf_len;
-  float *grow = yrow + W;
+  float *ylrow = yrow + W;                       // Y's low parts
+  float *grow = ylrow + W;
   float *dd = grow + W;                          // d_len difference entries
   float *wsum = dd + d_len;                      // per-warp scan totals
   uint32_t *evm = reinterpret_cast<uint32_t *>(wsum + 32);   // warps x 33 event ballots
@@ -407,6 +431,7 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   build_prefix(buf, buf_len, fh, fl, wtot);
   for (int j = threadIdx.x; j < W; j += blockDim.x) {
     yrow[j] = y[t.seg_g * static_cast<int64_t>(W) + j];
+    ylrow[j] = ylo[t.seg_g * static_cast<int64_t>(W) + j];
     grow[j] = gy[t.seg_g * static_cast<int64_t>(W) + j];
   }
   for (int j = threadIdx.x; j < d_len; j += blockDim.x) dd[j] = 0.0f;
@@ -436,10 +461,12 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
           if (bal == 0u) continue;
           const int w = bi * kR + c + 1;
           const float yw = yrow[w - 1];
+          const float ylw = ylrow[w - 1];
           const float gw = grow[w - 1];
           for_event_windows(kgrp[(warp * kR + c) * 32 + lane], warp, lane, ll.at(w), w, yw - cut, fh, fl,
-                            evl + warp * 96, [&](int k, float sw) {
-            const float g = gw * expf((sw - yw) * inv_tau);
+                            evl + warp * 96, [&](int k, float hi, float lo) {
+            // (S - Y) from the two pairs: hi - yw is exact (Sterbenz)
+            const float g = gw * expf(__fadd_rn(__fsub_rn(hi, yw), __fsub_rn(lo, ylw)) * inv_tau);
             atomicAdd(&dd[k], g);
             atomicAdd(&dd[k + w], -g);
           });
@@ -724,8 +751,8 @@ using namespace ps;
 extern "C" {
 
 int pulscan_lse_forward(pulscan_plan p, const float *d_x, float *d_spec, float *d_power, float *d_stats,
-                        float *d_sel, float *d_y, float tau, pulscan_stream stream) {
-  if (!p || !d_x || !d_spec || !d_power || !d_stats || !d_sel || !d_y)
+                        float *d_sel, float *d_y, float *d_ylo, float tau, pulscan_stream stream) {
+  if (!p || !d_x || !d_spec || !d_power || !d_stats || !d_sel || !d_y || !d_ylo)
     return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   if (!(tau > 0.0f) || !std::isfinite(tau)) return fail(PULSCAN_ERR_INVALID_ARG, "tau must be finite and > 0");
   int rc = lse_prepare(p);
@@ -743,15 +770,15 @@ int pulscan_lse_forward(pulscan_plan p, const float *d_x, float *d_spec, float *
   if (rc) return rc;
   lse_forward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
       d_power, p->d_series, p->d_seg_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len, tau,
-      lse_cut(p, tau), d_y, p->d_counters, buf_len);
+      lse_cut(p, tau), d_y, d_ylo, p->d_counters, buf_len);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }
 
 int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_power, const float *d_stats,
-                         const float *d_sel, const float *d_y, const float *d_gy, float *d_gx, float tau,
-                         pulscan_stream stream) {
-  if (!p || !d_spec || !d_power || !d_stats || !d_sel || !d_y || !d_gy || !d_gx)
+                         const float *d_sel, const float *d_y, const float *d_ylo, const float *d_gy, float *d_gx,
+                         float tau, pulscan_stream stream) {
+  if (!p || !d_spec || !d_power || !d_stats || !d_sel || !d_y || !d_ylo || !d_gy || !d_gx)
     return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   if (!(tau > 0.0f) || !std::isfinite(tau)) return fail(PULSCAN_ERR_INVALID_ARG, "tau must be finite and > 0");
   int rc = lse_prepare(p);
@@ -764,13 +791,13 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   int64_t max_n = 0;
   for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
   const int d_len = static_cast<int>(max_n + p->z_max + 1);
-  const int smem = 128 + 4 * (buf_len + 2 * p->z_max + d_len + 32 + kLseMaxWarps * (kR + 96) +
+  const int smem = 128 + 4 * (buf_len + 3 * p->z_max + d_len + 32 + kLseMaxWarps * (kR + 96) +
                               kLseMaxWarps * kR * 8 + (buf_len + 1)) + 2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
   if (rc) return rc;
   lse_backward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
       d_power, p->d_series, p->d_seg_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len, tau,
-      lse_cut(p, tau), d_y, d_gy, p->d_dp, p->d_tail, p->d_counters, buf_len, d_len);
+      lse_cut(p, tau), d_y, d_ylo, d_gy, p->d_dp, p->d_tail, p->d_counters, buf_len, d_len);
   PS_CUDA(cudaGetLastError());
   normalise_backward_kernel<<<static_cast<unsigned>(p->total_seg), 256, 0, s>>>(
       reinterpret_cast<const float2 *>(d_spec), p->d_dp, p->d_tail, reinterpret_cast<const float4 *>(d_stats),

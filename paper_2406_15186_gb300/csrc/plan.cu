@@ -179,10 +179,12 @@ static int upload_layout(pulscan_plan p) {
   return PULSCAN_OK;
 }
 
-// Re-tile the bank with `warps` warps per CTA (tile = 1056 x warps bins).
-static int relayout_tiles(pulscan_plan p, int warps) {
+// Re-tile the bank with `warps` warps per CTA and `groups` 1056-bin slices
+// per warp (tile = 1056 x warps x groups bins; groups = 2: packed adds).
+static int relayout_tiles(pulscan_plan p, int warps, int groups) {
   p->search_warps = warps;
-  const int64_t tb = search_tile_bins(warps);
+  p->search_groups = groups;
+  const int64_t tb = search_tile_bins(warps, groups);
   int64_t tl = 0;
   for (auto &se : p->series) {
     se.tile_off = tl;
@@ -190,7 +192,7 @@ static int relayout_tiles(pulscan_plan p, int warps) {
   }
   p->total_tiles = tl;
   const int64_t nb = (p->z_max + kR - 1) / kR;
-  p->item_cap = std::min<int64_t>(std::min<int64_t>(tl * warps * nb, 65536), p->alloc_item_cap);
+  p->item_cap = std::min<int64_t>(std::min<int64_t>(tl * warps * groups * nb, 65536), p->alloc_item_cap);
   int rc = upload_layout(p);
   if (!rc) rc = prepare_bank(p);
   if (p->graph.exec) {
@@ -301,7 +303,7 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
   // items (277 MB of snapshots); an overflowing block is run exactly by its
   // own warp, which is far slower when whole regions are hot (the harmonic
   // stages of strong tones flag tens of thousands of blocks)
-  const int64_t total_warps = tl * p->search_warps;
+  const int64_t total_warps = tl * p->search_warps * p->search_groups;
   const int64_t nb = (z_max + kR - 1) / kR;
   p->item_cap = std::min<int64_t>(total_warps * nb, 65536);
   p->alloc_item_cap = p->item_cap;
@@ -503,10 +505,11 @@ int pulscan_plan_autotune(pulscan_plan p, const float *d_power, pulscan_stream s
   PS_CUDA(cudaEventCreate(&e0));
   PS_CUDA(cudaEventCreate(&e1));
   float best = INFINITY;
-  int best_w = p->search_warps, best_m = p->persist_mode;
+  int best_w = p->search_warps, best_m = p->persist_mode, best_g = p->search_groups;
   int rc = PULSCAN_OK;
-  for (int w : {1, 2, 3, 4}) {
-    rc = relayout_tiles(p, w);
+  for (int wg = 0; wg < 8 && !rc; ++wg) {
+    const int w = 1 + (wg & 3), g = 1 + (wg >> 2);
+    rc = relayout_tiles(p, w, g);
     for (int mode : {0, 1}) {
       if (rc) break;
       p->persist_mode = mode;
@@ -525,34 +528,43 @@ int pulscan_plan_autotune(pulscan_plan p, const float *d_power, pulscan_stream s
       if (!rc && tot < best) {
         best = tot;
         best_w = w;
+        best_g = g;
         best_m = mode;
       }
     }
-    if (rc) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   p->persist_mode = best_m;
-  const int rc2 = relayout_tiles(p, best_w);
+  const int rc2 = relayout_tiles(p, best_w, best_g);
   PS_CUDA(cudaMemsetAsync(p->d_counters, 0, (4 + static_cast<size_t>(p->n_ranges)) * sizeof(uint32_t), s));
   PS_CUDA(cudaStreamSynchronize(s));
   p->timing = timing;
   return rc ? rc : rc2;
 }
 
-int pulscan_plan_set_tiling(pulscan_plan p, int32_t warps, int32_t persistent) {
+int pulscan_plan_set_tiling(pulscan_plan p, int32_t warps, int32_t persistent, int32_t packed) {
   if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
   if (warps < 1 || warps > 4) return fail(PULSCAN_ERR_INVALID_ARG, "warps must be 1, 2, 3 or 4");
   if (persistent < -1 || persistent > 1) return fail(PULSCAN_ERR_INVALID_ARG, "persistent must be -1, 0 or 1");
+  if (packed < 0 || packed > 1) return fail(PULSCAN_ERR_INVALID_ARG, "packed must be 0 or 1");
   PS_CUDA(cudaDeviceSynchronize());
   p->persist_mode = persistent;
-  return relayout_tiles(p, warps);
+  return relayout_tiles(p, warps, packed ? 2 : 1);
 }
 
-int pulscan_plan_tiling(pulscan_plan p, int32_t *warps, int32_t *persistent) {
+int pulscan_plan_tiling(pulscan_plan p, int32_t *warps, int32_t *persistent, int32_t *packed) {
   if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
   if (warps) *warps = p->search_warps;
   if (persistent) *persistent = p->persist_mode;
+  if (packed) *packed = p->search_groups == 2 ? 1 : 0;
+  return PULSCAN_OK;
+}
+
+int pulscan_plan_test_wait_timeout(pulscan_plan p, int32_t limit_us) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  if (limit_us < 1 || limit_us > 1000) return fail(PULSCAN_ERR_INVALID_ARG, "limit_us must be 1..1000");
+  p->wait_test_us = static_cast<uint32_t>(limit_us);
   return PULSCAN_OK;
 }
 
@@ -711,7 +723,9 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
                    pulscan_stream stream) {
   if (!p || !d_x || !d_spec || !d_power) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (!use_graph) {
+  // an armed timeout test runs outside the graph (a captured graph would
+  // keep the test in every replay)
+  if (!use_graph || p->wait_test_us != 0u) {
     int rc = pulscan_rfft(p, d_x, d_spec, stream);
     if (!rc) rc = pulscan_power_normalise(p, d_spec, d_power, nullptr, stream);
     if (!rc) rc = pulscan_boxcar_search(p, d_power, stream);

@@ -24,9 +24,10 @@ class _LogSumExp(torch.autograd.Function):
         stats = torch.empty(4 * plan.total_segments, dtype=torch.float32, device=dev)
         sel = torch.empty(8 * plan.total_segments, dtype=torch.float32, device=dev)
         y = torch.empty(plan.total_segments * plan.z_max, dtype=torch.float32, device=dev)
+        ylo = torch.empty_like(y)
         _check(lib.pulscan_lse_forward(plan._h, x.data_ptr(), spec.data_ptr(), power.data_ptr(), stats.data_ptr(),
-                                       sel.data_ptr(), y.data_ptr(), float(tau), _stream(None)))
-        ctx.save_for_backward(spec, power, stats, sel, y)
+                                       sel.data_ptr(), y.data_ptr(), ylo.data_ptr(), float(tau), _stream(None)))
+        ctx.save_for_backward(spec, power, stats, sel, y, ylo)
         ctx.plan = plan
         ctx.tau = float(tau)
         return y.view(plan.total_segments, plan.z_max)
@@ -34,13 +35,13 @@ class _LogSumExp(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gy):
         lib = load()
-        spec, power, stats, sel, y = ctx.saved_tensors
+        spec, power, stats, sel, y, ylo = ctx.saved_tensors
         plan = ctx.plan
         gy = gy.contiguous().view(-1)
         gx = torch.empty(plan.x_floats, dtype=torch.float32, device=gy.device)
         _check(lib.pulscan_lse_backward(plan._h, spec.data_ptr(), power.data_ptr(), stats.data_ptr(),
-                                        sel.data_ptr(), y.data_ptr(), gy.data_ptr(), gx.data_ptr(), ctx.tau,
-                                        _stream(None)))
+                                        sel.data_ptr(), y.data_ptr(), ylo.data_ptr(), gy.data_ptr(), gx.data_ptr(),
+                                        ctx.tau, _stream(None)))
         return gx, None, None
 
 

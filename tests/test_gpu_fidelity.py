@@ -104,7 +104,7 @@ def test_fidelity_mode_validation(pkg):
     lib = pkg.load()
     z = [torch.zeros(k, device="cuda") for k in (plan.x_floats, plan.spec_floats, plan.power_floats,
                                                   4 * plan.total_segments, 8 * plan.total_segments,
-                                                  plan.total_segments * plan.z_max)]
+                                                  plan.total_segments * plan.z_max, plan.total_segments * plan.z_max)]
     rc = lib.pulscan_lse_forward(plan._h, *[t.data_ptr() for t in z], ctypes.c_float(0.1), None)
     assert rc == -6
     plan.set_fidelity(pkg.FIDELITY_EXACT)

@@ -53,10 +53,16 @@ def _series(n, seed=11):
     return synth.inject(x, tones)
 
 
+@pytest.mark.parametrize("packed", [0, 1])
 @pytest.mark.parametrize("n,w_max,seg_len,sigma", SHAPES)
-def test_stage_a_b_and_candidates(pkg, n, w_max, seg_len, sigma):
+def test_stage_a_b_and_candidates(pkg, n, w_max, seg_len, sigma, packed):
+    """Every shape with the scalar bank and with the packed one (two 1056-bin
+    slices per warp, add.f32x2), whose dump mode then runs the slices of a
+    packed tile one after the other."""
     x = _series(n)
     plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    if packed:
+        plan.set_tiling(2, -1, 1)
     out = parity.run_gpu(plan, x, stats=True)
     m = n // 2 + 1
     spec = parity.spectrum_complex(out["spec"], 0, m)
@@ -223,15 +229,17 @@ def test_rblock_reports_block_index(pkg):
         assert np.array_equal(approx[f], exact[f])
 
 
-@pytest.mark.parametrize("warps,persistent", [(1, 1), (2, 1), (3, 1), (4, 1), (1, 0), (3, 0), (4, 0)])
-def test_launch_shapes_give_the_same_search(pkg, warps, persistent):
-    """Every tile width and both launch forms (one CTA per tile; persistent
-    per-SM tile ranges with stealing) against the oracle on one input."""
+@pytest.mark.parametrize("warps,persistent,packed", [(1, 1, 0), (2, 1, 0), (3, 1, 0), (4, 1, 0), (1, 0, 0), (3, 0, 0),
+                                                     (4, 0, 0), (1, 1, 1), (2, 0, 1), (3, 1, 1), (4, 0, 1)])
+def test_launch_shapes_give_the_same_search(pkg, warps, persistent, packed):
+    """Every tile width, both launch forms (one CTA per tile; persistent
+    per-SM tile ranges with stealing) and both add forms (scalar; packed
+    pairs over two slices per warp) against the oracle on one input."""
     n, w_max, seg_len, sigma = 1 << 18, 48, 1024, 2.5
     x = _series(n, seed=12)
     plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
-    plan.set_tiling(warps, persistent)
-    assert plan.tiling() == (warps, persistent)
+    plan.set_tiling(warps, persistent, packed)
+    assert plan.tiling() == (warps, persistent, packed)
     out = parity.run_gpu(plan, x)
     m = n // 2 + 1
     p64 = out["power"][:m].astype(np.float64)
@@ -246,8 +254,8 @@ def test_autotune_keeps_the_candidates(pkg):
     plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
     before = parity.run_gpu(plan, x, maxima=False)
     d_power = torch.from_numpy(before["power"]).cuda()
-    warps, persistent = plan.autotune(d_power)
-    assert warps in (1, 2, 3, 4) and persistent in (0, 1)
+    warps, persistent, packed = plan.autotune(d_power)
+    assert warps in (1, 2, 3, 4) and persistent in (0, 1) and packed in (0, 1)
     after = parity.run_gpu(plan, x, maxima=False)
     assert len(after["cands"]) == len(before["cands"]) > 0
     for f in ("series", "width", "bin", "power", "sigma"):
@@ -281,3 +289,47 @@ def test_host_entry_points_match_the_device_path(pkg):
             plans[(i + 1) % 2].search_host_async(pins[i + 1], stream=streams[(i + 1) % 2])
         got = plans[i % 2].candidates(stream=streams[i % 2])
         assert np.array_equal(got, ref[i]), i
+
+
+def test_packed_and_scalar_banks_give_identical_records(pkg):
+    """The packed bank performs the scalar bank's FP32 adds in the same order
+    (each half of add.rn.f32x2 rounds as add.rn.f32), so the records agree
+    bit for bit, on a series hot enough to defer many blocks."""
+    n, w_max, seg_len, sigma = 1 << 18, 200, 2048, 2.0
+    x = _series(n, seed=15)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    plan.set_trials(1.0)
+    outs = []
+    for packed in (0, 1):
+        plan.set_tiling(4, 0, packed)
+        outs.append(parity.run_gpu(plan, x, maxima=True))
+        assert plan.counters()[0] > 0
+    assert len(outs[0]["cands"]) > 100
+    assert np.array_equal(outs[0]["cands"], outs[1]["cands"])
+    assert np.array_equal(outs[0]["mx"], outs[1]["mx"]) and np.array_equal(outs[0]["am"], outs[1]["am"])
+
+
+@pytest.mark.parametrize("packed", [0, 1])
+def test_timeout_path_reports_and_recovers(pkg, packed):
+    """The bounded-wait path without a fault: an armed search issues no copy
+    and waits 20 us on the copy's barrier, so every tile gives up with
+    nothing in flight; pulscan_candidates reports PULSCAN_ERR_TIMEOUT, and the
+    next search (graph replay) gives the normal records."""
+    n, w_max, seg_len, sigma = 1 << 16, 64, 1024, 4.0
+    x = _series(n, seed=14)
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    plan.set_tiling(2, -1, packed)
+    d_x, d_spec, d_power = plan.buffers("cuda")
+    d_x.copy_(torch.from_numpy(x))
+    plan.search(d_x, d_spec, d_power, use_graph=True)
+    ref = plan.candidates()
+    assert len(ref) > 0
+    plan.test_wait_timeout(20)
+    plan.search(d_x, d_spec, d_power, use_graph=True)
+    with pytest.raises(pkg.PulscanError) as err:
+        plan.candidates()
+    assert err.value.code == -5
+    plan.search(d_x, d_spec, d_power, use_graph=True)
+    assert np.array_equal(plan.candidates(), ref)
+    with pytest.raises(pkg.PulscanError):
+        plan.test_wait_timeout(0)

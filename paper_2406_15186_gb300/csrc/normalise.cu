@@ -45,10 +45,11 @@ constexpr int kCap = 256;                      // values ranked directly
 constexpr int kMaxLevels = 8;
 constexpr int kWarpsN = kNormThreads / 32;
 
-struct SelShared {
+template <int NT>
+struct SelSharedT {
   uint32_t hist[2][kBuckets];
-  uint32_t wsum[2][kWarpsN / 2];
-  float red[kWarpsN][4];
+  uint32_t wsum[2][NT / 64];
+  float red[NT / 32][4];
   float lo[kMaxLevels][2], scale[kMaxLevels][2];
   uint32_t b1[kMaxLevels][2], b2[kMaxLevels][2];
   uint32_t rank[2], below[2], cnt[2], list_n[2];
@@ -58,6 +59,7 @@ struct SelShared {
   int done[2];
   uint32_t flag;
 };
+using SelShared = SelSharedT<kNormThreads>;
 
 __device__ __forceinline__ uint32_t bucket_of(float x, float lo, float scale) {
   const float t = (x - lo) * scale;
@@ -71,10 +73,10 @@ __device__ __forceinline__ float bucket_scale(float lo, float hi) {
 
 // Block min/max of both components over the values cand(e, v0, c0, v1, c1)
 // flags as candidates; result in sh.mm.
-template <class Cand>
-__device__ __forceinline__ void block_minmax(SelShared &sh, Cand cand, int n) {
+template <int NT, class Cand>
+__device__ __forceinline__ void block_minmax(SelSharedT<NT> &sh, Cand cand, int n) {
   float a0 = INFINITY, a1 = INFINITY, z0 = -INFINITY, z1 = -INFINITY;
-  for (int e = threadIdx.x; e < n; e += kNormThreads) {
+  for (int e = threadIdx.x; e < n; e += NT) {
     float v0, v1;
     bool c0, c1;
     cand(e, v0, c0, v1, c1);
@@ -99,7 +101,7 @@ __device__ __forceinline__ void block_minmax(SelShared &sh, Cand cand, int n) {
   if (wid == 0 && lane < 4) {
     // lane k reduces column k over the warps
     float r = (lane < 2) ? INFINITY : -INFINITY;
-    for (int w = 0; w < kWarpsN; ++w) r = (lane < 2) ? fminf(r, sh.red[w][lane]) : fmaxf(r, sh.red[w][lane]);
+    for (int w = 0; w < NT / 32; ++w) r = (lane < 2) ? fminf(r, sh.red[w][lane]) : fmaxf(r, sh.red[w][lane]);
     sh.mm[lane] = r;
   }
   __syncthreads();
@@ -110,13 +112,15 @@ __device__ __forceinline__ void block_minmax(SelShared &sh, Cand cand, int n) {
 // skewed order to spread banks).  Writes the buckets holding ranks r and
 // r + pair, the count below the first and the cumulative count through the
 // second.
-__device__ __forceinline__ void scan_find(SelShared &sh, int level, bool pair) {
-  const int c = threadIdx.x / (kNormThreads / 2);
-  const int t = threadIdx.x % (kNormThreads / 2);
-  const uint32_t *h = sh.hist[c] + kPerThread * t;
+template <int NT>
+__device__ __forceinline__ void scan_find(SelSharedT<NT> &sh, int level, bool pair) {
+  constexpr int kPer = kBuckets / (NT / 2);   // buckets per scanning thread
+  const int c = threadIdx.x / (NT / 2);
+  const int t = threadIdx.x % (NT / 2);
+  const uint32_t *h = sh.hist[c] + kPer * t;
   uint32_t local = 0;
 #pragma unroll
-  for (int j = 0; j < kPerThread; ++j) local += h[(j + t) & (kPerThread - 1)];
+  for (int j = 0; j < kPer; ++j) local += h[(j + t) & (kPer - 1)];
   const int lane = t & 31, wid = t >> 5;
   uint32_t incl = local;
 #pragma unroll
@@ -133,14 +137,14 @@ __device__ __forceinline__ void scan_find(SelShared &sh, int level, bool pair) {
   const uint32_t r2 = r1 + (pair ? 1u : 0u);
   if (!sh.done[c] && ((r1 >= excl && r1 < excl + local) || (r2 >= excl && r2 < excl + local))) {
     uint32_t acc = excl;
-    for (int j = 0; j < kPerThread; ++j) {
+    for (int j = 0; j < kPer; ++j) {
       const uint32_t nxt = acc + h[j];
       if (r1 >= acc && r1 < nxt) {
-        sh.b1[level][c] = kPerThread * t + j;
+        sh.b1[level][c] = kPer * t + j;
         sh.below[c] = acc;
       }
       if (r2 >= acc && r2 < nxt) {
-        sh.b2[level][c] = kPerThread * t + j;
+        sh.b2[level][c] = kPer * t + j;
         sh.cnt[c] = nxt;
       }
       acc = nxt;
@@ -176,7 +180,7 @@ __device__ __forceinline__ void rank_lists(Sh &sh, const bool (&active)[2], bool
 // empty): rank r is the largest value of bucket b1 and rank r + 1 the
 // smallest of bucket b2.  Block reduction of those two per component from
 // each thread's contributions; results to res[c][0..1] where split[c].
-template <class Sh>
+template <int NW, class Sh>
 __device__ __forceinline__ void split_pair(Sh &sh, const bool (&split)[2], float x0, float x1, float n0, float n1) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -196,7 +200,7 @@ __device__ __forceinline__ void split_pair(Sh &sh, const bool (&split)[2], float
   if (threadIdx.x < 2 && split[threadIdx.x]) {
     const int c = threadIdx.x;
     float hi = -INFINITY, lo = INFINITY;
-    for (int w = 0; w < kWarpsN; ++w) {
+    for (int w = 0; w < NW; ++w) {
       hi = fmaxf(hi, sh.red[w][c]);
       lo = fminf(lo, sh.red[w][2 + c]);
     }
@@ -208,8 +212,8 @@ __device__ __forceinline__ void split_pair(Sh &sh, const bool (&split)[2], float
 
 // Multi-level select (the general path): get(e, v0, v1) gives element e's
 // two component values; level 0 starts from the whole block.
-template <class Get>
-__device__ void select_levels(SelShared &sh, Get get, int n, uint32_t rank, bool pair,
+template <int NT, class Get>
+__device__ void select_levels(SelSharedT<NT> &sh, Get get, int n, uint32_t rank, bool pair,
                                            float (&out_lo)[2], float (&out_hi)[2]) {
   if (threadIdx.x < 2) {
     sh.rank[threadIdx.x] = rank;
@@ -248,10 +252,10 @@ __device__ void select_levels(SelShared &sh, Get get, int n, uint32_t rank, bool
         }
       }
     }
-    for (int j = threadIdx.x; j < 2 * kBuckets; j += kNormThreads) (&sh.hist[0][0])[j] = 0u;
+    for (int j = threadIdx.x; j < 2 * kBuckets; j += NT) (&sh.hist[0][0])[j] = 0u;
     __syncthreads();
     if (sh.done[0] && sh.done[1]) break;
-    for (int e = threadIdx.x; e < n; e += kNormThreads) {
+    for (int e = threadIdx.x; e < n; e += NT) {
       float v0, v1;
       bool c0, c1;
       cand(e, v0, c0, v1, c1, level);
@@ -259,13 +263,13 @@ __device__ void select_levels(SelShared &sh, Get get, int n, uint32_t rank, bool
       if (c1) atomicAdd(&sh.hist[1][bucket_of(v1, sh.lo[level][1], sh.scale[level][1])], 1u);
     }
     __syncthreads();
-    scan_find(sh, level, pair);
+    scan_find<NT>(sh, level, pair);
     bool split[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) split[c] = !sh.done[c] && pair && sh.b1[level][c] != sh.b2[level][c];
     if (split[0] || split[1]) {
       float x0 = -INFINITY, x1 = -INFINITY, n0 = INFINITY, n1 = INFINITY;
-      for (int e = threadIdx.x; e < n; e += kNormThreads) {
+      for (int e = threadIdx.x; e < n; e += NT) {
         float v0, v1;
         bool c0, c1;
         cand(e, v0, c0, v1, c1, level);
@@ -280,7 +284,7 @@ __device__ void select_levels(SelShared &sh, Get get, int n, uint32_t rank, bool
           if (b == sh.b2[level][1]) n1 = fminf(n1, v1);
         }
       }
-      split_pair(sh, split, x0, x1, n0, n1);
+      split_pair<NT / 32>(sh, split, x0, x1, n0, n1);
       if (threadIdx.x < 2 && split[threadIdx.x]) sh.done[threadIdx.x] = 1;
       __syncthreads();
       if (sh.done[0] && sh.done[1]) break;
@@ -289,7 +293,7 @@ __device__ void select_levels(SelShared &sh, Get get, int n, uint32_t rank, bool
 #pragma unroll
     for (int c = 0; c < 2; ++c) gather[c] = !sh.done[c] && (sh.cnt[c] - sh.below[c] <= static_cast<uint32_t>(kCap));
     if (gather[0] || gather[1]) {
-      for (int e = threadIdx.x; e < n; e += kNormThreads) {
+      for (int e = threadIdx.x; e < n; e += NT) {
         float v0, v1;
         bool c0, c1;
         cand(e, v0, c0, v1, c1, level + 1);   // includes this level's [b1, b2]
@@ -341,7 +345,7 @@ __device__ __forceinline__ bool select_fast(SelShared &sh, Get get, uint32_t *bk
     if (bkt) bkt[e] = q0 | (q1 << 16);
   }
   __syncthreads();
-  scan_find(sh, 0, pair);
+  scan_find<kNormThreads>(sh, 0, pair);
   if ((!flat0 && sh.cnt[0] - sh.below[0] > static_cast<uint32_t>(kCap)) ||
       (!flat1 && sh.cnt[1] - sh.below[1] > static_cast<uint32_t>(kCap))) {
     __syncthreads();
@@ -380,25 +384,8 @@ __device__ __forceinline__ bool select_fast(SelShared &sh, Get get, uint32_t *bk
   return true;
 }
 
-// ---------------------------------------------------------------------------
-// Register-resident variant (the common case: blocks of at most 256 * 32
-// bins).  Thread t holds bins t, t + 256, t + 512, ... in registers, loaded
-// with coalesced 8-byte reads straight from global memory, and every pass
-// (range, two selects, power) works on those registers: no staging copy,
-// fewer instructions per bin, and small shared memory (histograms of 1024
-// buckets).  A crowded target bucket falls back to the multi-level select
-// above, reading the block from global memory.
+// Value buckets of the lean kernel's selects (1024 per component).
 constexpr int kFastBuckets = 1024;
-
-struct RegShared {
-  uint32_t hist[2][kFastBuckets];
-  uint32_t wsum[2][kWarpsN / 2];
-  float red[kWarpsN][4];
-  uint32_t rank[2], below[2], cnt[2], list_n[2], b1[2], b2[2];
-  float list[2][kCap];
-  float res[2][2];
-  float mm[4];
-};
 
 __device__ __forceinline__ uint32_t fast_bucket(float x, float lo, float scale) {
   const float t = (x - lo) * scale;
@@ -407,155 +394,6 @@ __device__ __forceinline__ uint32_t fast_bucket(float x, float lo, float scale) 
 
 __device__ __forceinline__ float fast_scale(float lo, float hi) {
   return (hi > lo) ? static_cast<float>(kFastBuckets) / (hi - lo) * (1.0f - 1.0f / 4096.0f) : 0.0f;
-}
-
-// Block min (mm[0..1]) and max (mm[2..3]) of the two components.
-__device__ __forceinline__ void reg_minmax(RegShared &rs, float a0, float a1, float z0, float z1) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 = fminf(a0, __shfl_xor_sync(0xffffffffu, a0, o));
-    a1 = fminf(a1, __shfl_xor_sync(0xffffffffu, a1, o));
-    z0 = fmaxf(z0, __shfl_xor_sync(0xffffffffu, z0, o));
-    z1 = fmaxf(z1, __shfl_xor_sync(0xffffffffu, z1, o));
-  }
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    rs.red[wid][0] = a0;
-    rs.red[wid][1] = a1;
-    rs.red[wid][2] = z0;
-    rs.red[wid][3] = z1;
-  }
-  __syncthreads();
-  if (wid == 0 && lane < 4) {
-    float r = (lane < 2) ? INFINITY : -INFINITY;
-    for (int w = 0; w < kWarpsN; ++w) r = (lane < 2) ? fminf(r, rs.red[w][lane]) : fmaxf(r, rs.red[w][lane]);
-    rs.mm[lane] = r;
-  }
-  __syncthreads();
-}
-
-// Scan of both 1024-bucket histograms (threads [0,128): component 0,
-// [128,256): component 1, 8 buckets each): the buckets of ranks r and
-// r + pair, the count below the first and the cumulative count through the
-// second.
-__device__ __forceinline__ void reg_scan(RegShared &rs, bool pair) {
-  constexpr int kPer = kFastBuckets / (kNormThreads / 2);
-  const int c = threadIdx.x / (kNormThreads / 2);
-  const int t = threadIdx.x % (kNormThreads / 2);
-  const uint32_t *h = rs.hist[c] + kPer * t;
-  uint32_t local = 0;
-#pragma unroll
-  for (int j = 0; j < kPer; ++j) local += h[(j + t) & (kPer - 1)];
-  const int lane = t & 31, wid = t >> 5;
-  uint32_t incl = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += u;
-  }
-  if (lane == 31) rs.wsum[c][wid] = incl;
-  __syncthreads();
-  uint32_t base = 0;
-  for (int j = 0; j < wid; ++j) base += rs.wsum[c][j];
-  const uint32_t excl = base + incl - local;
-  const uint32_t r1 = rs.rank[c];
-  const uint32_t r2 = r1 + (pair ? 1u : 0u);
-  if ((r1 >= excl && r1 < excl + local) || (r2 >= excl && r2 < excl + local)) {
-    uint32_t acc = excl;
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const uint32_t nxt = acc + h[j];
-      if (r1 >= acc && r1 < nxt) {
-        rs.b1[c] = kPer * t + j;
-        rs.below[c] = acc;
-      }
-      if (r2 >= acc && r2 < nxt) {
-        rs.b2[c] = kPer * t + j;
-        rs.cnt[c] = nxt;
-      }
-      acc = nxt;
-    }
-  }
-  __syncthreads();
-}
-
-// Level-0 select of ranks `rank` (and rank + 1 when `pair`) of both
-// components over [lo, hi] from this thread's nv register values val(j).
-// Returns false, having decided nothing, when a target bucket is crowded.
-template <int K, class Val>
-__device__ __forceinline__ bool reg_select(RegShared &rs, Val val, int nv, uint32_t rank, bool pair, float lo0,
-                                           float lo1, float hi0, float hi1, float (&out_lo)[2],
-                                           float (&out_hi)[2]) {
-  const float s0 = fast_scale(lo0, hi0), s1 = fast_scale(lo1, hi1);
-  const bool flat0 = !(hi0 > lo0), flat1 = !(hi1 > lo1);
-  for (int j = threadIdx.x; j < 2 * kFastBuckets; j += kNormThreads) (&rs.hist[0][0])[j] = 0u;
-  if (threadIdx.x < 2) {
-    rs.rank[threadIdx.x] = rank;
-    rs.list_n[threadIdx.x] = 0u;
-  }
-  __syncthreads();
-  uint32_t qq[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if (j < nv) {
-      const float2 f = val(j);
-      const uint32_t q0 = fast_bucket(f.x, lo0, s0), q1 = fast_bucket(f.y, lo1, s1);
-      atomicAdd(&rs.hist[0][q0], 1u);
-      atomicAdd(&rs.hist[1][q1], 1u);
-      qq[j] = q0 | (q1 << 16);
-    }
-  }
-  __syncthreads();
-  reg_scan(rs, pair);
-  // a pair split over two buckets is decided by one max and one min
-  const bool split[2] = {!flat0 && pair && rs.b1[0] != rs.b2[0], !flat1 && pair && rs.b1[1] != rs.b2[1]};
-  if (split[0] || split[1]) {
-    float x0 = -INFINITY, x1 = -INFINITY, n0 = INFINITY, n1 = INFINITY;
-    const uint32_t sb10 = rs.b1[0], sb20 = rs.b2[0], sb11 = rs.b1[1], sb21 = rs.b2[1];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      if (j < nv) {
-        const uint32_t q0 = qq[j] & 0xffffu, q1 = qq[j] >> 16;
-        if ((split[0] && (q0 == sb10 || q0 == sb20)) || (split[1] && (q1 == sb11 || q1 == sb21))) {
-          const float2 f = val(j);
-          if (split[0] && q0 == sb10) x0 = fmaxf(x0, f.x);
-          if (split[0] && q0 == sb20) n0 = fminf(n0, f.x);
-          if (split[1] && q1 == sb11) x1 = fmaxf(x1, f.y);
-          if (split[1] && q1 == sb21) n1 = fminf(n1, f.y);
-        }
-      }
-    }
-    split_pair(rs, split, x0, x1, n0, n1);
-  }
-  const bool need0 = !flat0 && !split[0], need1 = !flat1 && !split[1];
-  if ((need0 && rs.cnt[0] - rs.below[0] > static_cast<uint32_t>(kCap)) ||
-      (need1 && rs.cnt[1] - rs.below[1] > static_cast<uint32_t>(kCap))) {
-    __syncthreads();
-    return false;
-  }
-  const uint32_t l0 = need0 ? rs.b1[0] : 1u, h0 = need0 ? rs.b2[0] : 0u;
-  const uint32_t l1 = need1 ? rs.b1[1] : 1u, h1 = need1 ? rs.b2[1] : 0u;
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if (j < nv) {
-      const uint32_t q0 = qq[j] & 0xffffu, q1 = qq[j] >> 16;
-      const bool g0 = q0 >= l0 && q0 <= h0, g1 = q1 >= l1 && q1 <= h1;
-      if (g0 || g1) {
-        const float2 f = val(j);
-        if (g0) rs.list[0][atomicAdd(&rs.list_n[0], 1u)] = f.x;
-        if (g1) rs.list[1][atomicAdd(&rs.list_n[1], 1u)] = f.y;
-      }
-    }
-  }
-  __syncthreads();
-  const bool active[2] = {need0, need1};
-  rank_lists(rs, active, pair);
-  out_lo[0] = flat0 ? lo0 : rs.res[0][0];
-  out_lo[1] = flat1 ? lo1 : rs.res[1][0];
-  out_hi[0] = flat0 ? lo0 : (pair ? rs.res[0][1] : rs.res[0][0]);
-  out_hi[1] = flat1 ? lo1 : (pair ? rs.res[1][1] : rs.res[1][0]);
-  __syncthreads();
-  return true;
 }
 
 __device__ __forceinline__ float mean_of(float a, float b) {
@@ -710,40 +548,227 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
   if (threadIdx.x == 0 && stats != nullptr) stats[g] = make_float4(med_re, mad_re, med_im, mad_im);
 }
 
-// Blocks per SM the register budget must allow: all values of a thread plus
-// one bucket word per value stay in registers.  Up to K = 17 four blocks per
-// SM (64 registers; K = 17 spills ~90 bytes to L1, which costs less than a
-// third round of CTAs on 1024-block grids).
-constexpr int reg_min_blocks(int k) { return k <= 17 ? 4 : 1; }
+// ---------------------------------------------------------------------------
+// Lean register kernel: the same exact selection with fewer block-wide
+// barriers (9 per block: one after the range pass, four per select), for
+// blocks of up to NT * K bins (NT = 256 or 1024 threads).  Thread t holds
+// bins t, t + NT, ... in registers.
+//   * the range pass also zeroes both selects' histograms, and every thread
+//     reduces the per-warp range partials itself (no second barrier);
+//   * per select: (1) histogram of both components into 1024 value buckets;
+//     (2) one warp per component scans its histogram and classifies the
+//     target bucket(s) of ranks r and r + 1: few enough values to gather,
+//     a pair split over two buckets (rank r is then the largest value of the
+//     first, rank r + 1 the smallest of the second: every bucket between is
+//     empty), a flat range (all values equal), or crowded; (3) all threads
+//     gather the target values, or fold the split pair's two extremes with
+//     atomic max / min on order-preserving integer keys; (4) the component's
+//     warp ranks its list and forms the statistic (FP64 mean of the two middle
+//     values, and for the MAD also 1 / (kappa MAD)).  A crowded bucket (a block
+//     dominated by a strong tone) falls back to the multi-level select, which
+//     re-reads the block from global memory.
+constexpr int kLeanBuckets = kFastBuckets;
 
-template <int K>
-__global__ void __launch_bounds__(kNormThreads, reg_min_blocks(K)) normalise_reg_kernel(
+template <int NT>
+struct LeanShared {
+  uint32_t hist[2][2][kLeanBuckets];   // [median, MAD][component]
+  float red[NT / 32][4];               // per-warp min0, min1, max0, max1
+  float list[2][kCap];
+  uint32_t list_n[2];
+  uint32_t b1[2], b2[2], below[2];
+  uint32_t kmax[2], kmin[2];           // split pairs: order-preserving keys
+  int mode[2];                         // per component: kGather, kSplit, kFlat, kCrowded
+  float res[2][2];                     // selected order statistics (rank r, rank r + 1)
+  float stat[2];                       // median or MAD per component
+  float inv[2];                        // 1 / (kappa MAD), 0 if MAD = 0
+};
+
+enum : int { kGather = 0, kSplit = 1, kFlat = 2, kCrowded = 3 };
+
+// Order-preserving map of a float to uint32 (finite values) and its inverse.
+__device__ __forceinline__ uint32_t order_key(float x) {
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float order_unkey(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// One exact select of ranks `rank` (and rank + 1 when `pair`) of both
+// components over [lo, hi] from this thread's nv register values val(j).
+// hist[sel] must be zero and visible.  On return (after a barrier) every
+// thread holds the order statistics in olo / ohi, and sh.stat the statistic
+// (with sh.inv for the MAD, sel = 1); false (decided by the whole block,
+// nothing written) when a target bucket is crowded.
+template <int NT, int K, class Val>
+__device__ __forceinline__ bool lean_select(LeanShared<NT> &sh, int sel, Val val, int nv, uint32_t rank, bool pair,
+                                            const float (&lo)[2], const float (&hi)[2], float (&olo)[2],
+                                            float (&ohi)[2]) {
+  float scale[2];
+  bool flat[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    flat[c] = !(hi[c] > lo[c]);
+    scale[c] = fast_scale(lo[c], hi[c]);
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    if (j < nv) {
+      const float2 f = val(j);
+      atomicAdd(&sh.hist[sel][0][fast_bucket(f.x, lo[0], scale[0])], 1u);
+      atomicAdd(&sh.hist[sel][1][fast_bucket(f.y, lo[1], scale[1])], 1u);
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 2) {
+    // warp c: the 1024 buckets of component c, 32 per lane (summed in a
+    // skewed order: conflict-free banks), then a warp scan of the lane sums
+    const int c = warp;
+    const uint32_t *h = sh.hist[sel][c] + 32 * lane;
+    uint32_t local = 0;
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) local += h[(q + lane) & 31];
+    uint32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    const uint32_t excl = incl - local;
+    const uint32_t r1 = rank, r2 = rank + (pair ? 1u : 0u);
+    uint32_t b1 = 0, b2 = 0, below = 0, through = 0;
+    bool has1 = false, has2 = false;
+    if ((r1 >= excl && r1 < incl) || (r2 >= excl && r2 < incl)) {
+      uint32_t acc = excl;
+      for (int q = 0; q < 32; ++q) {
+        const uint32_t nxt = acc + h[q];
+        if (r1 >= acc && r1 < nxt) {
+          b1 = 32 * lane + q;
+          below = acc;
+          has1 = true;
+        }
+        if (r2 >= acc && r2 < nxt) {
+          b2 = 32 * lane + q;
+          through = nxt;
+          has2 = true;
+        }
+        acc = nxt;
+      }
+    }
+    const uint32_t m1 = __ballot_sync(0xffffffffu, has1), m2 = __ballot_sync(0xffffffffu, has2);
+    b1 = __shfl_sync(0xffffffffu, b1, __ffs(static_cast<int>(m1)) - 1);
+    below = __shfl_sync(0xffffffffu, below, __ffs(static_cast<int>(m1)) - 1);
+    b2 = __shfl_sync(0xffffffffu, b2, __ffs(static_cast<int>(m2)) - 1);
+    through = __shfl_sync(0xffffffffu, through, __ffs(static_cast<int>(m2)) - 1);
+    if (lane == 0) {
+      int mode = kGather;
+      if (flat[c]) mode = kFlat;
+      else if (through - below <= static_cast<uint32_t>(kCap)) mode = kGather;
+      else if (b1 != b2) mode = kSplit;
+      else mode = kCrowded;
+      sh.mode[c] = mode;
+      sh.b1[c] = b1;
+      sh.b2[c] = b2;
+      sh.below[c] = below;
+      sh.list_n[c] = 0u;
+      sh.kmax[c] = 0u;
+      sh.kmin[c] = 0xffffffffu;
+    }
+  }
+  __syncthreads();
+  const int mode0 = sh.mode[0], mode1 = sh.mode[1];
+  if (mode0 == kCrowded || mode1 == kCrowded) return false;
+  const uint32_t lo0 = sh.b1[0], hi0 = sh.b2[0], lo1 = sh.b1[1], hi1 = sh.b2[1];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    if (j < nv) {
+      const float2 f = val(j);
+      const uint32_t q0 = fast_bucket(f.x, lo[0], scale[0]), q1 = fast_bucket(f.y, lo[1], scale[1]);
+      if (mode0 == kGather && q0 >= lo0 && q0 <= hi0) sh.list[0][atomicAdd(&sh.list_n[0], 1u)] = f.x;
+      if (mode1 == kGather && q1 >= lo1 && q1 <= hi1) sh.list[1][atomicAdd(&sh.list_n[1], 1u)] = f.y;
+      if (mode0 == kSplit) {
+        if (q0 == lo0) atomicMax(&sh.kmax[0], order_key(f.x));
+        if (q0 == hi0) atomicMin(&sh.kmin[0], order_key(f.x));
+      }
+      if (mode1 == kSplit) {
+        if (q1 == lo1) atomicMax(&sh.kmax[1], order_key(f.y));
+        if (q1 == hi1) atomicMin(&sh.kmin[1], order_key(f.y));
+      }
+    }
+  }
+  __syncthreads();
+  if (warp < 2) {
+    const int c = warp;
+    const int mode = c ? mode1 : mode0;
+    if (mode == kGather) {
+      const uint32_t m = sh.list_n[c];
+      const uint32_t want = rank - sh.below[c];
+      for (uint32_t i = lane; i < m; i += 32) {
+        const float v = sh.list[c][i];
+        uint32_t rk = 0;
+        for (uint32_t f = 0; f < m; ++f) {
+          const float u = sh.list[c][f];
+          rk += (u < v || (u == v && f < i)) ? 1u : 0u;
+        }
+        if (rk == want) sh.res[c][0] = v;
+        if (pair && rk == want + 1) sh.res[c][1] = v;
+      }
+    } else if (lane == 0) {
+      sh.res[c][0] = (mode == kFlat) ? lo[c] : order_unkey(sh.kmax[c]);
+      sh.res[c][1] = (mode == kFlat) ? lo[c] : order_unkey(sh.kmin[c]);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const float a = sh.res[c][0], b = pair ? sh.res[c][1] : a;
+      const float st = pair ? mean_of(a, b) : a;
+      sh.stat[c] = st;
+      if (sel == 1) sh.inv[c] = (st > 0.0f) ? static_cast<float>(1.0 / (kKappa * static_cast<double>(st))) : 0.0f;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    olo[c] = sh.res[c][0];
+    ohi[c] = pair ? sh.res[c][1] : sh.res[c][0];
+  }
+  return true;
+}
+
+template <int NT, int K>
+constexpr int lean_min_blocks() {
+  return NT == 1024 ? 1 : (K <= 9 ? 6 : (K <= 17 ? 4 : 2));
+}
+
+template <int NT, int K>
+__global__ void __launch_bounds__(NT, lean_min_blocks<NT, K>()) normalise_lean_kernel(
     const float2 *__restrict__ spec, float *__restrict__ power, float4 *__restrict__ stats,
     const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off, int n_series, int seg_len,
     float *__restrict__ sel) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  RegShared &rs = *reinterpret_cast<RegShared *>(smem_raw);
-  SelShared &sh = *reinterpret_cast<SelShared *>(smem_raw);   // the fallback's (same memory, used after rs)
+  LeanShared<NT> &sh = *reinterpret_cast<LeanShared<NT> *>(smem_raw);
+  SelSharedT<NT> &legacy = *reinterpret_cast<SelSharedT<NT> *>(smem_raw);   // the fallback's (same memory)
   const int64_t g = blockIdx.x;
-  int lo = 0, hi = n_series - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (seg_off[mid] <= g) lo = mid; else hi = mid - 1;
+  int lo_s = 0, hi_s = n_series - 1;
+  while (lo_s < hi_s) {
+    const int mid = (lo_s + hi_s + 1) >> 1;
+    if (seg_off[mid] <= g) lo_s = mid; else hi_s = mid - 1;
   }
-  const SeriesDev S = series[lo];
+  const SeriesDev S = series[lo_s];
   const int64_t sl = g - S.seg_off;
   const int64_t b0 = sl * seg_len;
   const int n = static_cast<int>(((sl == S.n_seg - 1) ? S.m : b0 + seg_len) - b0);
   const float2 *src = spec + S.spec_off + b0;
   const int t = threadIdx.x;
-  const int nv = (t < n) ? min(K, (n - t + kNormThreads - 1) / kNormThreads) : 0;
+  const int nv = (t < n) ? min(K, (n - t + NT - 1) / NT) : 0;
   float2 v[K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) v[j] = (j < nv) ? __ldg(src + j * kNormThreads + t) : make_float2(0.0f, 0.0f);
+  for (int j = 0; j < K; ++j) v[j] = (j < nv) ? __ldg(src + j * NT + t) : make_float2(0.0f, 0.0f);
   const bool dc_here = (b0 == 0);
   if (dc_here && t == 0) v[0] = make_float2(0.0f, 0.0f);   // DC := 0
   auto gval = [&](int e) -> float2 { return (dc_here && e == 0) ? make_float2(0.0f, 0.0f) : src[e]; };
 
+  // range of both components; both selects' histograms zeroed meanwhile
   float a0 = INFINITY, a1 = INFINITY, z0 = -INFINITY, z1 = -INFINITY;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
@@ -754,83 +779,146 @@ __global__ void __launch_bounds__(kNormThreads, reg_min_blocks(K)) normalise_reg
       z1 = fmaxf(z1, v[j].y);
     }
   }
-  reg_minmax(rs, a0, a1, z0, z1);
-  const float mn0 = rs.mm[0], mn1 = rs.mm[1], mx0 = rs.mm[2], mx1 = rs.mm[3];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 = fminf(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+    a1 = fminf(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+    z0 = fmaxf(z0, __shfl_xor_sync(0xffffffffu, z0, o));
+    z1 = fmaxf(z1, __shfl_xor_sync(0xffffffffu, z1, o));
+  }
+  if ((t & 31) == 0) {
+    sh.red[t >> 5][0] = a0;
+    sh.red[t >> 5][1] = a1;
+    sh.red[t >> 5][2] = z0;
+    sh.red[t >> 5][3] = z1;
+  }
+  for (int j = t; j < 4 * kLeanBuckets; j += NT) (&sh.hist[0][0][0])[j] = 0u;
   __syncthreads();
+  float mn[2] = {INFINITY, INFINITY}, mx[2] = {-INFINITY, -INFINITY};
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) {
+    mn[0] = fminf(mn[0], sh.red[w][0]);
+    mn[1] = fminf(mn[1], sh.red[w][1]);
+    mx[0] = fmaxf(mx[0], sh.red[w][2]);
+    mx[1] = fmaxf(mx[1], sh.red[w][3]);
+  }
 
   const bool even = (n % 2) == 0;
   const uint32_t rank = even ? static_cast<uint32_t>(n / 2 - 1) : static_cast<uint32_t>(n / 2);
-  // Two passes through ONE copy of the select code (a smaller kernel keeps
-  // the instruction cache warm): pass 0 selects the median of the values,
-  // pass 1 the median of their absolute deviations from it (the MAD).
-  float med_re = 0.0f, med_im = 0.0f, mad_re = 0.0f, mad_im = 0.0f;
-  float lo0 = mn0, lo1 = mn1, hi0 = mx0, hi1 = mx1;
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    const float c0 = med_re, c1 = med_im;
-    float lo_v[2], hi_v[2];
-    if (!reg_select<K>(rs, [&](int j) {
-          return pass ? make_float2(fabsf(v[j].x - c0), fabsf(v[j].y - c1)) : v[j];
-        }, nv, rank, even, lo0, lo1, hi0, hi1, lo_v, hi_v))
-      select_levels(sh, [&](int e, float &v0, float &v1) {
-        const float2 f = gval(e);
-        v0 = pass ? fabsf(f.x - c0) : f.x;
-        v1 = pass ? fabsf(f.y - c1) : f.y;
-      }, n, rank, even, lo_v, hi_v);
-    float a, b;
-    bcast_mid(rs.mm, lo_v, hi_v, even, a, b);
-    if (sel != nullptr && t == 0) {
-      sel[8 * g + 2 * pass + 0] = lo_v[0];
-      sel[8 * g + 2 * pass + 1] = hi_v[0];
-      sel[8 * g + 2 * pass + 4] = lo_v[1];
-      sel[8 * g + 2 * pass + 5] = hi_v[1];
-    }
-    if (pass == 0) {
-      med_re = a;
-      med_im = b;
-      // the deviations lie in [0, max distance of the block's range from the median]
-      lo0 = 0.0f;
-      lo1 = 0.0f;
-      hi0 = fmaxf(fabsf(mx0 - med_re), fabsf(med_re - mn0));
-      hi1 = fmaxf(fabsf(mx1 - med_im), fabsf(med_im - mn1));
-    } else {
-      mad_re = a;
-      mad_im = b;
-    }
+  float lo_v[2], hi_v[2];
+  float med[2], mad[2], inv[2];
+  bool fell_back = false;
+  if (lean_select<NT, K>(sh, 0, [&](int j) { return v[j]; }, nv, rank, even, mn, mx, lo_v, hi_v)) {
+    med[0] = sh.stat[0];
+    med[1] = sh.stat[1];
+  } else {
+    __syncthreads();
+    select_levels<NT>(legacy, [&](int e, float &v0, float &v1) {
+      const float2 f = gval(e);
+      v0 = f.x;
+      v1 = f.y;
+    }, n, rank, even, lo_v, hi_v);
+    med[0] = even ? mean_of(lo_v[0], hi_v[0]) : lo_v[0];
+    med[1] = even ? mean_of(lo_v[1], hi_v[1]) : lo_v[1];
+    fell_back = true;
   }
-  float inv_re, inv_im;
-  bcast_inv(rs.mm, mad_re, mad_im, inv_re, inv_im);
+  if (sel != nullptr && t == 0) {
+    sel[8 * g + 0] = lo_v[0];
+    sel[8 * g + 1] = hi_v[0];
+    sel[8 * g + 4] = lo_v[1];
+    sel[8 * g + 5] = hi_v[1];
+  }
+  if (fell_back) {
+    // the fallback used the shared memory: zero the MAD histogram again
+    __syncthreads();
+    for (int j = t; j < 2 * kLeanBuckets; j += NT) (&sh.hist[1][0][0])[j] = 0u;
+    __syncthreads();
+  }
+  // MADs: the same selection on |x - med| over [0, the largest deviation]
+  const float c0 = med[0], c1 = med[1];
+  const float dlo[2] = {0.0f, 0.0f};
+  const float dhi[2] = {fmaxf(fabsf(mx[0] - c0), fabsf(c0 - mn[0])), fmaxf(fabsf(mx[1] - c1), fabsf(c1 - mn[1]))};
+  if (lean_select<NT, K>(sh, 1, [&](int j) { return make_float2(fabsf(v[j].x - c0), fabsf(v[j].y - c1)); }, nv,
+                         rank, even, dlo, dhi, lo_v, hi_v)) {
+    mad[0] = sh.stat[0];
+    mad[1] = sh.stat[1];
+    inv[0] = sh.inv[0];
+    inv[1] = sh.inv[1];
+  } else {
+    __syncthreads();
+    select_levels<NT>(legacy, [&](int e, float &v0, float &v1) {
+      const float2 f = gval(e);
+      v0 = fabsf(f.x - c0);
+      v1 = fabsf(f.y - c1);
+    }, n, rank, even, lo_v, hi_v);
+    mad[0] = even ? mean_of(lo_v[0], hi_v[0]) : lo_v[0];
+    mad[1] = even ? mean_of(lo_v[1], hi_v[1]) : lo_v[1];
+    inv[0] = mad[0] > 0.0f ? static_cast<float>(1.0 / (kKappa * static_cast<double>(mad[0]))) : 0.0f;
+    inv[1] = mad[1] > 0.0f ? static_cast<float>(1.0 / (kKappa * static_cast<double>(mad[1]))) : 0.0f;
+  }
+  if (sel != nullptr && t == 0) {
+    sel[8 * g + 2] = lo_v[0];
+    sel[8 * g + 3] = hi_v[0];
+    sel[8 * g + 6] = lo_v[1];
+    sel[8 * g + 7] = hi_v[1];
+  }
+  // a block with either MAD zero is degenerate: P = 0
+  if (!(inv[0] > 0.0f) || !(inv[1] > 0.0f)) {
+    inv[0] = 0.0f;
+    inv[1] = 0.0f;
+  }
   float *out = power + S.p_off + b0;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     if (j < nv) {
-      const float a = (v[j].x - med_re) * inv_re;
-      const float b = (v[j].y - med_im) * inv_im;
-      out[j * kNormThreads + t] = 0.5f * (a * a + b * b);
+      const float a = (v[j].x - med[0]) * inv[0];
+      const float b = (v[j].y - med[1]) * inv[1];
+      out[j * NT + t] = 0.5f * (a * a + b * b);
     }
   }
-  if (t == 0 && stats != nullptr) stats[g] = make_float4(med_re, mad_re, med_im, mad_im);
+  if (t == 0 && stats != nullptr) stats[g] = make_float4(med[0], mad[0], med[1], mad[1]);
 }
 
-// Bins per thread of the register kernel for the plan's largest block (0:
-// too large, use the staged kernel).  Power-of-two series leave a last block
-// of L + 1 bins, hence the odd sizes.
-constexpr int kRegK[] = {1, 2, 3, 4, 5, 6, 8, 9, 12, 16, 17, 24, 32};
+// Kernel shape for the plan's largest block: (threads, bins per thread) of
+// the lean register kernel, or (0, 0) for the staged kernel.  Power-of-two
+// series leave a last block of L + 1 bins, hence the odd sizes.
+constexpr int kLeanK[] = {1, 2, 3, 4, 5, 6, 8, 9, 12, 16, 17, 24, 32};
 
-int reg_bins_per_thread(pulscan_plan p) {
+int64_t largest_block(pulscan_plan p) {
   int64_t max_n = 0;
   for (int64_t i = 0; i < p->n_base; ++i) {
     const auto &se = p->series[i];
     max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
   }
-  for (int k : kRegK)
-    if (max_n <= static_cast<int64_t>(k) * kNormThreads) return k;
-  return 0;
+  return max_n;
 }
 
-template <int K>
-void launch_reg(pulscan_plan p, const float *d_spec, float *d_power, float4 *st4, float *d_sel, cudaStream_t s) {
-  normalise_reg_kernel<K><<<static_cast<unsigned>(p->base_seg), kNormThreads, sizeof(SelShared), s>>>(
+void lean_shape(pulscan_plan p, int *nt, int *k) {
+  const int64_t max_n = largest_block(p);
+  *nt = 0;
+  *k = 0;
+  for (int kk : kLeanK) {
+    if (max_n <= static_cast<int64_t>(kk) * kNormThreads) {
+      *nt = kNormThreads;
+      *k = kk;
+      return;
+    }
+  }
+  if (max_n <= 17LL * 1024) {
+    *nt = 1024;
+    *k = 17;
+  }
+}
+
+template <int NT>
+constexpr int lean_smem() {
+  return static_cast<int>(sizeof(LeanShared<NT>) > sizeof(SelSharedT<NT>) ? sizeof(LeanShared<NT>)
+                                                                          : sizeof(SelSharedT<NT>));
+}
+
+template <int NT, int K>
+void launch_lean(pulscan_plan p, const float *d_spec, float *d_power, float4 *st4, float *d_sel, cudaStream_t s) {
+  normalise_lean_kernel<NT, K><<<static_cast<unsigned>(p->base_seg), NT, lean_smem<NT>(), s>>>(
       reinterpret_cast<const float2 *>(d_spec), d_power, st4, p->d_series, p->d_seg_off,
       static_cast<int>(p->n_base), p->seg_len, d_sel);
 }
@@ -866,23 +954,28 @@ int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, fl
   }
   if (p->base_seg > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many segments");
   float4 *st4 = d_stats ? reinterpret_cast<float4 *>(d_stats) : reinterpret_cast<float4 *>(p->d_stats);
-  switch (reg_bins_per_thread(p)) {
-    case 0: break;
-    case 1: launch_reg<1>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 2: launch_reg<2>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 3: launch_reg<3>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 4: launch_reg<4>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 5: launch_reg<5>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 6: launch_reg<6>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 8: launch_reg<8>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 9: launch_reg<9>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 12: launch_reg<12>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 16: launch_reg<16>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 17: launch_reg<17>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 24: launch_reg<24>(p, d_spec, d_power, st4, d_sel, s); break;
-    default: launch_reg<32>(p, d_spec, d_power, st4, d_sel, s); break;
+  int nt = 0, k = 0;
+  lean_shape(p, &nt, &k);
+  if (nt == 1024) {
+    launch_lean<1024, 17>(p, d_spec, d_power, st4, d_sel, s);
+  } else if (nt > 0) {
+    switch (k) {
+      case 1: launch_lean<kNormThreads, 1>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 2: launch_lean<kNormThreads, 2>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 3: launch_lean<kNormThreads, 3>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 4: launch_lean<kNormThreads, 4>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 5: launch_lean<kNormThreads, 5>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 6: launch_lean<kNormThreads, 6>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 8: launch_lean<kNormThreads, 8>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 9: launch_lean<kNormThreads, 9>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 12: launch_lean<kNormThreads, 12>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 16: launch_lean<kNormThreads, 16>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 17: launch_lean<kNormThreads, 17>(p, d_spec, d_power, st4, d_sel, s); break;
+      case 24: launch_lean<kNormThreads, 24>(p, d_spec, d_power, st4, d_sel, s); break;
+      default: launch_lean<kNormThreads, 32>(p, d_spec, d_power, st4, d_sel, s); break;
+    }
   }
-  if (reg_bins_per_thread(p) > 0) {
+  if (nt > 0) {
     PS_CUDA(cudaGetLastError());
     return PULSCAN_OK;
   }

@@ -73,13 +73,13 @@ def _gauss(m, seed):
 
 
 @pytest.mark.parametrize("n,seg_len", [(1 << 14, 2048), (1 << 13, 1000), (1 << 15, 4096), (1 << 16, 8192),
-                                       (1 << 16, 16384), (1 << 12, 37)])
+                                       (1 << 17, 16384), (1 << 16, 16384), (1 << 12, 37)])
 def test_gaussian_blocks(pkg, n, seg_len):
     spec = _gauss(n // 2 + 1, n + seg_len)
     _check(*_run(pkg, spec, n, seg_len), seg_len)
 
 
-@pytest.mark.parametrize("n,seg_len", [(1 << 14, 2048), (1 << 16, 16384)])
+@pytest.mark.parametrize("n,seg_len", [(1 << 14, 2048), (1 << 15, 8192), (1 << 16, 16384)])
 def test_crowded_buckets_fall_back_to_levels(pkg, n, seg_len):
     """A few outliers 1e5 times the noise: ~all values land in one bucket."""
     m = n // 2 + 1
@@ -91,16 +91,16 @@ def test_crowded_buckets_fall_back_to_levels(pkg, n, seg_len):
     _check(*_run(pkg, spec, n, seg_len), seg_len)
 
 
-def test_integer_ties(pkg):
-    n, seg_len = 1 << 14, 2048
+@pytest.mark.parametrize("n,seg_len", [(1 << 14, 2048), (1 << 17, 16384)])
+def test_integer_ties(pkg, n, seg_len):
     m = n // 2 + 1
     rng = np.random.default_rng(8)
     spec = rng.integers(-3, 4, m).astype(np.float64) + 1j * rng.integers(-2, 3, m).astype(np.float64)
     _check(*_run(pkg, spec, n, seg_len), seg_len)
 
 
-def test_median_inside_a_run_of_equal_values(pkg):
-    n, seg_len = 1 << 13, 1024
+@pytest.mark.parametrize("n,seg_len", [(1 << 13, 1024), (1 << 15, 8192)])
+def test_median_inside_a_run_of_equal_values(pkg, n, seg_len):
     m = n // 2 + 1
     spec = _gauss(m, 9)
     rng = np.random.default_rng(10)
@@ -118,3 +118,22 @@ def test_constant_block_gives_zero_power(pkg):
     p_gpu, st_gpu, p_ref, st_ref, flags = _run(pkg, spec, n, seg_len)
     assert flags[1] and not flags[0]
     _check(p_gpu, st_gpu, p_ref, st_ref, flags, seg_len)
+
+
+@pytest.mark.parametrize("n,seg_len", [(1 << 13, 2048), (1 << 15, 8192)])
+def test_middle_pair_split_over_two_crowded_buckets(pkg, n, seg_len):
+    """Each block holds half its values in a narrow cluster at -1 and half at
+    +1 (each within 1e-4), per component: the two middle order statistics sit
+    in two crowded buckets with only empty buckets between them (decided from
+    the two buckets' extremes), and every deviation from the median lies in
+    one crowded bucket (the multi-level select)."""
+    m = n // 2 + 1
+    rng = np.random.default_rng(12)
+    spec = np.empty(m, dtype=complex)
+    for lo, hi in onorm.block_bounds(m, seg_len):
+        k = hi - lo
+        half = np.r_[-np.ones(k // 2), np.ones(k - k // 2)]
+        re = rng.permutation(half) * (1.0 + 1e-4 * rng.random(k))
+        im = rng.permutation(half) * (1.0 + 1e-4 * rng.random(k))
+        spec[lo:hi] = re + 1j * im
+    _check(*_run(pkg, spec, n, seg_len), seg_len)

@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable 4096-binary measurement")
     ap.add_argument("--only-headline", action="store_true",
                     help="skip every section after the headline's timed steps (profiling)")
+    ap.add_argument("--only-diff", action="store_true",
+                    help="run only the differentiable measurement and print its JSON (profiling)")
     ap.add_argument("--diff-binaries", type=int, default=None,
                     help="run the differentiable measurement on its first N binaries only (profiling)")
     ap.add_argument("--no-graph", action="store_true",
@@ -649,6 +651,11 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    if args.only_diff:
+        r = run_diff(torch, pkg, synth, dev, torch.cuda.Stream(device=dev), 3, args.diff_binaries)
+        if rank == 0:
+            print(json.dumps({"differentiable": r}), flush=True)
+        return
     name = args.workload
     cfg = synth.WORKLOADS[name]
     n, w_max, seg_len, sigma = cfg["n"], cfg["z_max"], cfg["segment_len"], cfg["sigma"]

@@ -46,6 +46,7 @@
 //   dL/dA = sum_n dL/dx[n] template[n], per series.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include <cuda_fp16.h>
 
@@ -139,16 +140,22 @@ __device__ __forceinline__ void ring_steps(float (&s)[kR], float (&b)[kR], const
   }
 }
 
-// Runs widths 1..W over the lane's 33 sums, calling cb(w, c, s) after each
+// Runs widths 1..W over the lane's 33 sums, calling cb(w, c, full) after each
 // width's adds: full 33-width blocks use the ring, the last partial block
-// reads the window straight from shared memory.  block_end(bi, nsteps) is
-// called after every block.
-template <class F, class G>
-__device__ __forceinline__ void walk_widths(float (&s)[kR], const float *__restrict__ lane_buf, int W, F &&cb,
-                                            G &&block_end) {
+// reads the window straight from shared memory.  full is a compile-time
+// flag: full_block(bi, nsteps) (warp-uniform) says whether every lane of the
+// warp has all its windows valid through block bi, and such blocks run an
+// instantiation of the 33 steps with no per-step branch (a branch in every
+// step splits the unrolled body, and the steps could no longer overlap).
+// block_end(bi, nsteps) is called after every block.
+// Start bins i >= n_valid (past the segment's end) start at -inf and stay
+// there, so they never win a maximum and need no mask.
+template <class Full, class F, class G>
+__device__ __forceinline__ void walk_widths(float (&s)[kR], const float *__restrict__ lane_buf, int W, int n_valid,
+                                            Full &&full_block, F &&cb, G &&block_end) {
   float b[kR];
 #pragma unroll
-  for (int i = 0; i < kR; ++i) s[i] = 0.0f;
+  for (int i = 0; i < kR; ++i) s[i] = (i < n_valid) ? 0.0f : -INFINITY;
 #pragma unroll
   for (int j = 0; j < kR - 1; ++j) b[j] = lane_buf[j];
   b[kR - 1] = 0.0f;
@@ -158,13 +165,16 @@ __device__ __forceinline__ void walk_widths(float (&s)[kR], const float *__restr
     const int wf = bi * kR + 1;
     const int nsteps = min(kR, W - bi * kR);
     if (nsteps == kR) {
-      ring_steps<0, kR>(s, b, pb, [&](int c) { cb(wf + c, c); });
+      if (full_block(bi, nsteps))
+        ring_steps<0, kR>(s, b, pb, [&](int c) { cb(wf + c, c, std::true_type{}); });
+      else
+        ring_steps<0, kR>(s, b, pb, [&](int c) { cb(wf + c, c, std::false_type{}); });
     } else {
       for (int c = 0; c < nsteps; ++c) {
         const float *pw = lane_buf + (wf + c - 1);
 #pragma unroll
         for (int i = 0; i < kR; ++i) s[i] += pw[i];
-        cb(wf + c, c);
+        cb(wf + c, c, std::false_type{});
       }
     }
     block_end(bi, nsteps);
@@ -222,10 +232,13 @@ __device__ __forceinline__ SegTile seg_tile(const SeriesDev *__restrict__ series
 
 // Valid windows of the lane starting at local bin x at width w: start inside
 // the segment, window inside the spectrum:  lim(w) = clamp(min(a, b - w), 0, 33)
-// with a = nb - x and b = M - (b0 + x) + 1 fixed per lane.
+// with a = nb - x and b = M - (b0 + x) + 1 fixed per lane.  The running sums
+// of bins past a start at -inf (walk_widths), so only the spectrum's end needs
+// a mask: `masked(w)` says whether it cuts one of the lane's windows at width w.
 struct LaneLim {
   int a, b;
   __device__ __forceinline__ int at(int w) const { return max(0, min(kR, min(a, b - w))); }
+  __device__ __forceinline__ bool masked(int w) const { return a > 0 && b - w < min(a, kR); }
 };
 
 __device__ __forceinline__ LaneLim lane_lim(const SegTile &t, int x) {
@@ -239,27 +252,12 @@ __device__ __forceinline__ float max3(float a, float b, float c) {
   return r;
 }
 
-// max over the lane's first lim windows (-inf if none).
-__device__ __forceinline__ float lane_max(const float (&s)[kR], int lim) {
-  float m = -INFINITY;
-  if (lim >= kR) {
-    float t11[11];
-#pragma unroll
-    for (int i = 0; i < 11; ++i) t11[i] = max3(s[3 * i], s[3 * i + 1], s[3 * i + 2]);
-    m = fmaxf(max3(max3(t11[0], t11[1], t11[2]), max3(t11[3], t11[4], t11[5]), max3(t11[6], t11[7], t11[8])),
-              fmaxf(t11[9], t11[10]));
-  } else {
-#pragma unroll
-    for (int i = 0; i < kR; ++i) m = fmaxf(m, (i < lim) ? s[i] : -INFINITY);
-  }
-  return m;
-}
-
 // Maxima of the lane's three 11-bin groups (windows i < lim only; -inf where
-// none) and their maximum.
+// none) and their maximum.  kFull: all 33 windows valid (lim ignored).
 constexpr int kGrp = 11;
+template <bool kFull>
 __device__ __forceinline__ float lane_groups(const float (&s)[kR], int lim, float (&g)[3]) {
-  if (lim >= kR) {
+  if (kFull) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int o = kGrp * j;
@@ -349,10 +347,10 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   // of the lanes within `cut` of M (a group below lane max - cut is below
   // M - cut too) have their windows summed.
   walk_widths(
-      s, buf + x0, W,
-      [&](int w, int c) {
+      s, buf + x0, W, ll.a, [&](int bi, int nsteps) { return !__any_sync(kFullMask, ll.masked(bi * kR + nsteps)); },
+      [&](int w, int c, auto full) {
         float g[3];
-        const float lm = lane_groups(s, ll.at(w), g);
+        const float lm = lane_groups<decltype(full)::value>(s, ll.at(w), g);
         kmax[(warp * kR + c) * 32 + lane] = lm;
         const float lo = lm - cut;
         kgrp[(warp * kR + c) * 32 + lane] =
@@ -419,7 +417,8 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   float *yrow = buf + buf_len;
   float *ylrow = yrow + W;                       // Y's low parts
   float *grow = ylrow + W;
-  float *dd = grow + W;                          // d_len difference entries
+  float *trow = grow + W;                        // Y - cut, +inf where G = 0
+  float *dd = trow + W;                          // d_len difference entries
   float *wsum = dd + d_len;                      // per-warp scan totals
   uint32_t *evm = reinterpret_cast<uint32_t *>(wsum + 32);   // warps x 33 event ballots
   int *evl = reinterpret_cast<int *>(evm + kLseMaxWarps * kR);   // warps x 96 flagged-group lists
@@ -430,9 +429,12 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
   build_prefix(buf, buf_len, fh, fl, wtot);
   for (int j = threadIdx.x; j < W; j += blockDim.x) {
-    yrow[j] = y[t.seg_g * static_cast<int64_t>(W) + j];
-    ylrow[j] = ylo[t.seg_g * static_cast<int64_t>(W) + j];
-    grow[j] = gy[t.seg_g * static_cast<int64_t>(W) + j];
+    const int64_t o = t.seg_g * static_cast<int64_t>(W) + j;
+    const float gj = gy[o];
+    yrow[j] = y[o];
+    ylrow[j] = ylo[o];
+    grow[j] = gj;
+    trow[j] = (gj != 0.0f) ? y[o] - cut : INFINITY;
   }
   for (int j = threadIdx.x; j < d_len; j += blockDim.x) dd[j] = 0.0f;
   __syncthreads();
@@ -443,18 +445,24 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   uint32_t *wev = evm + warp * kR;
   const LaneLim ll = lane_lim(t, x0);
   float s[kR];
+  uint64_t hot = 0ull;   // steps of the current block at which this lane has a flagged group
   walk_widths(
-      s, lane_buf, W,
-      [&](int w, int c) {
+      s, lane_buf, W, ll.a, [&](int bi, int nsteps) { return !__any_sync(kFullMask, ll.masked(bi * kR + nsteps)); },
+      [&](int w, int c, auto full) {
         float g[3];
-        lane_groups(s, ll.at(w), g);
-        const float thr = grow[w - 1] != 0.0f ? yrow[w - 1] - cut : INFINITY;
+        lane_groups<decltype(full)::value>(s, ll.at(w), g);
+        const float thr = trow[w - 1];
         const uint32_t m = (g[0] > thr ? 1u : 0u) | (g[1] > thr ? 2u : 0u) | (g[2] > thr ? 4u : 0u);
         kgrp[(warp * kR + c) * 32 + lane] = static_cast<uint8_t>(m);
-        const uint32_t bal = __ballot_sync(kFullMask, m != 0u);
-        if (lane == 0) wev[c] = bal;
+        hot |= static_cast<uint64_t>(m != 0u) << c;
       },
       [&](int bi, int nsteps) {
+        // per step, the warp's lanes with a flagged group
+        for (int c = 0; c < nsteps; ++c) {
+          const uint32_t bal = __ballot_sync(kFullMask, (hot >> c) & 1ull);
+          if (lane == 0) wev[c] = bal;
+        }
+        hot = 0ull;
         __syncwarp();
         for (int c = 0; c < nsteps; ++c) {
           const uint32_t bal = wev[c];
@@ -791,7 +799,7 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   int64_t max_n = 0;
   for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
   const int d_len = static_cast<int>(max_n + p->z_max + 1);
-  const int smem = 128 + 4 * (buf_len + 3 * p->z_max + d_len + 32 + kLseMaxWarps * (kR + 96) +
+  const int smem = 128 + 4 * (buf_len + 4 * p->z_max + d_len + 32 + kLseMaxWarps * (kR + 96) +
                               kLseMaxWarps * kR * 8 + (buf_len + 1)) + 2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
   if (rc) return rc;

@@ -276,39 +276,106 @@ __device__ __forceinline__ float lane_groups(const float (&s)[kR], int lim, floa
   return max3(g[0], g[1], g[2]);
 }
 
-// Works off one width's events of this warp: the 11-bin groups flagged by
-// their lanes (grp: this lane's 3-bit mask, zero if not flagged), their
-// windows packed over the warp's lanes; every window whose exact sum lies
-// above thr calls f(k, hi, lo) with k the local start bin and S = hi + lo
-// (window_sum2).  A window is first
-// screened with the high parts of the prefix alone: each is within half an
-// ulp of F, so fh[b] - fh[a] is within 1.5 ulp of S; the margin is 4 ulp of
-// F[b].  my_lim: the calling lane's valid window count at w; evl: this warp's
-// 96-entry scratch for the list of flagged groups.
-template <class F>
-__device__ __forceinline__ void for_event_windows(uint32_t grp, int warp, int lane, int my_lim, int w, float thr,
-                                                  const float *__restrict__ fh, const __half *__restrict__ fl,
-                                                  int *evl, F &&f) {
-  int n_ev = 0;
+// The window limits of a segment in 32-bit form: start bin x of the
+// segment has valid windows of width w for its lane's bins up to
+// lim = clamp(min(nb - x, room - x - w), 0, 33), room = M - b0 + 1.
+struct SegLim {
+  int nb, room;
+  __device__ __forceinline__ int at(int x, int w) const { return max(0, min(kR, min(nb - x, room - x - w))); }
+};
+
+__device__ __forceinline__ SegLim seg_lim(const SegTile &t) {
+  return SegLim{t.nb, static_cast<int>(min64(t.m - t.b0 + 1, static_cast<int64_t>(1) << 30))};
+}
+
+// All events of one 33-width block at once: (step c, lane l, group j)
+// triples, c | l << 6 | j << 11, for every 11-bin group whose flag
+// flags(c, l) (a 3-bit mask, read by the lane that owns step c: lane c, and
+// lane 0 for step 32) is set; then their windows (11 per event) are worked
+// off by the whole warp, two per lane per trip (independent chains of shared
+// loads), in rounds of at most kEvCap events.  Collecting a block's events
+// first gives the window work the whole block's parallelism instead of one
+// width's.  evl: the warp's list (kEvCap entries; it may reuse the flags'
+// memory: every flag is read before the first entry is written).
+// f(c, k, w, hi, lo) is called for every window whose exact sum lies above
+// thr(c) (S = hi + lo, k the segment-local start bin).
+constexpr int kEvCap = 256;
+
+template <class Flags, class Thr, class F>
+__device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lane, int wf, int nsteps, Flags flags,
+                                             Thr thr, const float *__restrict__ fh, const __half *__restrict__ fl,
+                                             int *evl, F &&f) {
+  // this lane's steps (lane, and 32 for lane 0): per step three 32-bit
+  // masks, mask j holding group j of every lane
+  uint32_t mk[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const uint32_t bj = __ballot_sync(kFullMask, (grp >> j) & 1u);
-    if ((bj >> lane) & 1u) evl[n_ev + __popc(bj & ((1u << lane) - 1u))] = lane | (j << 5) | (my_lim << 8);
-    n_ev += __popc(bj);
+  for (int r = 0; r < 2; ++r) {
+    const int c = r ? kR - 1 : lane;
+    if ((r == 0 && lane < nsteps) || (r == 1 && lane == 0 && nsteps == kR)) {
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) {
+        const int ls = (l + c) & 31;   // skewed: conflict-free reads
+        const uint32_t fg = flags(c, ls);
+        mk[r][0] |= (fg & 1u) << ls;
+        mk[r][1] |= ((fg >> 1) & 1u) << ls;
+        mk[r][2] |= ((fg >> 2) & 1u) << ls;
+      }
+    }
   }
-  __syncwarp();
-  const int n = kGrp * n_ev;
-  for (int q = lane; q < n; q += 32) {
-    const int e = q / kGrp;
-    const int ev = evl[e];
-    const int i = kGrp * ((ev >> 5) & 7) + (q - kGrp * e);   // bin of the lane
-    if (i < (ev >> 8)) {
-      const int k = warp * (32 * kR) + (ev & 31) * kR + i;
-      const float hb = fh[k + w];
-      if (hb - fh[k] > thr - 4.8e-7f * fabsf(hb)) {
-        float lo;
-        const float hi = window_sum2(fh, fl, k, k + w, lo);
-        if (__fadd_rn(__fsub_rn(hi, thr), lo) > 0.0f) f(k, hi, lo);
+  const uint32_t cnt = __popc(mk[0][0]) + __popc(mk[0][1]) + __popc(mk[0][2]) + __popc(mk[1][0]) +
+                       __popc(mk[1][1]) + __popc(mk[1][2]);
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(kFullMask, incl, o);
+    if (lane >= o) incl += u;
+  }
+  const int n_ev = static_cast<int>(__shfl_sync(kFullMask, incl, 31));
+  const int first = static_cast<int>(incl - cnt);   // this lane's events are [first, incl)
+  for (int base = 0; base < n_ev; base += kEvCap) {
+    __syncwarp();
+    int pos = first;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int c = r ? kR - 1 : lane;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        for (uint32_t mm = mk[r][j]; mm != 0u; mm &= mm - 1u, ++pos)
+          if (pos >= base && pos < base + kEvCap) evl[pos - base] = c | ((__ffs(static_cast<int>(mm)) - 1) << 6) | (j << 11);
+      }
+    }
+    __syncwarp();
+    const int total = kGrp * min(kEvCap, n_ev - base);
+    for (int q0 = lane; q0 < total; q0 += 64) {
+      float hb[2], ha[2], th[2];
+      int kk[2], ww[2], cc[2];
+      bool ok[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int q = q0 + 32 * u;
+        ok[u] = q < total;
+        const int e = ok[u] ? q / kGrp : 0;
+        const int i = q - kGrp * e;
+        const int ev = evl[e];
+        cc[u] = ev & 63;
+        const int l = (ev >> 6) & 31, jg = ev >> 11;
+        ww[u] = wf + cc[u];
+        const int x = warp * (32 * kR) + l * kR;
+        const int b = kGrp * jg + i;   // bin of the lane
+        ok[u] = ok[u] && b < sl.at(x, ww[u]);
+        kk[u] = x + b;
+        th[u] = thr(cc[u]);
+        hb[u] = ok[u] ? fh[kk[u] + ww[u]] : 0.0f;
+        ha[u] = ok[u] ? fh[kk[u]] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        // fh alone is within 1.5 ulp of F: screen first
+        if (ok[u] && hb[u] - ha[u] > th[u] - 4.8e-7f * fabsf(hb[u])) {
+          float lo;
+          const float hi = window_sum2(fh, fl, kk[u], kk[u] + ww[u], lo);
+          if (__fadd_rn(__fsub_rn(hi, th[u]), lo) > 0.0f) f(cc[u], kk[u], ww[u], hi, lo);
+        }
       }
     }
   }
@@ -326,8 +393,7 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
   float *mblk = buf + buf_len;                   // 64: M of the current 33 widths
   float *lsb = mblk + 64;                        // 64: their sums of exp
-  int *evl = reinterpret_cast<int *>(lsb + 64);  // warps x 96 flagged-group lists
-  float *kmax = reinterpret_cast<float *>(evl + kLseMaxWarps * 96);   // warps x 33 x 32 lane maxima
+  float *kmax = lsb + 64;                        // warps x 33 x 32 lane maxima
   const int warps = blockDim.x >> 5;
   uint8_t *kgrp = reinterpret_cast<uint8_t *>(kmax + warps * kR * 32);   // their group masks
   float *wmax = kmax + warps * kR * 32 + warps * kR * 8;   // warps x 33 per-warp maxima
@@ -339,6 +405,7 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int x0 = warp * (32 * kR) + lane * kR;
   const LaneLim ll = lane_lim(t, x0);
+  const SegLim sgl = seg_lim(t);
   const float inv_tau = 1.0f / tau;
   float s[kR];
   // One sweep over the widths.  Per step every lane stores the max of its 33
@@ -374,22 +441,17 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
           lsb[c] = 0.0f;
         }
         __syncthreads();
-        for (int c = 0; c < nsteps; ++c) {
-          const float mw = mblk[c];
-          const float thr = mw - cut;
-          const bool hot = kmax[(warp * kR + c) * 32 + lane] > thr;
-          if (!__any_sync(kFullMask, hot)) continue;
-          float acc = 0.0f;
-          const int w = bi * kR + c + 1;
-          const uint32_t grp = hot ? kgrp[(warp * kR + c) * 32 + lane] : 0u;
-          for_event_windows(grp, warp, lane, ll.at(w), w, thr, fh, fl, evl + warp * 96,
-                            [&](int, float hi, float lo) {
-                              acc += expf(__fadd_rn(__fsub_rn(hi, mw), lo) * inv_tau);
-                            });
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
-          if (lane == 0) atomicAdd(&lsb[c], acc);
-        }
+        // the block's events: groups of lanes within the cut of M (the list
+        // reuses the warp's lane maxima, all read first)
+        const float *km = kmax + warp * (kR * 32);
+        const uint8_t *kg = kgrp + warp * (kR * 32);
+        block_events(
+            sgl, warp, lane, bi * kR + 1, nsteps,
+            [&](int c, int l) { return (km[c * 32 + l] > mblk[c] - cut) ? static_cast<uint32_t>(kg[c * 32 + l]) : 0u; },
+            [&](int c) { return mblk[c] - cut; }, fh, fl, reinterpret_cast<int *>(kmax + warp * (kR * 32)),
+            [&](int c, int, int, float hi, float lo) {
+              atomicAdd(&lsb[c], expf(__fadd_rn(__fsub_rn(hi, mblk[c]), lo) * inv_tau));
+            });
         __syncthreads();
         // Y = M + tau log(sum) as a pair: the FP32 value and its exact
         // rounding error (the backward's weights exp((S - Y) / tau) need Y to
@@ -420,9 +482,7 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   float *trow = grow + W;                        // Y - cut, +inf where G = 0
   float *dd = trow + W;                          // d_len difference entries
   float *wsum = dd + d_len;                      // per-warp scan totals
-  uint32_t *evm = reinterpret_cast<uint32_t *>(wsum + 32);   // warps x 33 event ballots
-  int *evl = reinterpret_cast<int *>(evm + kLseMaxWarps * kR);   // warps x 96 flagged-group lists
-  uint8_t *kgrp = reinterpret_cast<uint8_t *>(evl + kLseMaxWarps * 96);   // warps x 33 x 32 group masks
+  uint8_t *kgrp = reinterpret_cast<uint8_t *>(wsum + 32);   // warps x 33 x 32 group masks
   float *fh = reinterpret_cast<float *>(kgrp + kLseMaxWarps * kR * 32);   // prefix: high part, buf_len + 1
   __half *fl = reinterpret_cast<__half *>(fh + buf_len + 1);   // low part, buf_len + 1
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
@@ -442,10 +502,9 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   const int x0 = warp * (32 * kR) + lane * kR;
   const float *lane_buf = buf + x0;
   const float inv_tau = 1.0f / tau;
-  uint32_t *wev = evm + warp * kR;
   const LaneLim ll = lane_lim(t, x0);
+  const SegLim sgl = seg_lim(t);
   float s[kR];
-  uint64_t hot = 0ull;   // steps of the current block at which this lane has a flagged group
   walk_widths(
       s, lane_buf, W, ll.a, [&](int bi, int nsteps) { return !__any_sync(kFullMask, ll.masked(bi * kR + nsteps)); },
       [&](int w, int c, auto full) {
@@ -454,32 +513,22 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
         const float thr = trow[w - 1];
         const uint32_t m = (g[0] > thr ? 1u : 0u) | (g[1] > thr ? 2u : 0u) | (g[2] > thr ? 4u : 0u);
         kgrp[(warp * kR + c) * 32 + lane] = static_cast<uint8_t>(m);
-        hot |= static_cast<uint64_t>(m != 0u) << c;
       },
       [&](int bi, int nsteps) {
-        // per step, the warp's lanes with a flagged group
-        for (int c = 0; c < nsteps; ++c) {
-          const uint32_t bal = __ballot_sync(kFullMask, (hot >> c) & 1ull);
-          if (lane == 0) wev[c] = bal;
-        }
-        hot = 0ull;
         __syncwarp();
-        for (int c = 0; c < nsteps; ++c) {
-          const uint32_t bal = wev[c];
-          if (bal == 0u) continue;
-          const int w = bi * kR + c + 1;
-          const float yw = yrow[w - 1];
-          const float ylw = ylrow[w - 1];
-          const float gw = grow[w - 1];
-          for_event_windows(kgrp[(warp * kR + c) * 32 + lane], warp, lane, ll.at(w), w, yw - cut, fh, fl,
-                            evl + warp * 96, [&](int k, float hi, float lo) {
-            // (S - Y) from the two pairs: hi - yw is exact (Sterbenz)
-            const float g = gw * expf(__fadd_rn(__fsub_rn(hi, yw), __fsub_rn(lo, ylw)) * inv_tau);
-            atomicAdd(&dd[k], g);
-            atomicAdd(&dd[k + w], -g);
-          });
-        }
-        __syncwarp();
+        // the block's events (the list reuses the warp's flags, all read first)
+        const uint8_t *kg = kgrp + warp * (kR * 32);
+        const int wf = bi * kR + 1;
+        block_events(
+            sgl, warp, lane, wf, nsteps, [&](int c, int l) { return static_cast<uint32_t>(kg[c * 32 + l]); },
+            [&](int c) { return trow[wf + c - 1]; }, fh, fl, reinterpret_cast<int *>(kgrp + warp * (kR * 32)),
+            [&](int, int k, int w, float hi, float lo) {
+              // (S - Y) from the two pairs: hi - Y is exact (Sterbenz)
+              const float g =
+                  grow[w - 1] * expf(__fadd_rn(__fsub_rn(hi, yrow[w - 1]), __fsub_rn(lo, ylrow[w - 1])) * inv_tau);
+              atomicAdd(&dd[k], g);
+              atomicAdd(&dd[k + w], -g);
+            });
       });
   __syncthreads();
   // inclusive prefix sum of dd: thread t owns a contiguous chunk
@@ -772,7 +821,7 @@ int pulscan_lse_forward(pulscan_plan p, const float *d_x, float *d_spec, float *
   if (rc) return rc;
   const int warps = lse_warps(p);
   const int buf_len = lse_buf_len(p, warps);
-  const int smem = 128 + 4 * (buf_len + 128 + kLseMaxWarps * 96 + warps * kR * 32 + warps * kR * 8 +
+  const int smem = 128 + 4 * (buf_len + 128 + warps * kR * 32 + warps * kR * 8 +
                               kLseMaxWarps * kR + (buf_len + 1)) + 2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_forward_kernel, smem, g_lim_fwd);
   if (rc) return rc;
@@ -799,8 +848,8 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   int64_t max_n = 0;
   for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
   const int d_len = static_cast<int>(max_n + p->z_max + 1);
-  const int smem = 128 + 4 * (buf_len + 4 * p->z_max + d_len + 32 + kLseMaxWarps * (kR + 96) +
-                              kLseMaxWarps * kR * 8 + (buf_len + 1)) + 2 * (buf_len + 1) + 16;
+  const int smem = 128 + 4 * (buf_len + 4 * p->z_max + d_len + 32 + kLseMaxWarps * kR * 8 + (buf_len + 1)) +
+                   2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
   if (rc) return rc;
   lse_backward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(

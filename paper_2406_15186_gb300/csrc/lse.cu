@@ -289,39 +289,22 @@ __device__ __forceinline__ SegLim seg_lim(const SegTile &t) {
 }
 
 // All events of one 33-width block at once: (step c, lane l, group j)
-// triples, c | l << 6 | j << 11, for every 11-bin group whose flag
-// flags(c, l) (a 3-bit mask, read by the lane that owns step c: lane c, and
-// lane 0 for step 32) is set; then their windows (11 per event) are worked
-// off by the whole warp, two per lane per trip (independent chains of shared
-// loads), in rounds of at most kEvCap events.  Collecting a block's events
-// first gives the window work the whole block's parallelism instead of one
-// width's.  evl: the warp's list (kEvCap entries; it may reuse the flags'
-// memory: every flag is read before the first entry is written).
-// f(c, k, w, hi, lo) is called for every window whose exact sum lies above
-// thr(c) (S = hi + lo, k the segment-local start bin).
-constexpr int kEvCap = 256;
+// triples, c | l << 6 | j << 11, for every 11-bin group whose bit is set in
+// the step masks mk (ballots: bit l of mk[r][j] is group j of lane l; this
+// lane holds those of step `lane` in mk[0] and lane 0 also those of step 32
+// in mk[1], zero where the lane owns no step); then their windows (11 per
+// event) are worked off by the whole warp, two per lane per trip
+// (independent chains of shared loads), in rounds of at most kEvCap events.
+// Collecting a block's events first gives the window work the whole
+// block's parallelism instead of one width's.  evl: the warp's list
+// (kEvCap entries).  f(c, k, w, hi, lo) is called for every window whose
+// exact sum lies above thr(c) (S = hi + lo, k the segment-local start bin).
+constexpr int kEvCap = 128;
 
-template <class Flags, class Thr, class F>
-__device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lane, int wf, int nsteps, Flags flags,
+template <class Thr, class F>
+__device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lane, int wf, const uint32_t (&mk)[2][3],
                                              Thr thr, const float *__restrict__ fh, const __half *__restrict__ fl,
                                              int *evl, F &&f) {
-  // this lane's steps (lane, and 32 for lane 0): per step three 32-bit
-  // masks, mask j holding group j of every lane
-  uint32_t mk[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int c = r ? kR - 1 : lane;
-    if ((r == 0 && lane < nsteps) || (r == 1 && lane == 0 && nsteps == kR)) {
-#pragma unroll 8
-      for (int l = 0; l < 32; ++l) {
-        const int ls = (l + c) & 31;   // skewed: conflict-free reads
-        const uint32_t fg = flags(c, ls);
-        mk[r][0] |= (fg & 1u) << ls;
-        mk[r][1] |= ((fg >> 1) & 1u) << ls;
-        mk[r][2] |= ((fg >> 2) & 1u) << ls;
-      }
-    }
-  }
   const uint32_t cnt = __popc(mk[0][0]) + __popc(mk[0][1]) + __popc(mk[0][2]) + __popc(mk[1][0]) +
                        __popc(mk[1][1]) + __popc(mk[1][2]);
   uint32_t incl = cnt;
@@ -382,6 +365,16 @@ __device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lan
   __syncwarp();
 }
 
+// The warp's maximum of v (a single reduction instruction on sm_100+).
+__device__ __forceinline__ float warp_max(float v) {
+  float r;
+  asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+// Per-warp rows of 33 widths, double-buffered by block parity.
+constexpr int kRows = kLseMaxWarps * kR;
+
 __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
     int n_series, int W, int seg_len, float tau, float cut, float *__restrict__ y, float *__restrict__ ylo,
@@ -391,14 +384,13 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   double *wtot = reinterpret_cast<double *>(smem_raw + 32);
   uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
-  float *mblk = buf + buf_len;                   // 64: M of the current 33 widths
-  float *lsb = mblk + 64;                        // 64: their sums of exp
-  float *kmax = lsb + 64;                        // warps x 33 x 32 lane maxima
+  float *wmax = buf + buf_len;          // [2][warps][33]: each warp's maximum per width
+  float *mrow = wmax + 2 * kRows;       // [2][warps][33]: M per width, a copy per warp
+  float *lsbw = mrow + 2 * kRows;       // [2][warps][33]: each warp's sums of exp
   const int warps = blockDim.x >> 5;
-  uint8_t *kgrp = reinterpret_cast<uint8_t *>(kmax + warps * kR * 32);   // their group masks
-  float *wmax = kmax + warps * kR * 32 + warps * kR * 8;   // warps x 33 per-warp maxima
-  float *fh = wmax + kLseMaxWarps * kR;                   // prefix: high part, buf_len + 1
-  __half *fl = reinterpret_cast<__half *>(fh + buf_len + 1);   // low part, buf_len + 1
+  int *evl = reinterpret_cast<int *>(lsbw + 2 * kRows);   // warps x kEvCap event lists
+  float *fh = reinterpret_cast<float *>(evl + warps * kEvCap);   // prefix: high part, buf_len + 1
+  __half *fl = reinterpret_cast<__half *>(fh + buf_len + 1);     // low part, buf_len + 1
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
   build_prefix(buf, buf_len, fh, fl, wtot);
@@ -407,63 +399,92 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   const LaneLim ll = lane_lim(t, x0);
   const SegLim sgl = seg_lim(t);
   const float inv_tau = 1.0f / tau;
+  // Y = M + tau log(sum) of block bj's widths as a pair: the FP32 value and
+  // its exact rounding error (the backward's weights exp((S - Y) / tau) need
+  // Y to better than FP32 resolution: an error dY moves them all by dY / tau).
+  // Thread c (< nst) takes width c: the warps' partial sums, its own warp's M.
+  auto emit_y = [&](int bj, int nst) {
+    const int pp = bj & 1;
+    for (int c = threadIdx.x; c < nst; c += blockDim.x) {
+      float sum = 0.0f;
+      for (int v = 0; v < warps; ++v) sum += lsbw[pp * kRows + v * kR + c];
+      float e;
+      const float yh = two_sum(mrow[pp * kRows + warp * kR + c], tau * logf(sum), e);
+      const int64_t o = t.seg_g * static_cast<int64_t>(W) + bj * kR + c;
+      y[o] = yh;
+      ylo[o] = e;
+    }
+  };
   float s[kR];
-  // One sweep over the widths.  Per step every lane stores the max of its 33
-  // windows and which of its 11-bin groups come within `cut` of that max;
-  // after each 33-width block the lane maxima give M[s, w], and the groups
-  // of the lanes within `cut` of M (a group below lane max - cut is below
-  // M - cut too) have their windows summed.
+  uint32_t mk[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
+  float wme = -INFINITY, wm32 = -INFINITY;   // this warp's maximum at step `lane`, and at step 32
+  // One sweep over the widths.  Per step the warp takes its maximum wm of
+  // all windows and ballots which lanes' 11-bin groups reach wm - cut; lane c
+  // keeps the ballots of step c.  After each 33-width block the warps'
+  // maxima give M[s, w] (one block barrier), and the flagged groups are
+  // screened against M - cut (a group within the cut of M is within the
+  // cut of wm <= M; a step whose wm is below M - cut has none).
   walk_widths(
       s, buf + x0, W, ll.a, [&](int bi, int nsteps) { return !__any_sync(kFullMask, ll.masked(bi * kR + nsteps)); },
       [&](int w, int c, auto full) {
         float g[3];
-        const float lm = lane_groups<decltype(full)::value>(s, ll.at(w), g);
-        kmax[(warp * kR + c) * 32 + lane] = lm;
-        const float lo = lm - cut;
-        kgrp[(warp * kR + c) * 32 + lane] =
-            static_cast<uint8_t>((g[0] >= lo ? 1u : 0u) | (g[1] >= lo ? 2u : 0u) | (g[2] >= lo ? 4u : 0u));
+        const float wm = warp_max(lane_groups<decltype(full)::value>(s, ll.at(w), g));
+        const float lo = wm - cut;
+        const uint32_t b0 = __ballot_sync(kFullMask, g[0] >= lo);
+        const uint32_t b1 = __ballot_sync(kFullMask, g[1] >= lo);
+        const uint32_t b2 = __ballot_sync(kFullMask, g[2] >= lo);
+        if (c == lane) {
+          mk[0][0] = b0;
+          mk[0][1] = b1;
+          mk[0][2] = b2;
+          wme = wm;
+        }
+        if (c == kR - 1) {
+          mk[1][0] = b0;
+          mk[1][1] = b1;
+          mk[1][2] = b2;
+          wm32 = wm;
+        }
       },
       [&](int bi, int nsteps) {
-        // M per width: each warp reduces its own lanes (lane c takes width c,
-        // skewed reads are conflict-free), then the warps' maxima are merged
+        const int p = bi & 1;
+        const float *wm_p = wmax + p * kRows;
+        if (lane < nsteps) wmax[p * kRows + warp * kR + lane] = wme;
+        if (lane == 0 && nsteps == kR) wmax[p * kRows + warp * kR + kR - 1] = wm32;
         __syncthreads();
-        for (int c = lane; c < nsteps; c += 32) {
+        if (bi > 0) emit_y(bi - 1, kR);
+        // M per width (each warp its own copy); this warp's sums start at 0
+        float *mr = mrow + p * kRows + warp * kR;
+        float *ls = lsbw + p * kRows + warp * kR;
+        if (lane < nsteps) {
           float m = -INFINITY;
-#pragma unroll 8
-          for (int l = 0; l < 32; ++l) m = fmaxf(m, kmax[(warp * kR + c) * 32 + ((l + c) & 31)]);
-          wmax[warp * kR + c] = m;
+          for (int v = 0; v < warps; ++v) m = fmaxf(m, wm_p[v * kR + lane]);
+          mr[lane] = m;
+          ls[lane] = 0.0f;
+          if (wme < m - cut) mk[0][0] = mk[0][1] = mk[0][2] = 0u;
+        } else {
+          mk[0][0] = mk[0][1] = mk[0][2] = 0u;
         }
-        __syncthreads();
-        for (int c = threadIdx.x; c < nsteps; c += blockDim.x) {
+        if (nsteps == kR) {
           float m = -INFINITY;
-          for (int v = 0; v < warps; ++v) m = fmaxf(m, wmax[v * kR + c]);
-          mblk[c] = m;
-          lsb[c] = 0.0f;
+          for (int v = 0; v < warps; ++v) m = fmaxf(m, wm_p[v * kR + kR - 1]);
+          if (lane == 0) {
+            mr[kR - 1] = m;
+            ls[kR - 1] = 0.0f;
+          }
+          if (lane != 0 || wm32 < m - cut) mk[1][0] = mk[1][1] = mk[1][2] = 0u;
+        } else {
+          mk[1][0] = mk[1][1] = mk[1][2] = 0u;
         }
-        __syncthreads();
-        // the block's events: groups of lanes within the cut of M (the list
-        // reuses the warp's lane maxima, all read first)
-        const float *km = kmax + warp * (kR * 32);
-        const uint8_t *kg = kgrp + warp * (kR * 32);
-        block_events(
-            sgl, warp, lane, bi * kR + 1, nsteps,
-            [&](int c, int l) { return (km[c * 32 + l] > mblk[c] - cut) ? static_cast<uint32_t>(kg[c * 32 + l]) : 0u; },
-            [&](int c) { return mblk[c] - cut; }, fh, fl, reinterpret_cast<int *>(kmax + warp * (kR * 32)),
-            [&](int c, int, int, float hi, float lo) {
-              atomicAdd(&lsb[c], expf(__fadd_rn(__fsub_rn(hi, mblk[c]), lo) * inv_tau));
-            });
-        __syncthreads();
-        // Y = M + tau log(sum) as a pair: the FP32 value and its exact
-        // rounding error (the backward's weights exp((S - Y) / tau) need Y to
-        // better than FP32 resolution: an error dY moves them all by dY / tau)
-        for (int c = threadIdx.x; c < nsteps; c += blockDim.x) {
-          float e;
-          const float yh = two_sum(mblk[c], tau * logf(lsb[c]), e);
-          const int64_t o = t.seg_g * static_cast<int64_t>(W) + bi * kR + c;
-          y[o] = yh;
-          ylo[o] = e;
-        }
+        __syncwarp();
+        block_events(sgl, warp, lane, bi * kR + 1, mk, [&](int c) { return mr[c] - cut; }, fh, fl,
+                     evl + warp * kEvCap, [&](int c, int, int, float hi, float lo) {
+                       atomicAdd(&ls[c], expf(__fadd_rn(__fsub_rn(hi, mr[c]), lo) * inv_tau));
+                     });
       });
+  __syncthreads();
+  const int nb = (W + kR - 1) / kR;
+  emit_y(nb - 1, W - (nb - 1) * kR);
 }
 
 __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
@@ -482,8 +503,8 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   float *trow = grow + W;                        // Y - cut, +inf where G = 0
   float *dd = trow + W;                          // d_len difference entries
   float *wsum = dd + d_len;                      // per-warp scan totals
-  uint8_t *kgrp = reinterpret_cast<uint8_t *>(wsum + 32);   // warps x 33 x 32 group masks
-  float *fh = reinterpret_cast<float *>(kgrp + kLseMaxWarps * kR * 32);   // prefix: high part, buf_len + 1
+  int *evl = reinterpret_cast<int *>(wsum + 32);   // warps x kEvCap event lists
+  float *fh = reinterpret_cast<float *>(evl + (blockDim.x >> 5) * kEvCap);   // prefix: high part, buf_len + 1
   __half *fl = reinterpret_cast<__half *>(fh + buf_len + 1);   // low part, buf_len + 1
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
@@ -505,30 +526,42 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   const LaneLim ll = lane_lim(t, x0);
   const SegLim sgl = seg_lim(t);
   float s[kR];
+  uint32_t mk[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
+  // Per step the warp ballots which lanes' 11-bin groups reach Y - cut (lane
+  // c keeps the ballots of step c); after each 33-width block the flagged
+  // groups' windows are weighted.  Y is known: no block barrier.
   walk_widths(
       s, lane_buf, W, ll.a, [&](int bi, int nsteps) { return !__any_sync(kFullMask, ll.masked(bi * kR + nsteps)); },
       [&](int w, int c, auto full) {
         float g[3];
         lane_groups<decltype(full)::value>(s, ll.at(w), g);
         const float thr = trow[w - 1];
-        const uint32_t m = (g[0] > thr ? 1u : 0u) | (g[1] > thr ? 2u : 0u) | (g[2] > thr ? 4u : 0u);
-        kgrp[(warp * kR + c) * 32 + lane] = static_cast<uint8_t>(m);
+        const uint32_t b0 = __ballot_sync(kFullMask, g[0] > thr);
+        const uint32_t b1 = __ballot_sync(kFullMask, g[1] > thr);
+        const uint32_t b2 = __ballot_sync(kFullMask, g[2] > thr);
+        if (c == lane) {
+          mk[0][0] = b0;
+          mk[0][1] = b1;
+          mk[0][2] = b2;
+        }
+        if (c == kR - 1) {
+          mk[1][0] = b0;
+          mk[1][1] = b1;
+          mk[1][2] = b2;
+        }
       },
       [&](int bi, int nsteps) {
-        __syncwarp();
-        // the block's events (the list reuses the warp's flags, all read first)
-        const uint8_t *kg = kgrp + warp * (kR * 32);
+        if (lane >= nsteps) mk[0][0] = mk[0][1] = mk[0][2] = 0u;
+        if (lane != 0 || nsteps != kR) mk[1][0] = mk[1][1] = mk[1][2] = 0u;
         const int wf = bi * kR + 1;
-        block_events(
-            sgl, warp, lane, wf, nsteps, [&](int c, int l) { return static_cast<uint32_t>(kg[c * 32 + l]); },
-            [&](int c) { return trow[wf + c - 1]; }, fh, fl, reinterpret_cast<int *>(kgrp + warp * (kR * 32)),
-            [&](int, int k, int w, float hi, float lo) {
-              // (S - Y) from the two pairs: hi - Y is exact (Sterbenz)
-              const float g =
-                  grow[w - 1] * expf(__fadd_rn(__fsub_rn(hi, yrow[w - 1]), __fsub_rn(lo, ylrow[w - 1])) * inv_tau);
-              atomicAdd(&dd[k], g);
-              atomicAdd(&dd[k + w], -g);
-            });
+        block_events(sgl, warp, lane, wf, mk, [&](int c) { return trow[wf + c - 1]; }, fh, fl,
+                     evl + warp * kEvCap, [&](int, int k, int w, float hi, float lo) {
+                       // (S - Y) from the two pairs: hi - Y is exact (Sterbenz)
+                       const float g = grow[w - 1] *
+                                       expf(__fadd_rn(__fsub_rn(hi, yrow[w - 1]), __fsub_rn(lo, ylrow[w - 1])) * inv_tau);
+                       atomicAdd(&dd[k], g);
+                       atomicAdd(&dd[k + w], -g);
+                     });
       });
   __syncthreads();
   // inclusive prefix sum of dd: thread t owns a contiguous chunk
@@ -821,8 +854,7 @@ int pulscan_lse_forward(pulscan_plan p, const float *d_x, float *d_spec, float *
   if (rc) return rc;
   const int warps = lse_warps(p);
   const int buf_len = lse_buf_len(p, warps);
-  const int smem = 128 + 4 * (buf_len + 128 + warps * kR * 32 + warps * kR * 8 +
-                              kLseMaxWarps * kR + (buf_len + 1)) + 2 * (buf_len + 1) + 16;
+  const int smem = 128 + 4 * (buf_len + 6 * kRows + warps * kEvCap + (buf_len + 1)) + 2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_forward_kernel, smem, g_lim_fwd);
   if (rc) return rc;
   lse_forward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
@@ -848,7 +880,7 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   int64_t max_n = 0;
   for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
   const int d_len = static_cast<int>(max_n + p->z_max + 1);
-  const int smem = 128 + 4 * (buf_len + 4 * p->z_max + d_len + 32 + kLseMaxWarps * kR * 8 + (buf_len + 1)) +
+  const int smem = 128 + 4 * (buf_len + 4 * p->z_max + d_len + 32 + warps * kEvCap + (buf_len + 1)) +
                    2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
   if (rc) return rc;

@@ -59,7 +59,7 @@ namespace ps {
 namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
-constexpr int kLseMaxWarps = 4;
+constexpr int kLseMaxWarps = 2;
 
 // s + e == a + b exactly (Knuth's two-sum; explicit roundings, no contraction).
 __device__ __forceinline__ float two_sum(float a, float b, float &e) {
@@ -69,20 +69,21 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
   return t;
 }
 
-// Exclusive prefix F[j] = sum_{i<j} buf[i] for j = 0..n as fh[j] + fl[j];
+// Exclusive prefix F[j] = sum_{i<j} P[i] for j = 0..n as fh[j] + fl[j],
+// built in place: fh[0..n) holds P on entry (fh has n + 1 entries).
 // fl (at most half an ulp of fh) is kept in FP16, whose 11-bit mantissa
 // leaves an error below 2^-12 ulp of F.
 // Each thread sums a contiguous chunk with two-sum, the chunk totals are
 // scanned in FP64 (wtot: one double per warp), then each chunk is re-walked
-// from its FP64 carry split into a float pair.  Ends with a barrier.
-__device__ void build_prefix(const float *__restrict__ buf, int n, float *__restrict__ fh, __half *__restrict__ fl,
-                             double *wtot) {
+// from its FP64 carry split into a float pair (every thread reads and
+// overwrites its own chunk only).  Ends with a barrier.
+__device__ void build_prefix(float *__restrict__ fh, int n, __half *__restrict__ fl, double *wtot) {
   const int nt = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int chunk = (n + nt - 1) / nt;
   const int a0 = min(n, static_cast<int>(threadIdx.x) * chunk), a1 = min(n, a0 + chunk);
   float h = 0.0f, l = 0.0f, e;
   for (int j = a0; j < a1; ++j) {
-    h = two_sum(h, buf[j], e);
+    h = two_sum(h, fh[j], e);
     l = __fadd_rn(l, e);
   }
   const double tot = static_cast<double>(h) + static_cast<double>(l);
@@ -100,10 +101,11 @@ __device__ void build_prefix(const float *__restrict__ buf, int n, float *__rest
   l = static_cast<float>(carry - static_cast<double>(h));
   // stored normalised (fast two-sum, |l| << |h|): |fl| <= half an ulp of fh
   for (int j = a0; j < a1; ++j) {
+    const float v = fh[j];
     const float hs = __fadd_rn(h, l);
     fh[j] = hs;
     fl[j] = __float2half_rn(__fsub_rn(l, __fsub_rn(hs, h)));
-    h = two_sum(h, buf[j], e);
+    h = two_sum(h, v, e);
     l = __fadd_rn(l, e);
   }
   if (threadIdx.x == nt - 1) {   // its chunk ends at n, or is empty with the full total as carry
@@ -127,55 +129,81 @@ __device__ __forceinline__ float window_sum2(const float *__restrict__ fh, const
   return d;
 }
 
-// Ring steps C0..C0+NC-1 with a per-step callback cb(c) after the adds.
-template <int C0, int NC, class F>
-__device__ __forceinline__ void ring_steps(float (&s)[kR], float (&b)[kR], const float *__restrict__ pb, F &&cb) {
-#pragma unroll
-  for (int cc = 0; cc < NC; ++cc) {
-    const int c = C0 + cc;
-    b[(c + kR - 1) % kR] = pb[c + kR - 1];
-#pragma unroll
-    for (int i = 0; i < kR; ++i) s[i] += b[(i + c) % kR];
-    cb(c);
-  }
+// A lane works on two 33-bin tiles at once, a = warp * kSpan + lane * 33 and
+// b = a + kTile, as packed pairs: one add.rn.f32x2 forms a window sum of
+// both (two FP32 adds, the same roundings as scalar adds).
+constexpr int kTile = 32 * kR;     // 1056 bins: the lanes' first tiles
+constexpr int kSpan = 2 * kTile;   // 2112 bins per warp
+constexpr int kSub = 11;           // ring steps unrolled at a time (kR = 3 kSub)
+
+__device__ __forceinline__ uint64_t pk2(float x, float y) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(x), "f"(y));
+  return d;
 }
 
-// Runs widths 1..W over the lane's 33 sums, calling cb(w, c, full) after each
-// width's adds: full 33-width blocks use the ring, the last partial block
-// reads the window straight from shared memory.  full is a compile-time
-// flag: full_block(bi, nsteps) (warp-uniform) says whether every lane of the
-// warp has all its windows valid through block bi, and such blocks run an
-// instantiation of the 33 steps with no per-step branch (a branch in every
-// step splits the unrolled body, and the steps could no longer overlap).
-// block_end(bi, nsteps) is called after every block.
-// Start bins i >= n_valid (past the segment's end) start at -inf and stay
-// there, so they never win a maximum and need no mask.
+__device__ __forceinline__ void upk2(uint64_t d, float &x, float &y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(d));
+}
+
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Runs widths 1..W over the lane's two tiles, calling cb(w, c, sv, full)
+// per width: sv(i) gives the pair (S_w[xa + i], S_w[xb + i]) of window sums,
+// formed as F[x + i + w] - F[x + i] from the prefix's high parts.  These sums
+// only pick windows (the picked ones are recomputed exactly): their error,
+// about an ulp of F, is far below any cut.  The lane keeps -F[x + i]
+// (-inf for start bins past the segment's end, nva / nvb valid, so those
+// never win a maximum) and a ring of F[x + i + w] that advances one bin per
+// width (one shared load per tile and width).  Full 33-width blocks run the
+// ring unrolled with no per-step branch; full_block(bi, nsteps)
+// (warp-uniform) says whether every window of the warp is valid through
+// block bi -- cb gets a compile-time flag for it.  Other blocks (the
+// spectrum's end, the last partial block) read F straight from shared
+// memory in a rolled loop.  block_end(bi, nsteps) follows every block.
 template <class Full, class F, class G>
-__device__ __forceinline__ void walk_widths(float (&s)[kR], const float *__restrict__ lane_buf, int W, int n_valid,
-                                            Full &&full_block, F &&cb, G &&block_end) {
-  float b[kR];
+__device__ __forceinline__ void walk_pairs(const float *__restrict__ fh, int xa, int xb, int nva, int nvb, int W,
+                                           Full &&full_block, F &&cb, G &&block_end) {
+  uint64_t nb2[kR], r2[kR];
 #pragma unroll
-  for (int i = 0; i < kR; ++i) s[i] = (i < n_valid) ? 0.0f : -INFINITY;
+  for (int i = 0; i < kR; ++i) nb2[i] = pk2(i < nva ? -fh[xa + i] : -INFINITY, i < nvb ? -fh[xb + i] : -INFINITY);
+  auto load_ring = [&](int wf) {
 #pragma unroll
-  for (int j = 0; j < kR - 1; ++j) b[j] = lane_buf[j];
-  b[kR - 1] = 0.0f;
-  const int nb = (W + kR - 1) / kR;
-  for (int bi = 0; bi < nb; ++bi) {
-    const float *pb = lane_buf + bi * kR;
+    for (int j = 0; j < kR - 1; ++j) r2[j] = pk2(fh[xa + wf + j], fh[xb + wf + j]);
+  };
+  load_ring(1);
+  const int nblk = (W + kR - 1) / kR;
+  for (int bi = 0; bi < nblk; ++bi) {
     const int wf = bi * kR + 1;
     const int nsteps = min(kR, W - bi * kR);
-    if (nsteps == kR) {
-      if (full_block(bi, nsteps))
-        ring_steps<0, kR>(s, b, pb, [&](int c) { cb(wf + c, c, std::true_type{}); });
-      else
-        ring_steps<0, kR>(s, b, pb, [&](int c) { cb(wf + c, c, std::false_type{}); });
+    if (nsteps == kR && full_block(bi, nsteps)) {
+      // three rolled sub-blocks of 11 unrolled steps (a third of the code of
+      // 33 unrolled steps, for the instruction cache), each ending with the
+      // ring rotated by 11 so that the next starts from the same layout
+#pragma unroll 1
+      for (int sb = 0; sb < kR; sb += kSub) {
+        const int ws = wf + sb;
+#pragma unroll
+        for (int cc = 0; cc < kSub; ++cc) {
+          r2[(cc + kR - 1) % kR] = pk2(fh[xa + ws + cc + kR - 1], fh[xb + ws + cc + kR - 1]);
+          cb(ws + cc, sb + cc, [&](int i) { return add2(r2[(i + cc) % kR], nb2[i]); }, std::true_type{});
+        }
+        uint64_t rot[kR];
+#pragma unroll
+        for (int i = 0; i < kR; ++i) rot[i] = r2[(i + kSub) % kR];
+#pragma unroll
+        for (int i = 0; i < kR; ++i) r2[i] = rot[i];
+      }
     } else {
       for (int c = 0; c < nsteps; ++c) {
-        const float *pw = lane_buf + (wf + c - 1);
-#pragma unroll
-        for (int i = 0; i < kR; ++i) s[i] += pw[i];
-        cb(wf + c, c, std::false_type{});
+        const int w = wf + c;
+        cb(w, c, [&](int i) { return add2(pk2(fh[xa + i + w], fh[xb + i + w]), nb2[i]); }, std::false_type{});
       }
+      if (bi + 1 < nblk) load_ring(wf + kR);
     }
     block_end(bi, nsteps);
   }
@@ -232,9 +260,9 @@ __device__ __forceinline__ SegTile seg_tile(const SeriesDev *__restrict__ series
 
 // Valid windows of the lane starting at local bin x at width w: start inside
 // the segment, window inside the spectrum:  lim(w) = clamp(min(a, b - w), 0, 33)
-// with a = nb - x and b = M - (b0 + x) + 1 fixed per lane.  The running sums
-// of bins past a start at -inf (walk_widths), so only the spectrum's end needs
-// a mask: `masked(w)` says whether it cuts one of the lane's windows at width w.
+// with a = nb - x and b = M - (b0 + x) + 1 fixed per tile.  The sums of
+// bins past a start at -inf (walk_pairs), so only the spectrum's end needs a
+// mask: `masked(w)` says whether it cuts one of the tile's windows at width w.
 struct LaneLim {
   int a, b;
   __device__ __forceinline__ int at(int w) const { return max(0, min(kR, min(a, b - w))); }
@@ -252,28 +280,32 @@ __device__ __forceinline__ float max3(float a, float b, float c) {
   return r;
 }
 
-// Maxima of the lane's three 11-bin groups (windows i < lim only; -inf where
-// none) and their maximum.  kFull: all 33 windows valid (lim ignored).
+// Maxima of the lane's six 11-bin groups, g[j] of tile a and g[3 + j] of
+// tile b (windows i < lim only; -inf where none), and their maximum.
+// kFull: every window valid (the limits are ignored).
 constexpr int kGrp = 11;
-template <bool kFull>
-__device__ __forceinline__ float lane_groups(const float (&s)[kR], int lim, float (&g)[3]) {
-  if (kFull) {
+template <bool kFull, class S>
+__device__ __forceinline__ float lane_groups2(S &&sv, int lima, int limb, float (&g)[6]) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int o = kGrp * j;
-      g[j] = max3(max3(max3(s[o], s[o + 1], s[o + 2]), max3(s[o + 3], s[o + 4], s[o + 5]),
-                       max3(s[o + 6], s[o + 7], s[o + 8])), s[o + 9], s[o + 10]);
-    }
-  } else {
+  for (int j = 0; j < 3; ++j) {
+    float a[kGrp], b[kGrp];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float m = -INFINITY;
+    for (int i = 0; i < kGrp; ++i) upk2(sv(kGrp * j + i), a[i], b[i]);
+    if (kFull) {
+      g[j] = max3(max3(max3(a[0], a[1], a[2]), max3(a[3], a[4], a[5]), max3(a[6], a[7], a[8])), a[9], a[10]);
+      g[3 + j] = max3(max3(max3(b[0], b[1], b[2]), max3(b[3], b[4], b[5]), max3(b[6], b[7], b[8])), b[9], b[10]);
+    } else {
+      float ma = -INFINITY, mb = -INFINITY;
 #pragma unroll
-      for (int i = 0; i < kGrp; ++i) m = fmaxf(m, (kGrp * j + i < lim) ? s[kGrp * j + i] : -INFINITY);
-      g[j] = m;
+      for (int i = 0; i < kGrp; ++i) {
+        ma = fmaxf(ma, (kGrp * j + i < lima) ? a[i] : -INFINITY);
+        mb = fmaxf(mb, (kGrp * j + i < limb) ? b[i] : -INFINITY);
+      }
+      g[j] = ma;
+      g[3 + j] = mb;
     }
   }
-  return max3(g[0], g[1], g[2]);
+  return fmaxf(max3(g[0], g[1], g[2]), max3(g[3], g[4], g[5]));
 }
 
 // The window limits of a segment in 32-bit form: start bin x of the
@@ -290,7 +322,8 @@ __device__ __forceinline__ SegLim seg_lim(const SegTile &t) {
 
 // All events of one 33-width block at once: (step c, lane l, group j)
 // triples, c | l << 6 | j << 11, for every 11-bin group whose bit is set in
-// the step masks mk (ballots: bit l of mk[r][j] is group j of lane l; this
+// the step masks mk (ballots: bit l of mk[r][j] is group j of lane l, j < 3
+// in tile a and j - 3 in tile b; this
 // lane holds those of step `lane` in mk[0] and lane 0 also those of step 32
 // in mk[1], zero where the lane owns no step); then their windows (11 per
 // event) are worked off by the whole warp, two per lane per trip
@@ -302,11 +335,12 @@ __device__ __forceinline__ SegLim seg_lim(const SegTile &t) {
 constexpr int kEvCap = 128;
 
 template <class Thr, class F>
-__device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lane, int wf, const uint32_t (&mk)[2][3],
+__device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lane, int wf, const uint32_t (&mk)[2][6],
                                              Thr thr, const float *__restrict__ fh, const __half *__restrict__ fl,
                                              int *evl, F &&f) {
-  const uint32_t cnt = __popc(mk[0][0]) + __popc(mk[0][1]) + __popc(mk[0][2]) + __popc(mk[1][0]) +
-                       __popc(mk[1][1]) + __popc(mk[1][2]);
+  uint32_t cnt = 0u;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) cnt += __popc(mk[0][j]) + __popc(mk[1][j]);
   uint32_t incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -322,7 +356,7 @@ __device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lan
     for (int r = 0; r < 2; ++r) {
       const int c = r ? kR - 1 : lane;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
+      for (int j = 0; j < 6; ++j) {
         for (uint32_t mm = mk[r][j]; mm != 0u; mm &= mm - 1u, ++pos)
           if (pos >= base && pos < base + kEvCap) evl[pos - base] = c | ((__ffs(static_cast<int>(mm)) - 1) << 6) | (j << 11);
       }
@@ -343,8 +377,8 @@ __device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lan
         cc[u] = ev & 63;
         const int l = (ev >> 6) & 31, jg = ev >> 11;
         ww[u] = wf + cc[u];
-        const int x = warp * (32 * kR) + l * kR;
-        const int b = kGrp * jg + i;   // bin of the lane
+        const int x = warp * kSpan + (jg >= 3 ? kTile : 0) + l * kR;   // the tile's first bin
+        const int b = kGrp * (jg >= 3 ? jg - 3 : jg) + i;              // bin in the tile
         ok[u] = ok[u] && b < sl.at(x, ww[u]);
         kk[u] = x + b;
         th[u] = thr(cc[u]);
@@ -375,7 +409,19 @@ __device__ __forceinline__ float warp_max(float v) {
 // Per-warp rows of 33 widths, double-buffered by block parity.
 constexpr int kRows = kLseMaxWarps * kR;
 
-__global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
+// Per-step ballots of the six group flags g[j] >= lo (or > lo), kept by the
+// lane that owns the step (lane c for step c, every lane for step 32).
+template <bool kStrict>
+__device__ __forceinline__ void flag_groups(const float (&g)[6], float lo, int c, int lane, uint32_t (&mk)[2][6]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const uint32_t bal = __ballot_sync(kFullMask, kStrict ? g[j] > lo : g[j] >= lo);
+    if (c == lane) mk[0][j] = bal;
+    if (c == kR - 1) mk[1][j] = bal;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kLseMaxWarps, 6) lse_forward_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
     int n_series, int W, int seg_len, float tau, float cut, float *__restrict__ y, float *__restrict__ ylo,
     uint32_t *__restrict__ counters, int buf_len) {
@@ -383,20 +429,19 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   double *wtot = reinterpret_cast<double *>(smem_raw + 32);
   uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
-  float *buf = reinterpret_cast<float *>(smem_raw + 128);
-  float *wmax = buf + buf_len;          // [2][warps][33]: each warp's maximum per width
+  float *fh = reinterpret_cast<float *>(smem_raw + 128);   // P, then the prefix's high part: buf_len + 1
+  float *wmax = fh + buf_len + 1;       // [2][warps][33]: each warp's maximum per width
   float *mrow = wmax + 2 * kRows;       // [2][warps][33]: M per width, a copy per warp
   float *lsbw = mrow + 2 * kRows;       // [2][warps][33]: each warp's sums of exp
   const int warps = blockDim.x >> 5;
-  int *evl = reinterpret_cast<int *>(lsbw + 2 * kRows);   // warps x kEvCap event lists
-  float *fh = reinterpret_cast<float *>(evl + warps * kEvCap);   // prefix: high part, buf_len + 1
-  __half *fl = reinterpret_cast<__half *>(fh + buf_len + 1);     // low part, buf_len + 1
-  const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
+  int *evl = reinterpret_cast<int *>(lsbw + 2 * kRows);           // warps x kEvCap event lists
+  __half *fl = reinterpret_cast<__half *>(evl + warps * kEvCap);   // the prefix's low part: buf_len + 1
+  const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, fh);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
-  build_prefix(buf, buf_len, fh, fl, wtot);
+  build_prefix(fh, buf_len, fl, wtot);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int x0 = warp * (32 * kR) + lane * kR;
-  const LaneLim ll = lane_lim(t, x0);
+  const int xa = warp * kSpan + lane * kR, xb = xa + kTile;
+  const LaneLim la = lane_lim(t, xa), lb = lane_lim(t, xb);
   const SegLim sgl = seg_lim(t);
   const float inv_tau = 1.0f / tau;
   // Y = M + tau log(sum) of block bj's widths as a pair: the FP32 value and
@@ -415,36 +460,28 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
       ylo[o] = e;
     }
   };
-  float s[kR];
-  uint32_t mk[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
+  uint32_t mk[2][6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) mk[0][j] = mk[1][j] = 0u;
   float wme = -INFINITY, wm32 = -INFINITY;   // this warp's maximum at step `lane`, and at step 32
   // One sweep over the widths.  Per step the warp takes its maximum wm of
-  // all windows and ballots which lanes' 11-bin groups reach wm - cut; lane c
-  // keeps the ballots of step c.  After each 33-width block the warps'
-  // maxima give M[s, w] (one block barrier), and the flagged groups are
-  // screened against M - cut (a group within the cut of M is within the
-  // cut of wm <= M; a step whose wm is below M - cut has none).
-  walk_widths(
-      s, buf + x0, W, ll.a, [&](int bi, int nsteps) { return !__any_sync(kFullMask, ll.masked(bi * kR + nsteps)); },
-      [&](int w, int c, auto full) {
-        float g[3];
-        const float wm = warp_max(lane_groups<decltype(full)::value>(s, ll.at(w), g));
-        const float lo = wm - cut;
-        const uint32_t b0 = __ballot_sync(kFullMask, g[0] >= lo);
-        const uint32_t b1 = __ballot_sync(kFullMask, g[1] >= lo);
-        const uint32_t b2 = __ballot_sync(kFullMask, g[2] >= lo);
-        if (c == lane) {
-          mk[0][0] = b0;
-          mk[0][1] = b1;
-          mk[0][2] = b2;
-          wme = wm;
-        }
-        if (c == kR - 1) {
-          mk[1][0] = b0;
-          mk[1][1] = b1;
-          mk[1][2] = b2;
-          wm32 = wm;
-        }
+  // all windows and ballots which lanes' 11-bin groups reach wm - cut.
+  // After each 33-width block the warps' maxima give M[s, w] (one block
+  // barrier), and the flagged groups are screened against M - cut (a group
+  // within the cut of M is within the cut of wm <= M; a step whose wm is
+  // below M - cut has none).
+  walk_pairs(
+      fh, xa, xb, la.a, lb.a, W,
+      [&](int bi, int nsteps) {
+        const int w = bi * kR + nsteps;
+        return !__any_sync(kFullMask, la.masked(w) || lb.masked(w));
+      },
+      [&](int w, int c, auto sv, auto full) {
+        float g[6];
+        const float wm = warp_max(lane_groups2<decltype(full)::value>(sv, la.at(w), lb.at(w), g));
+        flag_groups<false>(g, wm - cut, c, lane, mk);
+        if (c == lane) wme = wm;
+        if (c == kR - 1) wm32 = wm;
       },
       [&](int bi, int nsteps) {
         const int p = bi & 1;
@@ -456,15 +493,15 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
         // M per width (each warp its own copy); this warp's sums start at 0
         float *mr = mrow + p * kRows + warp * kR;
         float *ls = lsbw + p * kRows + warp * kR;
+        bool drop = true;
         if (lane < nsteps) {
           float m = -INFINITY;
           for (int v = 0; v < warps; ++v) m = fmaxf(m, wm_p[v * kR + lane]);
           mr[lane] = m;
           ls[lane] = 0.0f;
-          if (wme < m - cut) mk[0][0] = mk[0][1] = mk[0][2] = 0u;
-        } else {
-          mk[0][0] = mk[0][1] = mk[0][2] = 0u;
+          drop = wme < m - cut;
         }
+        bool drop32 = true;
         if (nsteps == kR) {
           float m = -INFINITY;
           for (int v = 0; v < warps; ++v) m = fmaxf(m, wm_p[v * kR + kR - 1]);
@@ -472,9 +509,12 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
             mr[kR - 1] = m;
             ls[kR - 1] = 0.0f;
           }
-          if (lane != 0 || wm32 < m - cut) mk[1][0] = mk[1][1] = mk[1][2] = 0u;
-        } else {
-          mk[1][0] = mk[1][1] = mk[1][2] = 0u;
+          drop32 = lane != 0 || wm32 < m - cut;
+        }
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          if (drop) mk[0][j] = 0u;
+          if (drop32) mk[1][j] = 0u;
         }
         __syncwarp();
         block_events(sgl, warp, lane, bi * kR + 1, mk, [&](int c) { return mr[c] - cut; }, fh, fl,
@@ -487,7 +527,7 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_forward_kernel(
   emit_y(nb - 1, W - (nb - 1) * kR);
 }
 
-__global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
+__global__ void __launch_bounds__(32 * kLseMaxWarps, 6) lse_backward_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
     int n_series, int W, int seg_len, float tau, float cut, const float *__restrict__ y,
     const float *__restrict__ ylo, const float *__restrict__ gy, float *__restrict__ dp, float *__restrict__ tail,
@@ -496,72 +536,72 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps) lse_backward_kernel(
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   double *wtot = reinterpret_cast<double *>(smem_raw + 32);
   uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
-  float *buf = reinterpret_cast<float *>(smem_raw + 128);
-  float *yrow = buf + buf_len;
-  float *ylrow = yrow + W;                       // Y's low parts
-  float *grow = ylrow + W;
-  float *trow = grow + W;                        // Y - cut, +inf where G = 0
-  float *dd = trow + W;                          // d_len difference entries
+  float *fh = reinterpret_cast<float *>(smem_raw + 128);   // P, then the prefix's high part: buf_len + 1
+  float *rows = fh + buf_len + 1;                // warps x [Y, Y low part, G, Y - cut] x 33 widths of a block
+  float *dd = rows + kLseMaxWarps * 4 * kR;      // d_len difference entries
   float *wsum = dd + d_len;                      // per-warp scan totals
-  int *evl = reinterpret_cast<int *>(wsum + 32);   // warps x kEvCap event lists
-  float *fh = reinterpret_cast<float *>(evl + (blockDim.x >> 5) * kEvCap);   // prefix: high part, buf_len + 1
-  __half *fl = reinterpret_cast<__half *>(fh + buf_len + 1);   // low part, buf_len + 1
-  const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, buf);
+  int *evl = reinterpret_cast<int *>(wsum + 32);                                  // warps x kEvCap event lists
+  __half *fl = reinterpret_cast<__half *>(evl + (blockDim.x >> 5) * kEvCap);     // prefix: low part, buf_len + 1
+  const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, fh);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
-  build_prefix(buf, buf_len, fh, fl, wtot);
-  for (int j = threadIdx.x; j < W; j += blockDim.x) {
-    const int64_t o = t.seg_g * static_cast<int64_t>(W) + j;
-    const float gj = gy[o];
-    yrow[j] = y[o];
-    ylrow[j] = ylo[o];
-    grow[j] = gj;
-    trow[j] = (gj != 0.0f) ? y[o] - cut : INFINITY;
-  }
+  build_prefix(fh, buf_len, fl, wtot);
   for (int j = threadIdx.x; j < d_len; j += blockDim.x) dd[j] = 0.0f;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int x0 = warp * (32 * kR) + lane * kR;
-  const float *lane_buf = buf + x0;
+  // this warp's row of the block's widths: Y, its low part, G and the
+  // threshold Y - cut (+inf where G = 0: no window of that width counts)
+  float *yrow = rows + warp * 4 * kR, *ylrow = yrow + kR, *grow = ylrow + kR, *trow = grow + kR;
+  auto load_rows = [&](int bi) {
+    const int nst = min(kR, W - bi * kR);
+    for (int c = lane; c < nst; c += 32) {
+      const int64_t o = t.seg_g * static_cast<int64_t>(W) + bi * kR + c;
+      const float yv = y[o], gv = gy[o];
+      yrow[c] = yv;
+      ylrow[c] = ylo[o];
+      grow[c] = gv;
+      trow[c] = (gv != 0.0f) ? yv - cut : INFINITY;
+    }
+    __syncwarp();
+  };
+  load_rows(0);
+  const int xa = warp * kSpan + lane * kR, xb = xa + kTile;
   const float inv_tau = 1.0f / tau;
-  const LaneLim ll = lane_lim(t, x0);
+  const LaneLim la = lane_lim(t, xa), lb = lane_lim(t, xb);
   const SegLim sgl = seg_lim(t);
-  float s[kR];
-  uint32_t mk[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
-  // Per step the warp ballots which lanes' 11-bin groups reach Y - cut (lane
-  // c keeps the ballots of step c); after each 33-width block the flagged
-  // groups' windows are weighted.  Y is known: no block barrier.
-  walk_widths(
-      s, lane_buf, W, ll.a, [&](int bi, int nsteps) { return !__any_sync(kFullMask, ll.masked(bi * kR + nsteps)); },
-      [&](int w, int c, auto full) {
-        float g[3];
-        lane_groups<decltype(full)::value>(s, ll.at(w), g);
-        const float thr = trow[w - 1];
-        const uint32_t b0 = __ballot_sync(kFullMask, g[0] > thr);
-        const uint32_t b1 = __ballot_sync(kFullMask, g[1] > thr);
-        const uint32_t b2 = __ballot_sync(kFullMask, g[2] > thr);
-        if (c == lane) {
-          mk[0][0] = b0;
-          mk[0][1] = b1;
-          mk[0][2] = b2;
-        }
-        if (c == kR - 1) {
-          mk[1][0] = b0;
-          mk[1][1] = b1;
-          mk[1][2] = b2;
-        }
+  uint32_t mk[2][6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) mk[0][j] = mk[1][j] = 0u;
+  // Per step the warp ballots which lanes' 11-bin groups reach Y - cut;
+  // after each 33-width block the flagged groups' windows are weighted.  Y
+  // is known: no block barrier.
+  walk_pairs(
+      fh, xa, xb, la.a, lb.a, W,
+      [&](int bi, int nsteps) {
+        const int w = bi * kR + nsteps;
+        return !__any_sync(kFullMask, la.masked(w) || lb.masked(w));
+      },
+      [&](int w, int c, auto sv, auto full) {
+        float g[6];
+        lane_groups2<decltype(full)::value>(sv, la.at(w), lb.at(w), g);
+        flag_groups<true>(g, trow[c], c, lane, mk);
       },
       [&](int bi, int nsteps) {
-        if (lane >= nsteps) mk[0][0] = mk[0][1] = mk[0][2] = 0u;
-        if (lane != 0 || nsteps != kR) mk[1][0] = mk[1][1] = mk[1][2] = 0u;
+        const bool drop = lane >= nsteps, drop32 = lane != 0 || nsteps != kR;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          if (drop) mk[0][j] = 0u;
+          if (drop32) mk[1][j] = 0u;
+        }
         const int wf = bi * kR + 1;
-        block_events(sgl, warp, lane, wf, mk, [&](int c) { return trow[wf + c - 1]; }, fh, fl,
-                     evl + warp * kEvCap, [&](int, int k, int w, float hi, float lo) {
+        block_events(sgl, warp, lane, wf, mk, [&](int c) { return trow[c]; }, fh, fl, evl + warp * kEvCap,
+                     [&](int c, int k, int w, float hi, float lo) {
                        // (S - Y) from the two pairs: hi - Y is exact (Sterbenz)
-                       const float g = grow[w - 1] *
-                                       expf(__fadd_rn(__fsub_rn(hi, yrow[w - 1]), __fsub_rn(lo, ylrow[w - 1])) * inv_tau);
+                       const float g =
+                           grow[c] * expf(__fadd_rn(__fsub_rn(hi, yrow[c]), __fsub_rn(lo, ylrow[c])) * inv_tau);
                        atomicAdd(&dd[k], g);
                        atomicAdd(&dd[k + w], -g);
                      });
+        if (bi + 1 < (W + kR - 1) / kR) load_rows(bi + 1);
       });
   __syncthreads();
   // inclusive prefix sum of dd: thread t owns a contiguous chunk
@@ -778,12 +818,12 @@ __global__ void amp_grad_kernel(const float *__restrict__ gx, const float *__res
 int lse_warps(pulscan_plan p) {
   int64_t max_n = 0;
   for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
-  return static_cast<int>((max_n + 32 * kR - 1) / (32 * kR));
+  return static_cast<int>((max_n + kSpan - 1) / kSpan);
 }
 
 int lse_buf_len(pulscan_plan p, int warps) {
   const int nb = (p->z_max + kR - 1) / kR;
-  return ((32 * kR * warps + nb * kR + 3 * kR) + 3) & ~3;
+  return ((kSpan * warps + nb * kR + 3 * kR) + 3) & ~3;
 }
 
 SmemLimit g_lim_fwd, g_lim_bwd;
@@ -854,7 +894,7 @@ int pulscan_lse_forward(pulscan_plan p, const float *d_x, float *d_spec, float *
   if (rc) return rc;
   const int warps = lse_warps(p);
   const int buf_len = lse_buf_len(p, warps);
-  const int smem = 128 + 4 * (buf_len + 6 * kRows + warps * kEvCap + (buf_len + 1)) + 2 * (buf_len + 1) + 16;
+  const int smem = 128 + 4 * (buf_len + 1 + 6 * kRows + warps * kEvCap) + 2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_forward_kernel, smem, g_lim_fwd);
   if (rc) return rc;
   lse_forward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
@@ -880,7 +920,7 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   int64_t max_n = 0;
   for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
   const int d_len = static_cast<int>(max_n + p->z_max + 1);
-  const int smem = 128 + 4 * (buf_len + 4 * p->z_max + d_len + 32 + warps * kEvCap + (buf_len + 1)) +
+  const int smem = 128 + 4 * (buf_len + 1 + kLseMaxWarps * 4 * kR + d_len + 32 + warps * kEvCap) +
                    2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
   if (rc) return rc;

@@ -326,8 +326,7 @@ __device__ __forceinline__ SegLim seg_lim(const SegTile &t) {
 // in tile a and j - 3 in tile b; this
 // lane holds those of step `lane` in mk[0] and lane 0 also those of step 32
 // in mk[1], zero where the lane owns no step); then their windows (11 per
-// event) are worked off by the whole warp, two per lane per trip
-// (independent chains of shared loads), in rounds of at most kEvCap events.
+// event) are worked off a lane per event, in rounds of at most kEvCap events.
 // Collecting a block's events first gives the window work the whole
 // block's parallelism instead of one width's.  evl: the warp's list
 // (kEvCap entries).  f(c, k, w, hi, lo) is called for every window whose
@@ -362,37 +361,35 @@ __device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lan
       }
     }
     __syncwarp();
-    const int total = kGrp * min(kEvCap, n_ev - base);
-    for (int q0 = lane; q0 < total; q0 += 64) {
-      float hb[2], ha[2], th[2];
-      int kk[2], ww[2], cc[2];
-      bool ok[2];
+    // a lane per event: its 11 windows are screened with the prefix's high
+    // parts alone (independent loads; within 1.5 ulp of F, margin 4 ulp of
+    // F[b]), then the few that pass are summed exactly
+    const int n_round = min(kEvCap, n_ev - base);
+    for (int e = lane; e < n_round; e += 32) {
+      const int ev = evl[e];
+      const int c = ev & 63, l = (ev >> 6) & 31, jg = ev >> 11;
+      const int w = wf + c;
+      const int x = warp * kSpan + (jg >= 3 ? kTile : 0) + l * kR;   // the tile's first bin
+      const int b0 = kGrp * (jg >= 3 ? jg - 3 : jg);                  // the group's first bin in the tile
+      const int k0 = x + b0;
+      const int lim = sl.at(x, w) - b0;                               // valid windows: i < lim
+      const float th = thr(c);
+      float ha[kGrp], hb[kGrp];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int q = q0 + 32 * u;
-        ok[u] = q < total;
-        const int e = ok[u] ? q / kGrp : 0;
-        const int i = q - kGrp * e;
-        const int ev = evl[e];
-        cc[u] = ev & 63;
-        const int l = (ev >> 6) & 31, jg = ev >> 11;
-        ww[u] = wf + cc[u];
-        const int x = warp * kSpan + (jg >= 3 ? kTile : 0) + l * kR;   // the tile's first bin
-        const int b = kGrp * (jg >= 3 ? jg - 3 : jg) + i;              // bin in the tile
-        ok[u] = ok[u] && b < sl.at(x, ww[u]);
-        kk[u] = x + b;
-        th[u] = thr(cc[u]);
-        hb[u] = ok[u] ? fh[kk[u] + ww[u]] : 0.0f;
-        ha[u] = ok[u] ? fh[kk[u]] : 0.0f;
+      for (int i = 0; i < kGrp; ++i) {
+        ha[i] = fh[k0 + i];
+        hb[i] = fh[k0 + w + i];
       }
+      uint32_t hot = 0u;
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        // fh alone is within 1.5 ulp of F: screen first
-        if (ok[u] && hb[u] - ha[u] > th[u] - 4.8e-7f * fabsf(hb[u])) {
-          float lo;
-          const float hi = window_sum2(fh, fl, kk[u], kk[u] + ww[u], lo);
-          if (__fadd_rn(__fsub_rn(hi, th[u]), lo) > 0.0f) f(cc[u], kk[u], ww[u], hi, lo);
-        }
+      for (int i = 0; i < kGrp; ++i)
+        hot |= (i < lim && hb[i] - ha[i] > th - 4.8e-7f * fabsf(hb[i])) ? (1u << i) : 0u;
+      while (hot != 0u) {
+        const int k = k0 + __ffs(static_cast<int>(hot)) - 1;
+        hot &= hot - 1u;
+        float lo;
+        const float hi = window_sum2(fh, fl, k, k + w, lo);
+        if (__fadd_rn(__fsub_rn(hi, th), lo) > 0.0f) f(c, k, w, hi, lo);
       }
     }
   }

@@ -9,29 +9,31 @@
 // MAD normalisation of Eq. 8 (almost-everywhere derivatives at the selected
 // order statistics) and the real FFT, to the time series.
 //
-// Kernels (one CTA per segment; lanes own 33 bins with register running sums
-// as in the search):
-// * lse_forward_kernel: pass 1 finds M[s, w] = max S_w (per step a lane max
-//   into shared memory, merged per width once per 33-width block); pass 2
-//   re-runs the sums and exponentiates only windows within tau * ln 2^24 of
-//   M -- every other term weighs < 2^-24 of the largest, and at most 2L of
-//   them change Y by < tau 2L 2^-24 -- so exp work is rare;
-// * lse_backward_kernel: re-runs the sums; each window within
-//   tau * ln 2^24 of Y gets weight g = G exp((S - Y) / tau), entered as a
-//   difference pair D[k] += g, D[k + w] -= g in shared memory; one block
-//   prefix sum of D gives dL/dP over the segment and a (W - 1)-bin tail that
-//   spills into the next segment (no global atomics);
-// * the register ring only flags, per width, which 11-bin groups of which
-//   lanes hold a window within the cut (three group maxima per step); the
-//   flagged (group, width) events are worked off after each 33-width block
-//   by the whole warp, a lane per window.  Keeping the exp / scatter
-//   code out of the 33 unrolled ring steps keeps the loop body small enough
-//   for the instruction cache;
-// * the running FP32 sums pick windows only: an exponent (S - M) / tau
-//   amplifies an absolute error in S by 1 / tau, and a sequential FP32 sum of
-//   w terms of size S carries up to ~ w * 2^-24 * S.  Each picked window's S
-//   is recomputed as F[k + w] - F[k] from a per-segment exclusive prefix sum
-//   F held in shared memory as an unevaluated pair of floats (hi + lo, built
+// Kernels (one CTA per segment, one warp per 2112 bins: each lane holds two
+// 33-bin tiles as packed pairs and sweeps widths 1..W as in the search):
+// * lse_forward_kernel: per width the warp takes the maximum of its windows
+//   (one redux.sync), per 33-width block the warps' maxima give
+//   M[s, w] = max S_w; only windows within cut = tau * ln 2^24 of M are
+//   exponentiated -- every other term weighs < 2^-24 of the largest, and at
+//   most 2L of them change Y by < tau 2L 2^-24 -- so exp work is rare;
+// * lse_backward_kernel: the same sweep; each window within the cut of Y
+//   gets weight g = G exp((S - Y) / tau), entered as a difference pair
+//   D[k] += g, D[k + w] -= g (reductions into the segment's own dL/dP and
+//   tail slots, which stay in L2); after the sweep one block prefix sum of D
+//   gives dL/dP over the segment and a (W - 1)-bin tail that spills into the
+//   next segment;
+// * the sweep only flags, per width, which 11-bin groups of which lanes
+//   hold a window within the cut (six group maxima per lane and step,
+//   ballots kept by the lane that owns the step); the flagged (group, width)
+//   events of a 33-width block are worked off after it, a lane per event.
+//   Keeping the exp / scatter code out of the unrolled ring steps keeps the
+//   loop body small enough for the instruction cache;
+// * the sweep's FP32 window sums (differences of the prefix's high parts)
+//   pick windows only: an exponent (S - M) / tau amplifies an absolute
+//   error in S by 1 / tau, and such a sum carries about an ulp of F.  Each
+//   picked window's S is recomputed as F[k + w] - F[k] from the per-segment
+//   exclusive prefix sum F held in shared memory as an unevaluated pair of
+//   floats (hi + lo, built
 //   with error-free additions, carried between threads in FP64) and kept as
 //   a pair: even one rounding of S (half an ulp, 2.4e-4 at S = 4096) would
 //   move a weight by 2.4e-3 at tau = 0.1.  S - M is taken as (hi - M) + lo,
@@ -528,22 +530,29 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps, 6) lse_backward_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off,
     int n_series, int W, int seg_len, float tau, float cut, const float *__restrict__ y,
     const float *__restrict__ ylo, const float *__restrict__ gy, float *__restrict__ dp, float *__restrict__ tail,
-    uint32_t *__restrict__ counters, int buf_len, int d_len) {
+    uint32_t *__restrict__ counters, int buf_len) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   double *wtot = reinterpret_cast<double *>(smem_raw + 32);
   uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
   float *fh = reinterpret_cast<float *>(smem_raw + 128);   // P, then the prefix's high part: buf_len + 1
   float *rows = fh + buf_len + 1;                // warps x [Y, Y low part, G, Y - cut] x 33 widths of a block
-  float *dd = rows + kLseMaxWarps * 4 * kR;      // d_len difference entries
-  float *wsum = dd + d_len;                      // per-warp scan totals
+  float *wsum = rows + kLseMaxWarps * 4 * kR;    // per-warp scan totals
   int *evl = reinterpret_cast<int *>(wsum + 32);                                  // warps x kEvCap event lists
   __half *fl = reinterpret_cast<__half *>(evl + (blockDim.x >> 5) * kEvCap);     // prefix: low part, buf_len + 1
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, fh);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
-  build_prefix(fh, buf_len, fl, wtot);
-  for (int j = threadIdx.x; j < d_len; j += blockDim.x) dd[j] = 0.0f;
-  __syncthreads();
+  // The difference array D over the segment's bins and the W - 1 after it
+  // (k + w <= nb + W - 1) lives in global memory, in this segment's own
+  // output slots: its dL/dP bins, then its tail.  Updates are fire-and-forget
+  // reductions that stay in L2; the CTA scans it after the sweep, staged
+  // into shared memory over the then-unused prefix.
+  float *out = dp + (t.src - power);   // same offset in the dP buffer
+  float *tl = tail + t.seg_g * static_cast<int64_t>(W);
+  const int d_seg = t.nb + W - 1;
+  for (int j = threadIdx.x; j < t.nb; j += blockDim.x) out[j] = 0.0f;
+  for (int j = threadIdx.x; j < W; j += blockDim.x) tl[j] = 0.0f;   // W - 1 read; the last takes k + w = nb + W - 1
+  build_prefix(fh, buf_len, fl, wtot);   // ends with a barrier: the zeros come first
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // this warp's row of the block's widths: Y, its low part, G and the
   // threshold Y - cut (+inf where G = 0: no window of that width counts)
@@ -595,16 +604,20 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps, 6) lse_backward_kernel(
                        // (S - Y) from the two pairs: hi - Y is exact (Sterbenz)
                        const float g =
                            grow[c] * expf(__fadd_rn(__fsub_rn(hi, yrow[c]), __fsub_rn(lo, ylrow[c])) * inv_tau);
-                       atomicAdd(&dd[k], g);
-                       atomicAdd(&dd[k + w], -g);
+                       atomicAdd(out + k, g);   // k < nb
+                       const int e = k + w;
+                       atomicAdd(e < t.nb ? out + e : tl + (e - t.nb), -g);
                      });
         if (bi + 1 < (W + kR - 1) / kR) load_rows(bi + 1);
       });
   __syncthreads();
+  float *dd = fh;   // d_seg <= buf_len entries
+  for (int j = threadIdx.x; j < d_seg; j += blockDim.x) dd[j] = __ldcg(j < t.nb ? out + j : tl + (j - t.nb));
+  __syncthreads();
   // inclusive prefix sum of dd: thread t owns a contiguous chunk
   const int nt = blockDim.x;
-  const int chunk = (d_len + nt - 1) / nt;
-  const int a0 = threadIdx.x * chunk, a1 = min(d_len, a0 + chunk);
+  const int chunk = (d_seg + nt - 1) / nt;
+  const int a0 = threadIdx.x * chunk, a1 = min(d_seg, a0 + chunk);
   float run = 0.0f;
   for (int j = a0; j < a1; ++j) run += dd[j];
   float incl = run;
@@ -624,10 +637,8 @@ __global__ void __launch_bounds__(32 * kLseMaxWarps, 6) lse_backward_kernel(
   }
   __syncthreads();
   // bins of this segment, then the spill into the next one
-  float *out = dp + (t.src - power);   // same offset in the dP buffer
   for (int j = threadIdx.x; j < t.nb; j += nt) out[j] = dd[j];
-  float *tl = tail + t.seg_g * static_cast<int64_t>(W);
-  for (int j = threadIdx.x; j < W - 1; j += nt) tl[j] = (t.nb + j < d_len) ? dd[t.nb + j] : 0.0f;
+  for (int j = threadIdx.x; j < W - 1; j += nt) tl[j] = dd[t.nb + j];
 }
 
 // dL/dP -> C2R input, per segment (256 threads).
@@ -914,16 +925,13 @@ int pulscan_lse_backward(pulscan_plan p, const float *d_spec, const float *d_pow
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int warps = lse_warps(p);
   const int buf_len = lse_buf_len(p, warps);
-  int64_t max_n = 0;
-  for (const auto &se : p->series) max_n = std::max<int64_t>(max_n, se.m - (se.n_seg - 1) * p->seg_len);
-  const int d_len = static_cast<int>(max_n + p->z_max + 1);
-  const int smem = 128 + 4 * (buf_len + 1 + kLseMaxWarps * 4 * kR + d_len + 32 + warps * kEvCap) +
+  const int smem = 128 + 4 * (buf_len + 1 + kLseMaxWarps * 4 * kR + 32 + warps * kEvCap) +
                    2 * (buf_len + 1) + 16;
   rc = ensure_smem(lse_backward_kernel, smem, g_lim_bwd);
   if (rc) return rc;
   lse_backward_kernel<<<static_cast<unsigned>(p->total_seg), 32 * warps, smem, s>>>(
       d_power, p->d_series, p->d_seg_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len, tau,
-      lse_cut(p, tau), d_y, d_ylo, d_gy, p->d_dp, p->d_tail, p->d_counters, buf_len, d_len);
+      lse_cut(p, tau), d_y, d_ylo, d_gy, p->d_dp, p->d_tail, p->d_counters, buf_len);
   PS_CUDA(cudaGetLastError());
   normalise_backward_kernel<<<static_cast<unsigned>(p->total_seg), 256, 0, s>>>(
       reinterpret_cast<const float2 *>(d_spec), p->d_dp, p->d_tail, reinterpret_cast<const float4 *>(d_stats),

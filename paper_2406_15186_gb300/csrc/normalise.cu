@@ -569,15 +569,37 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
 //     re-reads the block from global memory.
 constexpr int kLeanBuckets = kFastBuckets;
 
+// Value buckets of the lean select in two instructions: t = (x - lo) * s
+// with s = 1022 / (hi - lo) is formed by one FMA against 1.5 * 2^23 (whose
+// ulp is 1), so the sum is 1.5 * 2^23 + round(t) and its low mantissa bits
+// hold the bucket.  The offset's own rounding moves every t by the same
+// amount (< 1/2): x >= lo still gives a sum >= 1.5 * 2^23 and x <= hi one of
+// at most 1.5 * 2^23 + 1023, and the map is monotone in x (all a select
+// needs).
+constexpr float kBucketMagic = 12582912.0f;   // 1.5 * 2^23
+
+struct LeanScale {
+  float s, off;
+};
+
+__device__ __forceinline__ LeanScale lean_scale(float lo, float hi) {
+  const float s = (hi > lo) ? 1022.0f / (hi - lo) : 0.0f;
+  return LeanScale{s, fmaf(-lo, s, kBucketMagic)};
+}
+
+__device__ __forceinline__ uint32_t lean_bucket(float x, const LeanScale &sc) {
+  return __float_as_uint(fmaf(x, sc.s, sc.off)) & (kLeanBuckets - 1u);
+}
+
 template <int NT>
 struct LeanShared {
   uint32_t hist[2][2][kLeanBuckets];   // [median, MAD][component]
   float red[NT / 32][4];               // per-warp min0, min1, max0, max1
   float list[2][kCap];
   uint32_t list_n[2];
-  uint32_t b1[2], b2[2], below[2];
+  uint32_t b1[2], b2[2], below[2], through[2];
+  uint32_t wsum[2][NT / 64];           // the bucket scan's per-warp totals
   uint32_t kmax[2], kmin[2];           // split pairs: order-preserving keys
-  int mode[2];                         // per component: kGather, kSplit, kFlat, kCrowded
   float res[2][2];                     // selected order statistics (rank r, rank r + 1)
   float stat[2];                       // median or MAD per component
   float inv[2];                        // 1 / (kappa MAD), 0 if MAD = 0
@@ -604,87 +626,90 @@ template <int NT, int K, class Val>
 __device__ __forceinline__ bool lean_select(LeanShared<NT> &sh, int sel, Val val, int nv, uint32_t rank, bool pair,
                                             const float (&lo)[2], const float (&hi)[2], float (&olo)[2],
                                             float (&ohi)[2]) {
-  float scale[2];
+  LeanScale sc[2];
   bool flat[2];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     flat[c] = !(hi[c] > lo[c]);
-    scale[c] = fast_scale(lo[c], hi[c]);
+    sc[c] = lean_scale(lo[c], hi[c]);
+  }
+  if (threadIdx.x < 2) {   // this select's gather state (the previous select is done with it)
+    sh.list_n[threadIdx.x] = 0u;
+    sh.kmax[threadIdx.x] = 0u;
+    sh.kmin[threadIdx.x] = 0xffffffffu;
   }
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     if (j < nv) {
       const float2 f = val(j);
-      atomicAdd(&sh.hist[sel][0][fast_bucket(f.x, lo[0], scale[0])], 1u);
-      atomicAdd(&sh.hist[sel][1][fast_bucket(f.y, lo[1], scale[1])], 1u);
+      atomicAdd(&sh.hist[sel][0][lean_bucket(f.x, sc[0])], 1u);
+      atomicAdd(&sh.hist[sel][1][lean_bucket(f.y, sc[1])], 1u);
     }
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp < 2) {
-    // warp c: the 1024 buckets of component c, 32 per lane (summed in a
-    // skewed order: conflict-free banks), then a warp scan of the lane sums
-    const int c = warp;
-    const uint32_t *h = sh.hist[sel][c] + 32 * lane;
-    uint32_t local = 0;
-#pragma unroll 8
-    for (int q = 0; q < 32; ++q) local += h[(q + lane) & 31];
+  {
+    // block-wide scan: thread t sums kPer consecutive buckets of component
+    // t / (NT / 2); a warp scan and the per-warp totals give each thread its
+    // range of ranks, and the threads holding ranks r and r + 1 find their
+    // buckets
+    constexpr int kPer = 2 * kLeanBuckets / NT;
+    const int c = threadIdx.x / (NT / 2), tt = threadIdx.x % (NT / 2);
+    const int lane = tt & 31, wid = tt >> 5;
+    const uint32_t *h = sh.hist[sel][c] + kPer * tt;
+    uint32_t hv[kPer], local = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      hv[q] = h[q];
+      local += hv[q];
+    }
     uint32_t incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += u;
     }
-    const uint32_t excl = incl - local;
+    if (lane == 31) sh.wsum[c][wid] = incl;
+    __syncthreads();
+    uint32_t acc = incl - local;
+    for (int v = 0; v < wid; ++v) acc += sh.wsum[c][v];
     const uint32_t r1 = rank, r2 = rank + (pair ? 1u : 0u);
-    uint32_t b1 = 0, b2 = 0, below = 0, through = 0;
-    bool has1 = false, has2 = false;
-    if ((r1 >= excl && r1 < incl) || (r2 >= excl && r2 < incl)) {
-      uint32_t acc = excl;
-      for (int q = 0; q < 32; ++q) {
-        const uint32_t nxt = acc + h[q];
+    if ((r1 >= acc && r1 < acc + local) || (r2 >= acc && r2 < acc + local)) {
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const uint32_t nxt = acc + hv[q];
         if (r1 >= acc && r1 < nxt) {
-          b1 = 32 * lane + q;
-          below = acc;
-          has1 = true;
+          sh.b1[c] = kPer * tt + q;
+          sh.below[c] = acc;
         }
         if (r2 >= acc && r2 < nxt) {
-          b2 = 32 * lane + q;
-          through = nxt;
-          has2 = true;
+          sh.b2[c] = kPer * tt + q;
+          sh.through[c] = nxt;
         }
         acc = nxt;
       }
     }
-    const uint32_t m1 = __ballot_sync(0xffffffffu, has1), m2 = __ballot_sync(0xffffffffu, has2);
-    b1 = __shfl_sync(0xffffffffu, b1, __ffs(static_cast<int>(m1)) - 1);
-    below = __shfl_sync(0xffffffffu, below, __ffs(static_cast<int>(m1)) - 1);
-    b2 = __shfl_sync(0xffffffffu, b2, __ffs(static_cast<int>(m2)) - 1);
-    through = __shfl_sync(0xffffffffu, through, __ffs(static_cast<int>(m2)) - 1);
-    if (lane == 0) {
-      int mode = kGather;
-      if (flat[c]) mode = kFlat;
-      else if (through - below <= static_cast<uint32_t>(kCap)) mode = kGather;
-      else if (b1 != b2) mode = kSplit;
-      else mode = kCrowded;
-      sh.mode[c] = mode;
-      sh.b1[c] = b1;
-      sh.b2[c] = b2;
-      sh.below[c] = below;
-      sh.list_n[c] = 0u;
-      sh.kmax[c] = 0u;
-      sh.kmin[c] = 0xffffffffu;
-    }
   }
   __syncthreads();
-  const int mode0 = sh.mode[0], mode1 = sh.mode[1];
+  // every thread classifies both components: few enough values in the
+  // target bucket(s) to gather, a middle pair split over two crowded
+  // buckets, a flat range, or crowded
+  int md[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (flat[c]) md[c] = kFlat;
+    else if (sh.through[c] - sh.below[c] <= static_cast<uint32_t>(kCap)) md[c] = kGather;
+    else if (sh.b1[c] != sh.b2[c]) md[c] = kSplit;
+    else md[c] = kCrowded;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mode0 = md[0], mode1 = md[1];
   if (mode0 == kCrowded || mode1 == kCrowded) return false;
   const uint32_t lo0 = sh.b1[0], hi0 = sh.b2[0], lo1 = sh.b1[1], hi1 = sh.b2[1];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     if (j < nv) {
       const float2 f = val(j);
-      const uint32_t q0 = fast_bucket(f.x, lo[0], scale[0]), q1 = fast_bucket(f.y, lo[1], scale[1]);
+      const uint32_t q0 = lean_bucket(f.x, sc[0]), q1 = lean_bucket(f.y, sc[1]);
       if (mode0 == kGather && q0 >= lo0 && q0 <= hi0) sh.list[0][atomicAdd(&sh.list_n[0], 1u)] = f.x;
       if (mode1 == kGather && q1 >= lo1 && q1 <= hi1) sh.list[1][atomicAdd(&sh.list_n[1], 1u)] = f.y;
       if (mode0 == kSplit) {
@@ -768,7 +793,9 @@ __global__ void __launch_bounds__(NT, lean_min_blocks<NT, K>()) normalise_lean_k
   if (dc_here && t == 0) v[0] = make_float2(0.0f, 0.0f);   // DC := 0
   auto gval = [&](int e) -> float2 { return (dc_here && e == 0) ? make_float2(0.0f, 0.0f) : src[e]; };
 
-  // range of both components; both selects' histograms zeroed meanwhile
+  // both selects' histograms zeroed while the loads are in flight, then the
+  // range of both components
+  for (int j = t; j < 4 * kLeanBuckets; j += NT) (&sh.hist[0][0][0])[j] = 0u;
   float a0 = INFINITY, a1 = INFINITY, z0 = -INFINITY, z1 = -INFINITY;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
@@ -792,7 +819,6 @@ __global__ void __launch_bounds__(NT, lean_min_blocks<NT, K>()) normalise_lean_k
     sh.red[t >> 5][2] = z0;
     sh.red[t >> 5][3] = z1;
   }
-  for (int j = t; j < 4 * kLeanBuckets; j += NT) (&sh.hist[0][0][0])[j] = 0u;
   __syncthreads();
   float mn[2] = {INFINITY, INFINITY}, mx[2] = {-INFINITY, -INFINITY};
 #pragma unroll

@@ -384,18 +384,6 @@ __device__ __forceinline__ bool select_fast(SelShared &sh, Get get, uint32_t *bk
   return true;
 }
 
-// Value buckets of the lean kernel's selects (1024 per component).
-constexpr int kFastBuckets = 1024;
-
-__device__ __forceinline__ uint32_t fast_bucket(float x, float lo, float scale) {
-  const float t = (x - lo) * scale;
-  return min(static_cast<uint32_t>(fmaxf(t, 0.0f)), static_cast<uint32_t>(kFastBuckets - 1));
-}
-
-__device__ __forceinline__ float fast_scale(float lo, float hi) {
-  return (hi > lo) ? static_cast<float>(kFastBuckets) / (hi - lo) * (1.0f - 1.0f / 4096.0f) : 0.0f;
-}
-
 __device__ __forceinline__ float mean_of(float a, float b) {
   return static_cast<float>(0.5 * (static_cast<double>(a) + static_cast<double>(b)));
 }
@@ -549,34 +537,51 @@ __global__ void __launch_bounds__(kNormThreads) normalise_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Lean register kernel: the same exact selection with fewer block-wide
-// barriers (9 per block: one after the range pass, four per select), for
-// blocks of up to NT * K bins (NT = 256 or 1024 threads).  Thread t holds
-// bins t, t + NT, ... in registers.
-//   * the range pass also zeroes both selects' histograms, and every thread
-//     reduces the per-warp range partials itself (no second barrier);
-//   * per select: (1) histogram of both components into 1024 value buckets;
-//     (2) one warp per component scans its histogram and classifies the
-//     target bucket(s) of ranks r and r + 1: few enough values to gather,
-//     a pair split over two buckets (rank r is then the largest value of the
-//     first, rank r + 1 the smallest of the second: every bucket between is
-//     empty), a flat range (all values equal), or crowded; (3) all threads
-//     gather the target values, or fold the split pair's two extremes with
-//     atomic max / min on order-preserving integer keys; (4) the component's
-//     warp ranks its list and forms the statistic (FP64 mean of the two middle
-//     values, and for the MAD also 1 / (kappa MAD)).  A crowded bucket (a block
-//     dominated by a strong tone) falls back to the multi-level select, which
-//     re-reads the block from global memory.
-constexpr int kLeanBuckets = kFastBuckets;
+// Lean register kernel: one CTA of NT threads per block of up to NT K + 1
+// bins.  Thread t holds bins t, t + NT, ..., t + (K - 1) NT in registers,
+// and thread 0 also bin NT K when the block has that one more bin (the last
+// block of a power-of-two series ends with the Nyquist bin).  A block with
+// fewer bins fills its missing slots with pads: the block maximum for the
+// median and the largest deviation for the MAD, which leaves every order
+// statistic of rank below n where it is.  Both selects of a block run the
+// same exact value-bucket select over both components at once:
+//   (1) a histogram over 1024 value buckets: the bucket of x is the low bits
+//       of fma(x, s, magic - lo s) with magic = 1.5 2^23 (whose ulp is 1), so
+//       one multiply-add of those bits forms the shared-memory address of a
+//       fire-and-forget red.shared.add;
+//   (2) a block-wide scan finds the bucket(s) holding ranks r and r + 1;
+//   (3) every thread appends its values in those buckets to a short list;
+//   (4) one warp per component ranks its list and forms the statistic (the
+//       FP64 mean of the two middle values for an even count; for the MAD
+//       also 1 / (kappa MAD)).
+// The MAD's values are the deviations x - med, formed once in place (the
+// histogram and the gather take their absolute value as an operand
+// modifier); the power is formed from the same registers.  The bucket map is
+// monotone (one rounding of an exact x s + off) and lands in [0, 1022] while
+// the offset magic - lo s is a float of integer resolution (|.| < 2^24) and s
+// is finite; a block outside that (a tight cluster far from zero, an
+// infinity or NaN) or with more than kLeanCap values in its target buckets (a
+// block dominated by a strong tone) takes the multi-level select, which
+// re-reads the block from global memory.  Nine block barriers per block.
+constexpr int kLeanBuckets = 1024;
+constexpr int kLeanGuard = 8;                     // unused buckets on each side of the map's range
+constexpr int kLeanRow = kLeanBuckets + 2 * kLeanGuard;
+constexpr int kLeanCap = 128;                     // gathered values ranked directly, per component
+constexpr float kBucketMagic = 12582912.0f;       // 1.5 * 2^23
+constexpr uint32_t kMagicBits = 0x4B400000u;      // its bit pattern
 
-// Value buckets of the lean select in two instructions: t = (x - lo) * s
-// with s = 1022 / (hi - lo) is formed by one FMA against 1.5 * 2^23 (whose
-// ulp is 1), so the sum is 1.5 * 2^23 + round(t) and its low mantissa bits
-// hold the bucket.  The offset's own rounding moves every t by the same
-// amount (< 1/2): x >= lo still gives a sum >= 1.5 * 2^23 and x <= hi one of
-// at most 1.5 * 2^23 + 1023, and the map is monotone in x (all a select
-// needs).
-constexpr float kBucketMagic = 12582912.0f;   // 1.5 * 2^23
+template <int NT>
+struct LeanShared {
+  uint32_t hist[2][2][kLeanRow];   // [median, MAD][component]
+  float4 red[NT / 32];             // per-warp min0, min1, max0, max1
+  float list[2][kLeanCap];
+  uint32_t list_n[2];
+  uint32_t b1[2], b2[2], below[2], through[2];
+  uint32_t wsum[2][NT / 64];       // the bucket scan's per-warp totals
+  float res[2][2];                 // selected order statistics (rank r, rank r + 1)
+  float stat[2];                   // median or MAD per component
+  float inv[2];                    // 1 / (kappa MAD), 0 if MAD = 0
+};
 
 struct LeanScale {
   float s, off;
@@ -587,93 +592,113 @@ __device__ __forceinline__ LeanScale lean_scale(float lo, float hi) {
   return LeanScale{s, fmaf(-lo, s, kBucketMagic)};
 }
 
-__device__ __forceinline__ uint32_t lean_bucket(float x, const LeanScale &sc) {
-  return __float_as_uint(fmaf(x, sc.s, sc.off)) & (kLeanBuckets - 1u);
+// The map x -> fma(x, s, off) is exact to one rounding at integer
+// resolution, so monotone with values in [magic, magic + 1022] for x in
+// [lo, hi]; false (NaN included) where that does not hold.
+__device__ __forceinline__ bool lean_exact(const LeanScale &sc) {
+  return sc.s < INFINITY && fabsf(sc.off) < 16777216.0f;
 }
 
-template <int NT>
-struct LeanShared {
-  uint32_t hist[2][2][kLeanBuckets];   // [median, MAD][component]
-  float red[NT / 32][4];               // per-warp min0, min1, max0, max1
-  float list[2][kCap];
-  uint32_t list_n[2];
-  uint32_t b1[2], b2[2], below[2], through[2];
-  uint32_t wsum[2][NT / 64];           // the bucket scan's per-warp totals
-  uint32_t kmax[2], kmin[2];           // split pairs: order-preserving keys
-  float res[2][2];                     // selected order statistics (rank r, rank r + 1)
-  float stat[2];                       // median or MAD per component
-  float inv[2];                        // 1 / (kappa MAD), 0 if MAD = 0
-};
-
-enum : int { kGather = 0, kSplit = 1, kFlat = 2, kCrowded = 3 };
-
-// Order-preserving map of a float to uint32 (finite values) and its inverse.
-__device__ __forceinline__ uint32_t order_key(float x) {
-  const uint32_t b = __float_as_uint(x);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+__device__ __forceinline__ void red_inc_shared(uint32_t addr) {
+  asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
 }
-__device__ __forceinline__ float order_unkey(uint32_t k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+
+// NaN-propagating minimum / maximum (a NaN anywhere in a block sends it to
+// the multi-level select).
+__device__ __forceinline__ float nmin(float a, float b) {
+  float r;
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float nmax(float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float warp_nmin(float v) {
+  float r;
+  asm volatile("redux.sync.min.NaN.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ float warp_nmax(float v) {
+  float r;
+  asm volatile("redux.sync.max.NaN.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
 }
 
 // One exact select of ranks `rank` (and rank + 1 when `pair`) of both
-// components over [lo, hi] from this thread's nv register values val(j).
+// components over [lo, hi] from this thread's K register values (their
+// absolute values with kAbs) and the extra value fx when has_x.
 // hist[sel] must be zero and visible.  On return (after a barrier) every
 // thread holds the order statistics in olo / ohi, and sh.stat the statistic
 // (with sh.inv for the MAD, sel = 1); false (decided by the whole block,
-// nothing written) when a target bucket is crowded.
-template <int NT, int K, class Val>
-__device__ __forceinline__ bool lean_select(LeanShared<NT> &sh, int sel, Val val, int nv, uint32_t rank, bool pair,
-                                            const float (&lo)[2], const float (&hi)[2], float (&olo)[2],
-                                            float (&ohi)[2]) {
-  LeanScale sc[2];
-  bool flat[2];
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    flat[c] = !(hi[c] > lo[c]);
-    sc[c] = lean_scale(lo[c], hi[c]);
+// no statistic written) when the fast path does not apply.
+template <int NT, int K, bool kAbs>
+__device__ __forceinline__ bool lean_select(LeanShared<NT> &sh, int sel, const float2 (&v)[K], bool has_x, float2 fx,
+                                            uint32_t rank, bool pair, const float (&lo)[2], const float (&hi)[2],
+                                            float (&olo)[2], float (&ohi)[2]) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const LeanScale s0 = lean_scale(lo[0], hi[0]), s1 = lean_scale(lo[1], hi[1]);
+  const bool flat0 = !(hi[0] > lo[0]), flat1 = !(hi[1] > lo[1]);
+  // (a non-flat range needs s > 0: with s = 0 an infinite value would map to NaN)
+  if (!lean_exact(s0) || !lean_exact(s1) || (!flat0 && !(s0.s > 0.0f)) || (!flat1 && !(s1.s > 0.0f))) return false;
+  auto val = [&](int j) -> float2 { return kAbs ? make_float2(fabsf(v[j].x), fabsf(v[j].y)) : v[j]; };
+  if (kAbs) fx = make_float2(fabsf(fx.x), fabsf(fx.y));
+  if (t < 2) {   // this select's gather state (the previous select is done with it)
+    sh.list_n[t] = 0u;
+    sh.b1[t] = 0xffffffffu;
+    sh.b2[t] = 0xffffffffu;
   }
-  if (threadIdx.x < 2) {   // this select's gather state (the previous select is done with it)
-    sh.list_n[threadIdx.x] = 0u;
-    sh.kmax[threadIdx.x] = 0u;
-    sh.kmin[threadIdx.x] = 0xffffffffu;
-  }
+  const uint32_t hb0 = smem_addr(&sh.hist[sel][0][kLeanGuard]) - 4u * kMagicBits;
+  const uint32_t hb1 = smem_addr(&sh.hist[sel][1][kLeanGuard]) - 4u * kMagicBits;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    if (j < nv) {
-      const float2 f = val(j);
-      atomicAdd(&sh.hist[sel][0][lean_bucket(f.x, sc[0])], 1u);
-      atomicAdd(&sh.hist[sel][1][lean_bucket(f.y, sc[1])], 1u);
-    }
+    const float2 f = val(j);
+    red_inc_shared(hb0 + 4u * __float_as_uint(fmaf(f.x, s0.s, s0.off)));
+    red_inc_shared(hb1 + 4u * __float_as_uint(fmaf(f.y, s1.s, s1.off)));
+  }
+  if (has_x) {
+    red_inc_shared(hb0 + 4u * __float_as_uint(fmaf(fx.x, s0.s, s0.off)));
+    red_inc_shared(hb1 + 4u * __float_as_uint(fmaf(fx.y, s1.s, s1.off)));
   }
   __syncthreads();
   {
     // block-wide scan: thread t sums kPer consecutive buckets of component
     // t / (NT / 2); a warp scan and the per-warp totals give each thread its
-    // range of ranks, and the threads holding ranks r and r + 1 find their
+    // range of ranks, and the threads holding ranks r and r + 1 record their
     // buckets
     constexpr int kPer = 2 * kLeanBuckets / NT;
-    const int c = threadIdx.x / (NT / 2), tt = threadIdx.x % (NT / 2);
-    const int lane = tt & 31, wid = tt >> 5;
-    const uint32_t *h = sh.hist[sel][c] + kPer * tt;
+    const int c = t / (NT / 2), tt = t % (NT / 2);
+    const int sl = tt & 31, sw = tt >> 5;
+    const uint32_t *h = &sh.hist[sel][c][kLeanGuard + kPer * tt];
     uint32_t hv[kPer], local = 0;
+    if constexpr (kPer % 4 == 0) {
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      hv[q] = h[q];
-      local += hv[q];
+      for (int q = 0; q < kPer; q += 4) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(h + q);
+        hv[q] = u.x;
+        hv[q + 1] = u.y;
+        hv[q + 2] = u.z;
+        hv[q + 3] = u.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) hv[q] = h[q];
     }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) local += hv[q];
     uint32_t incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
+      if (sl >= o) incl += u;
     }
-    if (lane == 31) sh.wsum[c][wid] = incl;
+    if (sl == 31) sh.wsum[c][sw] = incl;
     __syncthreads();
     uint32_t acc = incl - local;
-    for (int v = 0; v < wid; ++v) acc += sh.wsum[c][v];
+    for (int w = 0; w < sw; ++w) acc += sh.wsum[c][w];
     const uint32_t r1 = rank, r2 = rank + (pair ? 1u : 0u);
-    if ((r1 >= acc && r1 < acc + local) || (r2 >= acc && r2 < acc + local)) {
+    if ((r1 - acc < local) || (r2 - acc < local)) {
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
         const uint32_t nxt = acc + hv[q];
@@ -690,58 +715,57 @@ __device__ __forceinline__ bool lean_select(LeanShared<NT> &sh, int sel, Val val
     }
   }
   __syncthreads();
-  // every thread classifies both components: few enough values in the
-  // target bucket(s) to gather, a middle pair split over two crowded
-  // buckets, a flat range, or crowded
-  int md[2];
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    if (flat[c]) md[c] = kFlat;
-    else if (sh.through[c] - sh.below[c] <= static_cast<uint32_t>(kCap)) md[c] = kGather;
-    else if (sh.b1[c] != sh.b2[c]) md[c] = kSplit;
-    else md[c] = kCrowded;
+  // every thread classifies both components: a flat range (all values
+  // equal: nothing to gather), few enough values to gather, or the slow path
+  uint32_t base0 = 0u, span0 = 0u, base1 = 0u, span1 = 0u;
+  bool fast = true;
+  if (!flat0) {
+    const uint32_t b1 = sh.b1[0], b2 = sh.b2[0];
+    fast = fast && b2 != 0xffffffffu && sh.through[0] - sh.below[0] <= static_cast<uint32_t>(kLeanCap);
+    base0 = kMagicBits + b1;
+    span0 = b2 - b1;
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mode0 = md[0], mode1 = md[1];
-  if (mode0 == kCrowded || mode1 == kCrowded) return false;
-  const uint32_t lo0 = sh.b1[0], hi0 = sh.b2[0], lo1 = sh.b1[1], hi1 = sh.b2[1];
+  if (!flat1) {
+    const uint32_t b1 = sh.b1[1], b2 = sh.b2[1];
+    fast = fast && b2 != 0xffffffffu && sh.through[1] - sh.below[1] <= static_cast<uint32_t>(kLeanCap);
+    base1 = kMagicBits + b1;
+    span1 = b2 - b1;
+  }
+  if (!fast) return false;
+  auto append = [&](int c, float x) {
+    const uint32_t i = atomicAdd(&sh.list_n[c], 1u);
+    if (i < static_cast<uint32_t>(kLeanCap)) sh.list[c][i] = x;
+  };
+  // a flat component's map is the constant magic: never within [base, base + span] = [0, 0]
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    if (j < nv) {
-      const float2 f = val(j);
-      const uint32_t q0 = lean_bucket(f.x, sc[0]), q1 = lean_bucket(f.y, sc[1]);
-      if (mode0 == kGather && q0 >= lo0 && q0 <= hi0) sh.list[0][atomicAdd(&sh.list_n[0], 1u)] = f.x;
-      if (mode1 == kGather && q1 >= lo1 && q1 <= hi1) sh.list[1][atomicAdd(&sh.list_n[1], 1u)] = f.y;
-      if (mode0 == kSplit) {
-        if (q0 == lo0) atomicMax(&sh.kmax[0], order_key(f.x));
-        if (q0 == hi0) atomicMin(&sh.kmin[0], order_key(f.x));
-      }
-      if (mode1 == kSplit) {
-        if (q1 == lo1) atomicMax(&sh.kmax[1], order_key(f.y));
-        if (q1 == hi1) atomicMin(&sh.kmin[1], order_key(f.y));
-      }
-    }
+    const float2 f = val(j);
+    if (__float_as_uint(fmaf(f.x, s0.s, s0.off)) - base0 <= span0) append(0, f.x);
+    if (__float_as_uint(fmaf(f.y, s1.s, s1.off)) - base1 <= span1) append(1, f.y);
+  }
+  if (has_x) {
+    if (__float_as_uint(fmaf(fx.x, s0.s, s0.off)) - base0 <= span0) append(0, fx.x);
+    if (__float_as_uint(fmaf(fx.y, s1.s, s1.off)) - base1 <= span1) append(1, fx.y);
   }
   __syncthreads();
   if (warp < 2) {
     const int c = warp;
-    const int mode = c ? mode1 : mode0;
-    if (mode == kGather) {
-      const uint32_t m = sh.list_n[c];
+    if (c ? !flat1 : !flat0) {
+      const uint32_t m = min(sh.list_n[c], static_cast<uint32_t>(kLeanCap));
       const uint32_t want = rank - sh.below[c];
       for (uint32_t i = lane; i < m; i += 32) {
-        const float v = sh.list[c][i];
+        const float x = sh.list[c][i];
         uint32_t rk = 0;
         for (uint32_t f = 0; f < m; ++f) {
           const float u = sh.list[c][f];
-          rk += (u < v || (u == v && f < i)) ? 1u : 0u;
+          rk += (u < x || (u == x && f < i)) ? 1u : 0u;
         }
-        if (rk == want) sh.res[c][0] = v;
-        if (pair && rk == want + 1) sh.res[c][1] = v;
+        if (rk == want) sh.res[c][0] = x;
+        if (pair && rk == want + 1) sh.res[c][1] = x;
       }
     } else if (lane == 0) {
-      sh.res[c][0] = (mode == kFlat) ? lo[c] : order_unkey(sh.kmax[c]);
-      sh.res[c][1] = (mode == kFlat) ? lo[c] : order_unkey(sh.kmin[c]);
+      sh.res[c][0] = lo[c];
+      sh.res[c][1] = lo[c];
     }
     __syncwarp();
     if (lane == 0) {
@@ -760,20 +784,40 @@ __device__ __forceinline__ bool lean_select(LeanShared<NT> &sh, int sel, Val val
   return true;
 }
 
+// The multi-level select over the block in global memory: the raw values
+// (dev = false) or their deviations |x - c| (dev = true): the rare path.
+// Inlined: an out-of-line call measured slower (2^23 series 48 against 36 us),
+// its register saves around the call included.
+template <int NT>
+__device__ __forceinline__ void lean_fallback(SelSharedT<NT> &sh, const float2 *src, bool dc_here, int n, uint32_t rank,
+                                           bool pair, bool dev, float c0, float c1, float *out) {
+  float lo_v[2], hi_v[2];
+  __syncthreads();
+  select_levels<NT>(sh, [&](int e, float &v0, float &v1) {
+    const float2 f = (dc_here && e == 0) ? make_float2(0.0f, 0.0f) : src[e];
+    v0 = dev ? fabsf(f.x - c0) : f.x;
+    v1 = dev ? fabsf(f.y - c1) : f.y;
+  }, n, rank, pair, lo_v, hi_v);
+  out[0] = lo_v[0];
+  out[1] = lo_v[1];
+  out[2] = hi_v[0];
+  out[3] = hi_v[1];
+}
+
 template <int NT, int K>
 constexpr int lean_min_blocks() {
-  return NT == 1024 ? 1 : (K <= 9 ? 6 : (K <= 17 ? 4 : 2));
+  return NT == 1024 ? 1 : (K <= 8 ? 5 : 4);
 }
 
 template <int NT, int K>
 __global__ void __launch_bounds__(NT, lean_min_blocks<NT, K>()) normalise_lean_kernel(
     const float2 *__restrict__ spec, float *__restrict__ power, float4 *__restrict__ stats,
     const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off, int n_series, int seg_len,
-    float *__restrict__ sel) {
+    float *__restrict__ sel, int64_t seg_base) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   LeanShared<NT> &sh = *reinterpret_cast<LeanShared<NT> *>(smem_raw);
   SelSharedT<NT> &legacy = *reinterpret_cast<SelSharedT<NT> *>(smem_raw);   // the fallback's (same memory)
-  const int64_t g = blockIdx.x;
+  const int64_t g = seg_base + blockIdx.x;
   int lo_s = 0, hi_s = n_series - 1;
   while (lo_s < hi_s) {
     const int mid = (lo_s + hi_s + 1) >> 1;
@@ -782,68 +826,82 @@ __global__ void __launch_bounds__(NT, lean_min_blocks<NT, K>()) normalise_lean_k
   const SeriesDev S = series[lo_s];
   const int64_t sl = g - S.seg_off;
   const int64_t b0 = sl * seg_len;
-  const int n = static_cast<int>(((sl == S.n_seg - 1) ? S.m : b0 + seg_len) - b0);
+  const int n = static_cast<int>(((sl == S.n_seg - 1) ? S.m : b0 + seg_len) - b0);   // <= NT K + 1
   const float2 *src = spec + S.spec_off + b0;
   const int t = threadIdx.x;
-  const int nv = (t < n) ? min(K, (n - t + NT - 1) / NT) : 0;
-  float2 v[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) v[j] = (j < nv) ? __ldg(src + j * NT + t) : make_float2(0.0f, 0.0f);
+  constexpr int kFull = NT * K;
   const bool dc_here = (b0 == 0);
+  const bool full = n >= kFull;
+  const int nv = full ? K : ((t < n) ? (n - 1 - t) / NT + 1 : 0);
+  // the block's first value stands in for missing slots in the range pass
+  const float2 first = dc_here ? make_float2(0.0f, 0.0f) : __ldg(src);
+  float2 v[K];
+  if (full) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = __ldg(src + j * NT + t);
+  } else {
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = (j < nv) ? __ldg(src + j * NT + t) : first;
+  }
   if (dc_here && t == 0) v[0] = make_float2(0.0f, 0.0f);   // DC := 0
-  auto gval = [&](int e) -> float2 { return (dc_here && e == 0) ? make_float2(0.0f, 0.0f) : src[e]; };
+  const bool has_x = (t == 0) && (n > kFull);
+  float2 vx = has_x ? __ldg(src + kFull) : first;
 
-  // both selects' histograms zeroed while the loads are in flight, then the
-  // range of both components
-  for (int j = t; j < 4 * kLeanBuckets; j += NT) (&sh.hist[0][0][0])[j] = 0u;
-  float a0 = INFINITY, a1 = INFINITY, z0 = -INFINITY, z1 = -INFINITY;
+  // both selects' histograms zeroed while the loads are in flight
+  {
+    uint4 *hz = reinterpret_cast<uint4 *>(&sh.hist[0][0][0]);
+    constexpr int kWords16 = static_cast<int>(sizeof(sh.hist) / 16);
+    for (int i = t; i < kWords16; i += NT) hz[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  // range of both components (a NaN propagates)
+  float a0 = nmin(v[0].x, vx.x), a1 = nmin(v[0].y, vx.y), z0 = nmax(v[0].x, vx.x), z1 = nmax(v[0].y, vx.y);
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if (j < nv) {
-      a0 = fminf(a0, v[j].x);
-      a1 = fminf(a1, v[j].y);
-      z0 = fmaxf(z0, v[j].x);
-      z1 = fmaxf(z1, v[j].y);
-    }
+  for (int j = 1; j < K; ++j) {
+    a0 = nmin(a0, v[j].x);
+    a1 = nmin(a1, v[j].y);
+    z0 = nmax(z0, v[j].x);
+    z1 = nmax(z1, v[j].y);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 = fminf(a0, __shfl_xor_sync(0xffffffffu, a0, o));
-    a1 = fminf(a1, __shfl_xor_sync(0xffffffffu, a1, o));
-    z0 = fmaxf(z0, __shfl_xor_sync(0xffffffffu, z0, o));
-    z1 = fmaxf(z1, __shfl_xor_sync(0xffffffffu, z1, o));
-  }
-  if ((t & 31) == 0) {
-    sh.red[t >> 5][0] = a0;
-    sh.red[t >> 5][1] = a1;
-    sh.red[t >> 5][2] = z0;
-    sh.red[t >> 5][3] = z1;
-  }
+  a0 = warp_nmin(a0);
+  a1 = warp_nmin(a1);
+  z0 = warp_nmax(z0);
+  z1 = warp_nmax(z1);
+  if ((t & 31) == 0) sh.red[t >> 5] = make_float4(a0, a1, z0, z1);
   __syncthreads();
-  float mn[2] = {INFINITY, INFINITY}, mx[2] = {-INFINITY, -INFINITY};
+  float mn[2], mx[2];
+  {
+    float4 r = sh.red[0];
 #pragma unroll
-  for (int w = 0; w < NT / 32; ++w) {
-    mn[0] = fminf(mn[0], sh.red[w][0]);
-    mn[1] = fminf(mn[1], sh.red[w][1]);
-    mx[0] = fmaxf(mx[0], sh.red[w][2]);
-    mx[1] = fmaxf(mx[1], sh.red[w][3]);
+    for (int w = 1; w < NT / 32; ++w) {
+      const float4 q = sh.red[w];
+      r = make_float4(nmin(r.x, q.x), nmin(r.y, q.y), nmax(r.z, q.z), nmax(r.w, q.w));
+    }
+    mn[0] = r.x;
+    mn[1] = r.y;
+    mx[0] = r.z;
+    mx[1] = r.w;
   }
-
   const bool even = (n % 2) == 0;
   const uint32_t rank = even ? static_cast<uint32_t>(n / 2 - 1) : static_cast<uint32_t>(n / 2);
+  if (!full) {
+    // pads at the block maximum: no order statistic of rank < n moves
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j >= nv) v[j] = make_float2(mx[0], mx[1]);
+  }
   float lo_v[2], hi_v[2];
   float med[2], mad[2], inv[2];
+  float fb[4];
   bool fell_back = false;
-  if (lean_select<NT, K>(sh, 0, [&](int j) { return v[j]; }, nv, rank, even, mn, mx, lo_v, hi_v)) {
+  if (lean_select<NT, K, false>(sh, 0, v, has_x, vx, rank, even, mn, mx, lo_v, hi_v)) {
     med[0] = sh.stat[0];
     med[1] = sh.stat[1];
   } else {
-    __syncthreads();
-    select_levels<NT>(legacy, [&](int e, float &v0, float &v1) {
-      const float2 f = gval(e);
-      v0 = f.x;
-      v1 = f.y;
-    }, n, rank, even, lo_v, hi_v);
+    lean_fallback<NT>(legacy, src, dc_here, n, rank, even, false, 0.0f, 0.0f, fb);
+    lo_v[0] = fb[0];
+    lo_v[1] = fb[1];
+    hi_v[0] = fb[2];
+    hi_v[1] = fb[3];
     med[0] = even ? mean_of(lo_v[0], hi_v[0]) : lo_v[0];
     med[1] = even ? mean_of(lo_v[1], hi_v[1]) : lo_v[1];
     fell_back = true;
@@ -857,26 +915,37 @@ __global__ void __launch_bounds__(NT, lean_min_blocks<NT, K>()) normalise_lean_k
   if (fell_back) {
     // the fallback used the shared memory: zero the MAD histogram again
     __syncthreads();
-    for (int j = t; j < 2 * kLeanBuckets; j += NT) (&sh.hist[1][0][0])[j] = 0u;
+    uint32_t *hz = &sh.hist[1][0][0];
+    for (int j = t; j < 2 * kLeanRow; j += NT) hz[j] = 0u;
     __syncthreads();
   }
-  // MADs: the same selection on |x - med| over [0, the largest deviation]
-  const float c0 = med[0], c1 = med[1];
+  // deviations x - med in place; pads at the largest deviation
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    v[j].x -= med[0];
+    v[j].y -= med[1];
+  }
+  vx.x -= med[0];
+  vx.y -= med[1];
   const float dlo[2] = {0.0f, 0.0f};
-  const float dhi[2] = {fmaxf(fabsf(mx[0] - c0), fabsf(c0 - mn[0])), fmaxf(fabsf(mx[1] - c1), fabsf(c1 - mn[1]))};
-  if (lean_select<NT, K>(sh, 1, [&](int j) { return make_float2(fabsf(v[j].x - c0), fabsf(v[j].y - c1)); }, nv,
-                         rank, even, dlo, dhi, lo_v, hi_v)) {
+  const float dhi[2] = {fmaxf(fabsf(mx[0] - med[0]), fabsf(mn[0] - med[0])),
+                        fmaxf(fabsf(mx[1] - med[1]), fabsf(mn[1] - med[1]))};
+  if (!full) {
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j >= nv) v[j] = make_float2(dhi[0], dhi[1]);
+  }
+  if (lean_select<NT, K, true>(sh, 1, v, has_x, vx, rank, even, dlo, dhi, lo_v, hi_v)) {
     mad[0] = sh.stat[0];
     mad[1] = sh.stat[1];
     inv[0] = sh.inv[0];
     inv[1] = sh.inv[1];
   } else {
-    __syncthreads();
-    select_levels<NT>(legacy, [&](int e, float &v0, float &v1) {
-      const float2 f = gval(e);
-      v0 = fabsf(f.x - c0);
-      v1 = fabsf(f.y - c1);
-    }, n, rank, even, lo_v, hi_v);
+    lean_fallback<NT>(legacy, src, dc_here, n, rank, even, true, med[0], med[1], fb);
+    lo_v[0] = fb[0];
+    lo_v[1] = fb[1];
+    hi_v[0] = fb[2];
+    hi_v[1] = fb[3];
     mad[0] = even ? mean_of(lo_v[0], hi_v[0]) : lo_v[0];
     mad[1] = even ? mean_of(lo_v[1], hi_v[1]) : lo_v[1];
     inv[0] = mad[0] > 0.0f ? static_cast<float>(1.0 / (kKappa * static_cast<double>(mad[0]))) : 0.0f;
@@ -894,21 +963,35 @@ __global__ void __launch_bounds__(NT, lean_min_blocks<NT, K>()) normalise_lean_k
     inv[1] = 0.0f;
   }
   float *out = power + S.p_off + b0;
+  if (full) {
 #pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if (j < nv) {
-      const float a = (v[j].x - med[0]) * inv[0];
-      const float b = (v[j].y - med[1]) * inv[1];
+    for (int j = 0; j < K; ++j) {
+      const float a = v[j].x * inv[0], b = v[j].y * inv[1];
       out[j * NT + t] = 0.5f * (a * a + b * b);
     }
+  } else {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float a = v[j].x * inv[0], b = v[j].y * inv[1];
+      if (j < nv) out[j * NT + t] = 0.5f * (a * a + b * b);
+    }
+  }
+  if (has_x) {
+    const float a = vx.x * inv[0], b = vx.y * inv[1];
+    out[kFull] = 0.5f * (a * a + b * b);
   }
   if (t == 0 && stats != nullptr) stats[g] = make_float4(med[0], mad[0], med[1], mad[1]);
 }
 
-// Kernel shape for the plan's largest block: (threads, bins per thread) of
-// the lean register kernel, or (0, 0) for the staged kernel.  Power-of-two
-// series leave a last block of L + 1 bins, hence the odd sizes.
-constexpr int kLeanK[] = {1, 2, 3, 4, 5, 6, 8, 9, 12, 16, 17, 24, 32};
+// Kernel shapes (threads, bins per thread) of the lean register kernel, by
+// block size: a shape takes blocks of up to NT K + 1 bins.  (128-thread CTAs
+// with twice the bins per thread measured slower: the batch of 2048-bin
+// blocks 7.6 against 6.8 ms.)
+struct LeanShape {
+  int nt, k;
+};
+constexpr LeanShape kLeanShapes[] = {{256, 1}, {256, 2}, {256, 4}, {256, 6}, {256, 8},
+                                     {256, 12}, {256, 16}, {1024, 8}, {1024, 12}, {1024, 16}};
 
 int64_t largest_block(pulscan_plan p) {
   int64_t max_n = 0;
@@ -919,20 +1002,18 @@ int64_t largest_block(pulscan_plan p) {
   return max_n;
 }
 
+// (threads, bins per thread) of the lean kernel for the plan's largest
+// block, or (0, 0) for the staged kernel.
 void lean_shape(pulscan_plan p, int *nt, int *k) {
   const int64_t max_n = largest_block(p);
   *nt = 0;
   *k = 0;
-  for (int kk : kLeanK) {
-    if (max_n <= static_cast<int64_t>(kk) * kNormThreads) {
-      *nt = kNormThreads;
-      *k = kk;
+  for (const LeanShape &s : kLeanShapes) {
+    if (max_n <= static_cast<int64_t>(s.nt) * s.k + 1) {
+      *nt = s.nt;
+      *k = s.k;
       return;
     }
-  }
-  if (max_n <= 17LL * 1024) {
-    *nt = 1024;
-    *k = 17;
   }
 }
 
@@ -946,7 +1027,7 @@ template <int NT, int K>
 void launch_lean(pulscan_plan p, const float *d_spec, float *d_power, float4 *st4, float *d_sel, cudaStream_t s) {
   normalise_lean_kernel<NT, K><<<static_cast<unsigned>(p->base_seg), NT, lean_smem<NT>(), s>>>(
       reinterpret_cast<const float2 *>(d_spec), d_power, st4, p->d_series, p->d_seg_off,
-      static_cast<int>(p->n_base), p->seg_len, d_sel);
+      static_cast<int>(p->n_base), p->seg_len, d_sel, 0);
 }
 
 int normalise_smem(pulscan_plan p, int *bins_out) {
@@ -982,24 +1063,18 @@ int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, fl
   float4 *st4 = d_stats ? reinterpret_cast<float4 *>(d_stats) : reinterpret_cast<float4 *>(p->d_stats);
   int nt = 0, k = 0;
   lean_shape(p, &nt, &k);
-  if (nt == 1024) {
-    launch_lean<1024, 17>(p, d_spec, d_power, st4, d_sel, s);
-  } else if (nt > 0) {
-    switch (k) {
-      case 1: launch_lean<kNormThreads, 1>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 2: launch_lean<kNormThreads, 2>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 3: launch_lean<kNormThreads, 3>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 4: launch_lean<kNormThreads, 4>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 5: launch_lean<kNormThreads, 5>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 6: launch_lean<kNormThreads, 6>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 8: launch_lean<kNormThreads, 8>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 9: launch_lean<kNormThreads, 9>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 12: launch_lean<kNormThreads, 12>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 16: launch_lean<kNormThreads, 16>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 17: launch_lean<kNormThreads, 17>(p, d_spec, d_power, st4, d_sel, s); break;
-      case 24: launch_lean<kNormThreads, 24>(p, d_spec, d_power, st4, d_sel, s); break;
-      default: launch_lean<kNormThreads, 32>(p, d_spec, d_power, st4, d_sel, s); break;
-    }
+  switch (nt * 100 + k) {
+    case 25601: launch_lean<256, 1>(p, d_spec, d_power, st4, d_sel, s); break;
+    case 25602: launch_lean<256, 2>(p, d_spec, d_power, st4, d_sel, s); break;
+    case 25604: launch_lean<256, 4>(p, d_spec, d_power, st4, d_sel, s); break;
+    case 25606: launch_lean<256, 6>(p, d_spec, d_power, st4, d_sel, s); break;
+    case 25608: launch_lean<256, 8>(p, d_spec, d_power, st4, d_sel, s); break;
+    case 25612: launch_lean<256, 12>(p, d_spec, d_power, st4, d_sel, s); break;
+    case 25616: launch_lean<256, 16>(p, d_spec, d_power, st4, d_sel, s); break;
+    case 102408: launch_lean<1024, 8>(p, d_spec, d_power, st4, d_sel, s); break;
+    case 102412: launch_lean<1024, 12>(p, d_spec, d_power, st4, d_sel, s); break;
+    case 102416: launch_lean<1024, 16>(p, d_spec, d_power, st4, d_sel, s); break;
+    default: nt = 0; break;
   }
   if (nt > 0) {
     PS_CUDA(cudaGetLastError());

@@ -137,3 +137,19 @@ def test_middle_pair_split_over_two_crowded_buckets(pkg, n, seg_len):
         im = rng.permutation(half) * (1.0 + 1e-4 * rng.random(k))
         spec[lo:hi] = re + 1j * im
     _check(*_run(pkg, spec, n, seg_len), seg_len)
+
+
+@pytest.mark.parametrize("n,seg_len", [(1 << 14, 2048), (1 << 15, 4096)])
+def test_tight_cluster_far_from_zero(pkg, n, seg_len):
+    """Components in narrow clusters far from zero (1e6 + 0.1 noise, -3e5 +
+    0.05 noise), every other block: the value-bucket offset magic - lo s is
+    then far beyond integer resolution in FP32, so those blocks must take the
+    exact multi-level select, while their neighbours keep the fast one."""
+    m = n // 2 + 1
+    rng = np.random.default_rng(13)
+    spec = _gauss(m, 14)
+    for i, (lo, hi) in enumerate(onorm.block_bounds(m, seg_len)):
+        if i % 2 == 1:
+            k = hi - lo
+            spec[lo:hi] = (1e6 + 0.1 * rng.standard_normal(k)) + 1j * (-3e5 + 0.05 * rng.standard_normal(k))
+    _check(*_run(pkg, spec, n, seg_len), seg_len)

@@ -322,7 +322,8 @@ def workload_text(name):
 
 # ------------------------------------------------------------------ GPU arm
 def run_batched(torch, pkg, synth, dev, stream, steps):
-    """512 uneven DM-trial series: one graph replay vs per-series launches of the same kernels."""
+    """512 uneven DM-trial series: one graph replay vs per-series launches of
+    the same kernels; also the graph pipelined over parts of the batch."""
     cfg = synth.WORKLOADS["batch_512"]
     w_max, seg_len, sigma = cfg["z_max"], cfg["segment_len"], cfg["sigma"]
     lengths = synth.batch_lengths(cfg["n_series"], cfg["lengths"])
@@ -367,11 +368,19 @@ def run_batched(torch, pkg, synth, dev, stream, steps):
     t_b = timed(batched, steps)
     n_cands = len(plan.candidates(stream=stream))
     t_s = timed(per_series, max(1, steps // 2))
+    # the same batch graph pipelined over parts of 2^26 bins (each part's FFT
+    # and normalisation on a high-priority stream beside the previous part's bank)
+    plan.set_pipeline(1 << 26)
+    parts = plan.pipeline_parts()
+    batched()
+    t_q = timed(batched, steps)
+    plan.set_pipeline(0)
     return {"workload": f"batch_512: 512 series, lengths U{{2^20..2^23}} (sum {sum(lengths)} samples, "
                         f"{bins} bins), 26 with a tone, z_max={w_max}, segment_len={seg_len}, sigma={sigma:g}",
             "dm_trials_per_s": len(lengths) / (t_b * 1e-3), "ms_per_batch": t_b,
             "per_series_dm_trials_per_s": len(lengths) / (t_s * 1e-3), "ms_per_series_loop": t_s,
             "ratio_batched_vs_per_series": t_s / t_b, "bin_widths_per_s": bins * w_max / (t_b * 1e-3) / 1e9,
+            "ms_per_batch_pipelined": t_q, "pipeline_parts": parts,
             "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "packed": tiling[2],
                             "by": "pulscan_plan_autotune"},
             "unit": "G bin-widths/s", "candidates": n_cands, "graph": True,

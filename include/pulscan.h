@@ -203,6 +203,29 @@ PULSCAN_API int pulscan_plan_tiling(pulscan_plan plan, int32_t *warps, int32_t *
  * packed 0 or 1).  Synchronises the device.  Errors: INVALID_ARG. */
 PULSCAN_API int pulscan_plan_set_tiling(pulscan_plan plan, int32_t warps, int32_t persistent, int32_t packed);
 
+/* Pipelined batch search (a schedule of Algorithm 4's search over many
+ * series; the results are those of the sequential path).  pulscan_search
+ * with use_graph = 1 on a plan of several series splits them into parts of
+ * about part_bins bins (consecutive series of one length, in layout order)
+ * and captures, per part, its R2C transform and normalisation on a
+ * high-priority side stream and its boxcar bank on the capture stream after
+ * them, so that the bank of one part overlaps the transform and the
+ * normalisation of the next; the deferred blocks and the finaliser follow
+ * the last part.  part_bins = 0 (the default) turns it off: the stages run
+ * one after another over the whole batch, which measured faster on GB300
+ * (the bank's CTAs hold every SM's registers, so the side stream's work
+ * cannot run beside it).  Plans with harmonic stages, the paper-GPU fidelity
+ * mode or blocks too large for the register normalisation kernel always run
+ * the stages in turn.  Builds one
+ * cuFFT plan per (length, series count) of the parts, with one shared work
+ * area; synchronises the device and drops the plan's captured graph.
+ * Errors: INVALID_ARG, NOMEM, CUDA. */
+PULSCAN_API int pulscan_plan_set_pipeline(pulscan_plan plan, int64_t part_bins);
+
+/* Number of parts a captured pulscan_search of the plan is pipelined over
+ * (0: it runs sequentially).  Errors: INVALID_ARG. */
+PULSCAN_API int pulscan_plan_pipeline_parts(pulscan_plan plan, int64_t *n_parts);
+
 /* A test of the search's bounded-wait path that faults nothing: arms the
  * plan's next boxcar search so that its bank kernel issues no copy into
  * its staging buffer and waits on that copy's barrier for limit_us

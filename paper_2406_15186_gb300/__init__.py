@@ -78,6 +78,8 @@ _SIGS = {
     "pulscan_plan_tiling": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32)]),
     "pulscan_plan_set_tiling": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "pulscan_plan_set_pipeline": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "pulscan_plan_pipeline_parts": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "pulscan_plan_test_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int32]),
     "pulscan_plan_thresholds": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pulscan_threshold_power": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -248,6 +250,15 @@ class Plan:
         """Pick the bank's warps per CTA and launch form by timing the search on d_power."""
         _check(load().pulscan_plan_autotune(self._h, _ptr(d_power), _stream(stream)))
         return self.tiling()
+
+    def set_pipeline(self, part_bins):
+        """Parts of about part_bins bins for the pipelined captured search (0: off)."""
+        _check(load().pulscan_plan_set_pipeline(self._h, int(part_bins)))
+
+    def pipeline_parts(self):
+        n = ctypes.c_int64(0)
+        _check(load().pulscan_plan_pipeline_parts(self._h, ctypes.byref(n)))
+        return int(n.value)
 
     def set_tiling(self, warps, persistent=-1, packed=0):
         _check(load().pulscan_plan_set_tiling(self._h, int(warps), int(persistent), int(packed)))

@@ -560,7 +560,7 @@ __device__ __forceinline__ uint32_t sm_id() {
 }
 
 // The bank over all tiles.  With tile_ctr == nullptr every CTA takes tile
-// blockIdx.x.  Otherwise the launch is persistent (a few CTAs per SM): the
+// tile_base + blockIdx.x.  Otherwise the launch is persistent (a few CTAs per SM): the
 // tiles are split into n_ranges contiguous ranges [range_lo[r],
 // range_lo[r + 1]), one per SM, each with a claim counter in tile_ctr
 // (zeroed before the launch).  A CTA claims tiles from the range of the SM
@@ -580,10 +580,10 @@ __global__ void __launch_bounds__(kMaxThreads, kPacked ? 3 : kMinBlocks) boxcar_
     unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty, uint32_t *__restrict__ counters,
     unsigned long long *__restrict__ items, float *__restrict__ snaps, uint32_t item_cap, int tile_bins,
     int buf_len, uint32_t *__restrict__ tile_ctr, const int64_t *__restrict__ range_lo, int n_ranges, int groups,
-    uint32_t wait_test) {
+    uint32_t wait_test, int64_t tile_base) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (tile_ctr == nullptr) {
-    boxcar_tile<kSearch, kPacked>(blockIdx.x, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all,
+    boxcar_tile<kSearch, kPacked>(tile_base + blockIdx.x, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all,
                                   thrb_all, slots, dirty, counters, items, snaps, item_cap, tile_bins, buf_len, groups,
                                   wait_test);
     return;
@@ -1036,6 +1036,52 @@ int prepare_bank(pulscan_plan p) {
   return PULSCAN_OK;
 }
 
+// The deferred blocks the bank left in the item list (after every bank launch
+// of the search).
+int launch_deferred(pulscan_plan p, const float *d_power, cudaStream_t s) {
+  const int tile_bins = search_tile_bins(p->search_warps, p->search_groups);
+  const uint32_t cap = static_cast<uint32_t>(p->item_cap);
+  if (p->seg_len >= 2 * kR)
+    deferred_kernel<<<p->defer_grid, kDeferThreads, 0, s>>>(
+        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+        p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
+  else
+    deferred_small_kernel<<<p->defer_grid, 128, 0, s>>>(
+        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+        p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
+  PS_CUDA(cudaGetLastError());
+  return PULSCAN_OK;
+}
+
+// The search bank over tiles [tile_lo, tile_lo + n_tiles) only, one CTA per
+// tile (a part of a pipelined batch: its deferred blocks wait for
+// launch_deferred after the last part).
+int launch_search_tiles(pulscan_plan p, const float *d_power, int64_t tile_lo, int64_t n_tiles, cudaStream_t s) {
+  if (n_tiles <= 0) return PULSCAN_OK;
+  if (n_tiles > 0x7fffffffLL) return fail(PULSCAN_ERR_UNSUPPORTED, "too many search tiles");
+  int buf_len = 0;
+  const int groups = p->search_groups;
+  const int smem = search_smem_bytes(p->z_max, p->search_warps, groups, &buf_len);
+  const int tile_bins = search_tile_bins(p->search_warps, groups);
+  const uint32_t cap = static_cast<uint32_t>(p->item_cap);
+  const int rc = groups == 2 ? ensure_smem(boxcar_kernel<true, true>, smem, g_lim_search2)
+                             : ensure_smem(boxcar_kernel<true, false>, smem, g_lim_search);
+  if (rc) return rc;
+  const dim3 grid(static_cast<unsigned>(n_tiles)), block(32 * p->search_warps);
+  if (groups == 2)
+    boxcar_kernel<true, true><<<grid, block, smem, s>>>(
+        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+        p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
+        tile_bins, buf_len, nullptr, nullptr, 1, groups, 0u, tile_lo);
+  else
+    boxcar_kernel<true, false><<<grid, block, smem, s>>>(
+        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+        p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
+        tile_bins, buf_len, nullptr, nullptr, 1, groups, 0u, tile_lo);
+  PS_CUDA(cudaGetLastError());
+  return PULSCAN_OK;
+}
+
 static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaStream_t s) {
   int buf_len = 0;
   const int groups = p->search_groups;
@@ -1066,30 +1112,23 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
       boxcar_kernel<true, true><<<grid, block, smem, s>>>(
           d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
           p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
-          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test);
+          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test, 0);
     else
       boxcar_kernel<true, false><<<grid, block, smem, s>>>(
           d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
           p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
-          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test);
+          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test, 0);
     PS_CUDA(cudaGetLastError());
     record(p, 5, s);
     record(p, 6, s);
-    if (p->seg_len >= 2 * kR)
-      deferred_kernel<<<p->defer_grid, kDeferThreads, 0, s>>>(
-          d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
-          p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
-    else
-      deferred_small_kernel<<<p->defer_grid, 128, 0, s>>>(
-          d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
-          p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
-    PS_CUDA(cudaGetLastError());
+    rc = launch_deferred(p, d_power, s);
+    if (rc) return rc;
     record(p, 7, s);
   } else {
     boxcar_kernel<false, false><<<grid, block, smem, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
         p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, 0u,
-        tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, 0u);
+        tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, 0u, 0);
   }
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
@@ -1110,7 +1149,7 @@ int launch_segmax_raw(const float *d_power, const SeriesDev *d_series, const int
   if (rc) return rc;
   boxcar_kernel<false, false><<<static_cast<unsigned>(tiles), 32 * warps, smem, s>>>(
       d_power, d_series, d_tile_off, 1, W, seg_len, nullptr, nullptr, d_slots, nullptr, d_counters, nullptr,
-      nullptr, 0u, search_tile_bins(warps, 1), buf_len, nullptr, nullptr, 1, 1, 0u);
+      nullptr, 0u, search_tile_bins(warps, 1), buf_len, nullptr, nullptr, 1, 1, 0u, 0);
   PS_CUDA(cudaGetLastError());
   unpack_kernel<<<1024, 256, 0, s>>>(d_slots, n_slots, d_max, d_argmax);
   PS_CUDA(cudaGetLastError());

@@ -100,7 +100,16 @@ struct FftClass {
 struct GraphCache {
   const void *x = nullptr, *spec = nullptr, *power = nullptr;
   cudaStream_t capture = nullptr;   // plan-owned stream the graph is captured on
+  cudaStream_t side = nullptr;      // high-priority stream of a pipelined capture (FFT + normalisation)
+  std::vector<cudaEvent_t> ev;      // fork / join events of a pipelined capture
   cudaGraphExec_t exec = nullptr;
+};
+
+// A part of a pipelined batch: layout series [s_lo, s_hi), all of one length,
+// transformed by chunk_fft[fft].
+struct Chunk {
+  int64_t s_lo, s_hi;
+  int fft;
 };
 
 }  // namespace ps
@@ -165,6 +174,11 @@ struct pulscan_plan_s {
   cudaEvent_t ev[14] = {};
   bool ran[7] = {};
   ps::GraphCache graph;
+  // pipelined batch (pulscan_plan_set_pipeline): parts of about pipe_bins bins
+  int64_t pipe_bins = 0;           // 0: off
+  std::vector<ps::Chunk> chunks;
+  std::vector<ps::FftClass> chunk_fft;   // R2C plans per (length, series count) of the parts
+  void *d_fft_work = nullptr;      // their shared work area (the parts' transforms run one at a time)
 };
 
 namespace ps {
@@ -195,4 +209,12 @@ int launch_segmax_raw(const float *d_power, const SeriesDev *d_series, const int
                       int warps, int W, int seg_len, unsigned long long *d_slots, uint32_t *d_counters,
                       int64_t n_slots, float *d_max, uint64_t *d_argmax, cudaStream_t s);
 int prepare_normalise(pulscan_plan p);
+// pipelined batch parts: normalisation of segments [seg_lo, seg_lo + n_seg)
+// (register kernel only), the search bank over tiles [tile_lo, tile_lo +
+// n_tiles), and the deferred blocks after the last part
+bool normalise_range_ok(pulscan_plan p);
+int launch_normalise_range(pulscan_plan p, const float *d_spec, float *d_power, int64_t seg_lo, int64_t n_seg,
+                           cudaStream_t s);
+int launch_search_tiles(pulscan_plan p, const float *d_power, int64_t tile_lo, int64_t n_tiles, cudaStream_t s);
+int launch_deferred(pulscan_plan p, const float *d_power, cudaStream_t s);
 }  // namespace ps

@@ -1023,11 +1023,14 @@ constexpr int lean_smem() {
                                                                           : sizeof(SelSharedT<NT>));
 }
 
+// Segments [seg_lo, seg_lo + n_seg) of the series (all of them by default).
 template <int NT, int K>
-void launch_lean(pulscan_plan p, const float *d_spec, float *d_power, float4 *st4, float *d_sel, cudaStream_t s) {
-  normalise_lean_kernel<NT, K><<<static_cast<unsigned>(p->base_seg), NT, lean_smem<NT>(), s>>>(
+void launch_lean(pulscan_plan p, const float *d_spec, float *d_power, float4 *st4, float *d_sel, cudaStream_t s,
+                 int64_t seg_lo = 0, int64_t n_seg = -1) {
+  if (n_seg < 0) n_seg = p->base_seg;
+  normalise_lean_kernel<NT, K><<<static_cast<unsigned>(n_seg), NT, lean_smem<NT>(), s>>>(
       reinterpret_cast<const float2 *>(d_spec), d_power, st4, p->d_series, p->d_seg_off,
-      static_cast<int>(p->n_base), p->seg_len, d_sel, 0);
+      static_cast<int>(p->n_base), p->seg_len, d_sel, seg_lo);
 }
 
 int normalise_smem(pulscan_plan p, int *bins_out) {
@@ -1043,11 +1046,52 @@ int normalise_smem(pulscan_plan p, int *bins_out) {
   return 128 + static_cast<int>((sizeof(SelShared) + 127) & ~size_t(127)) + 8 * bins + 4 * store;
 }
 
+static int dispatch_lean(pulscan_plan p, int nt, int k, const float *d_spec, float *d_power, float4 *st4,
+                         float *d_sel, cudaStream_t s, int64_t seg_lo, int64_t n_seg) {
+  switch (nt * 100 + k) {
+  case 25601: launch_lean<256, 1>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 25602: launch_lean<256, 2>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 25604: launch_lean<256, 4>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 25606: launch_lean<256, 6>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 25608: launch_lean<256, 8>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 25612: launch_lean<256, 12>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 25616: launch_lean<256, 16>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 102408: launch_lean<1024, 8>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 102412: launch_lean<1024, 12>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 102416: launch_lean<1024, 16>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  default: return 0;
+  }
+  return nt;
+}
+
 }  // namespace
 
 SmemLimit g_lim_norm;
 
 int prepare_normalise(pulscan_plan p) { return ensure_smem(normalise_kernel, normalise_smem(p, nullptr), g_lim_norm); }
+
+bool normalise_range_ok(pulscan_plan p) {
+  int nt = 0, k = 0;
+  lean_shape(p, &nt, &k);
+  return nt > 0 && p->fidelity != PULSCAN_FIDELITY_PAPER_GPU;
+}
+
+// Segments [seg_lo, seg_lo + n_seg) only, with the lean kernel (a part of a
+// pipelined batch); PULSCAN_ERR_UNSUPPORTED where the plan's blocks need the
+// staged kernel or another mode.
+int launch_normalise_range(pulscan_plan p, const float *d_spec, float *d_power, int64_t seg_lo, int64_t n_seg,
+                           cudaStream_t s) {
+  if (p->fidelity == PULSCAN_FIDELITY_PAPER_GPU || n_seg > 0x7fffffffLL)
+    return fail(PULSCAN_ERR_UNSUPPORTED, "no range launch in this mode");
+  if (n_seg <= 0) return PULSCAN_OK;
+  int nt = 0, k = 0;
+  lean_shape(p, &nt, &k);
+  if (nt == 0 || dispatch_lean(p, nt, k, d_spec, d_power, reinterpret_cast<float4 *>(p->d_stats), nullptr, s, seg_lo,
+                               n_seg) == 0)
+    return fail(PULSCAN_ERR_UNSUPPORTED, "blocks too large for the register kernel");
+  PS_CUDA(cudaGetLastError());
+  return PULSCAN_OK;
+}
 
 int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, cudaStream_t s) {
   return launch_normalise_sel(p, d_spec, d_power, d_stats, nullptr, s);
@@ -1063,19 +1107,7 @@ int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, fl
   float4 *st4 = d_stats ? reinterpret_cast<float4 *>(d_stats) : reinterpret_cast<float4 *>(p->d_stats);
   int nt = 0, k = 0;
   lean_shape(p, &nt, &k);
-  switch (nt * 100 + k) {
-    case 25601: launch_lean<256, 1>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 25602: launch_lean<256, 2>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 25604: launch_lean<256, 4>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 25606: launch_lean<256, 6>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 25608: launch_lean<256, 8>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 25612: launch_lean<256, 12>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 25616: launch_lean<256, 16>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 102408: launch_lean<1024, 8>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 102412: launch_lean<1024, 12>(p, d_spec, d_power, st4, d_sel, s); break;
-    case 102416: launch_lean<1024, 16>(p, d_spec, d_power, st4, d_sel, s); break;
-    default: nt = 0; break;
-  }
+  nt = dispatch_lean(p, nt, k, d_spec, d_power, st4, d_sel, s, 0, -1);
   if (nt > 0) {
     PS_CUDA(cudaGetLastError());
     return PULSCAN_OK;

@@ -116,6 +116,16 @@ static int upload_thresholds(pulscan_plan p) {
   return PULSCAN_OK;
 }
 
+static void free_chunks(pulscan_plan p) {
+  for (auto &f : p->chunk_fft)
+    if (f.handle) cufftDestroy(f.handle);
+  p->chunk_fft.clear();
+  p->chunks.clear();
+  if (p->d_fft_work) cudaFree(p->d_fft_work);
+  p->d_fft_work = nullptr;
+  p->pipe_bins = 0;
+}
+
 static void free_plan(pulscan_plan p) {
   if (!p) return;
   for (auto &f : p->fft)
@@ -130,8 +140,12 @@ static void free_plan(pulscan_plan p) {
     if (q) cudaFree(q);
   for (auto &e : p->ev)
     if (e) cudaEventDestroy(e);
+  free_chunks(p);
+  for (auto &e : p->graph.ev)
+    if (e) cudaEventDestroy(e);
   if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
   if (p->graph.capture) cudaStreamDestroy(p->graph.capture);
+  if (p->graph.side) cudaStreamDestroy(p->graph.side);
   delete p;
 }
 
@@ -200,6 +214,71 @@ static int relayout_tiles(pulscan_plan p, int warps, int groups) {
     p->graph.exec = nullptr;
   }
   return rc;
+}
+
+// Parts of a pipelined batch: consecutive series (layout order) of one length,
+// about `bins` bins each, with one R2C plan per (length, series count); the
+// plans share one work area, since the parts' transforms run one after
+// another on one stream.  Fewer than two parts: no pipeline.
+static int build_chunks(pulscan_plan p, int64_t bins) {
+  free_chunks(p);
+  if (p->graph.exec) {
+    cudaGraphExecDestroy(p->graph.exec);
+    p->graph.exec = nullptr;
+  }
+  if (bins <= 0 || p->numharm != 1) return PULSCAN_OK;
+  std::vector<Chunk> ch;
+  for (int64_t i = 0; i < p->n_base;) {
+    const int64_t n = p->series[i].n;
+    int64_t j = i, acc = 0;
+    while (j < p->n_base && p->series[j].n == n && (j == i || acc + p->series[j].m <= bins)) acc += p->series[j++].m;
+    ch.push_back(Chunk{i, j, -1});
+    i = j;
+  }
+  if (ch.size() < 2) return PULSCAN_OK;
+  size_t work_max = 0;
+  int rc = PULSCAN_OK;
+  for (auto &c : ch) {
+    const Series &s0 = p->series[c.s_lo];
+    const int count = static_cast<int>(c.s_hi - c.s_lo);
+    for (size_t k = 0; k < p->chunk_fft.size(); ++k)
+      if (p->chunk_fft[k].n == s0.n && p->chunk_fft[k].count == count) c.fft = static_cast<int>(k);
+    if (c.fft >= 0) continue;
+    FftClass f{};
+    f.n = s0.n;
+    f.count = count;
+    f.spec_stride = (s0.m + 31) / 32 * 32;
+    long long nn = f.n, inembed = f.n, onembed = f.spec_stride;
+    size_t work = 0;
+    cufftResult r = cufftCreate(&f.handle);
+    if (r == CUFFT_SUCCESS) r = cufftSetAutoAllocation(f.handle, 0);
+    if (r == CUFFT_SUCCESS)
+      r = cufftMakePlanMany64(f.handle, 1, &nn, &inembed, 1, f.n, &onembed, 1, f.spec_stride, CUFFT_R2C, count,
+                              &work);
+    if (r != CUFFT_SUCCESS) {
+      rc = cufft_fail(r, "cufftMakePlanMany64");
+      if (f.handle) cufftDestroy(f.handle);
+      break;
+    }
+    work_max = std::max(work_max, work);
+    c.fft = static_cast<int>(p->chunk_fft.size());
+    p->chunk_fft.push_back(f);
+  }
+  if (!rc && work_max > 0 && cudaMalloc(&p->d_fft_work, work_max) != cudaSuccess) {
+    cudaGetLastError();
+    rc = fail(PULSCAN_ERR_NOMEM, "cuFFT work area");
+  }
+  for (size_t k = 0; !rc && k < p->chunk_fft.size(); ++k) {
+    const cufftResult r = cufftSetWorkArea(p->chunk_fft[k].handle, p->d_fft_work);
+    if (r != CUFFT_SUCCESS) rc = cufft_fail(r, "cufftSetWorkArea");
+  }
+  if (rc) {
+    free_chunks(p);
+    return rc;
+  }
+  p->chunks = ch;
+  p->pipe_bins = bins;
+  return PULSCAN_OK;
 }
 
 static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_series, int32_t z_max,
@@ -719,6 +798,76 @@ int pulscan_segment_maxima(pulscan_plan p, const float *d_power, float *d_max, u
   return launch_segmax(p, d_power, d_max, d_argmax, reinterpret_cast<cudaStream_t>(stream));
 }
 
+// A captured search of a batch runs pipelined: parts of about pipe_bins
+// bins (series of one length), whose R2C transform and normalisation go on a
+// high-priority side stream while the bank runs the previous part on the
+// capture stream, so the memory-bound transforms and the latency-bound
+// selects overlap the FP32-add-bound bank; the deferred blocks and the
+// finaliser follow the last part.
+static bool pipelined(pulscan_plan p) {
+  return p->pipe_bins > 0 && p->chunks.size() >= 2 && p->numharm == 1 && p->fidelity == PULSCAN_FIDELITY_EXACT &&
+         normalise_range_ok(p);
+}
+
+// Stream and events of a pipelined capture (created before the capture).
+static int prepare_pipeline(pulscan_plan p) {
+  GraphCache &g = p->graph;
+  if (!g.side) {
+    int least = 0, greatest = 0;
+    PS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    PS_CUDA(cudaStreamCreateWithPriority(&g.side, cudaStreamNonBlocking, greatest));
+  }
+  while (g.ev.size() < p->chunks.size() + 1) {
+    cudaEvent_t e = nullptr;
+    PS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    g.ev.push_back(e);
+  }
+  return PULSCAN_OK;
+}
+
+// The pipelined search, enqueued on the capture stream `a` (and the side
+// stream, forked from and joined back into `a`).
+static int enqueue_pipelined(pulscan_plan p, const float *d_x, float *d_spec, float *d_power, cudaStream_t a) {
+  GraphCache &g = p->graph;
+  PS_CUDA(cudaMemsetAsync(p->d_counters, 0, (4 + static_cast<size_t>(p->n_ranges)) * sizeof(uint32_t), a));
+  PS_CUDA(cudaEventRecord(g.ev[0], a));
+  PS_CUDA(cudaStreamWaitEvent(g.side, g.ev[0], 0));
+  const int64_t ns = static_cast<int64_t>(p->series.size());
+  for (size_t i = 0; i < p->chunks.size(); ++i) {
+    const Chunk &c = p->chunks[i];
+    const Series &s0 = p->series[c.s_lo];
+    const FftClass &f = p->chunk_fft[c.fft];
+    cufftResult r = cufftSetStream(f.handle, g.side);
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecR2C(f.handle, const_cast<cufftReal *>(d_x + s0.x_off),
+                       reinterpret_cast<cufftComplex *>(d_spec) + s0.spec_off);
+    if (r != CUFFT_SUCCESS) return cufft_fail(r, "cufftExecR2C");
+    const int64_t seg_hi = c.s_hi < p->n_base ? p->series[c.s_hi].seg_off : p->base_seg;
+    int rc = launch_normalise_range(p, d_spec, d_power, s0.seg_off, seg_hi - s0.seg_off, g.side);
+    if (rc) return rc;
+    PS_CUDA(cudaEventRecord(g.ev[i + 1], g.side));
+    PS_CUDA(cudaStreamWaitEvent(a, g.ev[i + 1], 0));
+    const int64_t tile_hi = c.s_hi < ns ? p->series[c.s_hi].tile_off : p->total_tiles;
+    rc = launch_search_tiles(p, d_power, s0.tile_off, tile_hi - s0.tile_off, a);
+    if (rc) return rc;
+  }
+  int rc = launch_deferred(p, d_power, a);
+  if (!rc) rc = launch_finalize(p, a);
+  return rc;
+}
+
+int pulscan_plan_set_pipeline(pulscan_plan p, int64_t part_bins) {
+  if (!p || part_bins < 0) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
+  PS_CUDA(cudaDeviceSynchronize());
+  return build_chunks(p, part_bins);
+}
+
+int pulscan_plan_pipeline_parts(pulscan_plan p, int64_t *n_parts) {
+  if (!p || !n_parts) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  *n_parts = pipelined(p) ? static_cast<int64_t>(p->chunks.size()) : 0;
+  return PULSCAN_OK;
+}
+
 int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_power, int use_graph,
                    pulscan_stream stream) {
   if (!p || !d_x || !d_spec || !d_power) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
@@ -743,10 +892,20 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
     // with timing on, the stage events are captured as event-record nodes and
     // re-recorded by every launch of the graph
     const pulscan_stream cs = reinterpret_cast<pulscan_stream>(g.capture);
+    const bool pipe = pipelined(p);
+    if (pipe) {
+      const int rp = prepare_pipeline(p);
+      if (rp) return rp;
+    }
     PS_CUDA(cudaStreamBeginCapture(g.capture, cudaStreamCaptureModeThreadLocal));
-    int rc = pulscan_rfft(p, d_x, d_spec, cs);
-    if (!rc) rc = pulscan_power_normalise(p, d_spec, d_power, nullptr, cs);
-    if (!rc) rc = pulscan_boxcar_search(p, d_power, cs);
+    int rc = PULSCAN_OK;
+    if (pipe) {
+      rc = enqueue_pipelined(p, d_x, d_spec, d_power, g.capture);
+    } else {
+      rc = pulscan_rfft(p, d_x, d_spec, cs);
+      if (!rc) rc = pulscan_power_normalise(p, d_spec, d_power, nullptr, cs);
+      if (!rc) rc = pulscan_boxcar_search(p, d_power, cs);
+    }
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(g.capture, &graph);
     if (rc) {
@@ -754,7 +913,9 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
       return rc;
     }
     if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
-    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    // the side stream's priority is kept per node (its parts start first on SMs that free up)
+    const cudaError_t ei =
+        cudaGraphInstantiateWithFlags(&g.exec, graph, pipe ? cudaGraphInstantiateFlagUseNodePriority : 0);
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate");
     g.x = d_x;

@@ -165,6 +165,51 @@ def test_batch_uneven_lengths(pkg):
                                 parity.n_trials_of(m, w_max), series=i)
 
 
+def test_batch_pipelined_graph_matches_oracle_and_sequential(pkg):
+    """The captured batch search, pipelined over parts of a few series (each
+    part's transform and normalisation on the side stream, its bank after
+    them), gives the oracle's maxima and candidates and exactly the records of
+    the stages run one after another."""
+    lengths = [1 << 13, 1 << 15, 1 << 12, 1 << 14, 1 << 13, 6000, 1 << 15, 1 << 14, 1 << 12]
+    w_max, seg_len, sigma = 40, 512, 3.0
+    xs = [_series(n, seed=300 + i) for i, n in enumerate(lengths)]
+    plan = pkg.Plan(lengths=lengths, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    plan.set_pipeline(10000)
+    assert plan.pipeline_parts() >= 6
+    xo, so, po, go = plan.offsets()
+    x_all = np.zeros(plan.x_floats, dtype=np.float32)
+    for i, x in enumerate(xs):
+        x_all[xo[i]: xo[i] + len(x)] = x
+    piped = parity.run_gpu(plan, x_all, stats=True, use_graph=True)
+    seq = parity.run_gpu(plan, x_all, stats=True, use_graph=False)
+    # a part's transform may round differently from the whole length class's
+    for i, n in enumerate(lengths):
+        m = n // 2 + 1
+        a = parity.spectrum_complex(piped["spec"], so[i], m)
+        b = parity.spectrum_complex(seq["spec"], so[i], m)
+        assert np.linalg.norm(a - b) <= 1e-6 * np.log2(n) * np.linalg.norm(b)
+    # on the same spectrum, the stages in turn give the pipelined power and records exactly
+    d_spec = torch.from_numpy(piped["spec"]).cuda()
+    d_power = torch.zeros(plan.power_floats, device="cuda")
+    plan.power_normalise(d_spec, d_power)
+    plan.boxcar_search(d_power)
+    again = plan.candidates()
+    assert np.array_equal(d_power.cpu().numpy(), piped["power"])
+    key = ["series", "bin", "width"]
+    assert np.array_equal(np.sort(piped["cands"], order=key), np.sort(again, order=key))
+    for i, n in enumerate(lengths):
+        m = n // 2 + 1
+        p = piped["power"][po[i]: po[i] + m].astype(np.float64)
+        rows = slice(go[i], go[i] + max(1, m // seg_len))
+        parity.check_normalise(parity.spectrum_complex(piped["spec"], so[i], m), piped["power"][po[i]: po[i] + m],
+                               piped["stats"][rows], seg_len)
+        mx_ref, am_ref = parity.check_maxima(p, piped["mx"][rows], piped["am"][rows], w_max, seg_len)
+        parity.check_candidates(piped["cands"], p, mx_ref, am_ref, w_max, seg_len, sigma,
+                                parity.n_trials_of(m, w_max), series=i)
+    plan.set_pipeline(0)
+    assert plan.pipeline_parts() == 0
+
+
 def test_deferred_overflow_falls_back_to_inline_exact(pkg):
     """With no room for deferred blocks every flagged block is inspected by its own warp."""
     n, w_max, seg_len, sigma = 1 << 16, 100, 1024, 3.0

@@ -375,12 +375,17 @@ def run_batched(torch, pkg, synth, dev, stream, steps):
     batched()
     t_q = timed(batched, steps)
     plan.set_pipeline(0)
+    # and with normalisation and bank fused
+    plan.set_fused(1)
+    batched()
+    t_f = timed(batched, steps)
+    plan.set_fused(0)
     return {"workload": f"batch_512: 512 series, lengths U{{2^20..2^23}} (sum {sum(lengths)} samples, "
                         f"{bins} bins), 26 with a tone, z_max={w_max}, segment_len={seg_len}, sigma={sigma:g}",
             "dm_trials_per_s": len(lengths) / (t_b * 1e-3), "ms_per_batch": t_b,
             "per_series_dm_trials_per_s": len(lengths) / (t_s * 1e-3), "ms_per_series_loop": t_s,
             "ratio_batched_vs_per_series": t_s / t_b, "bin_widths_per_s": bins * w_max / (t_b * 1e-3) / 1e9,
-            "ms_per_batch_pipelined": t_q, "pipeline_parts": parts,
+            "ms_per_batch_pipelined": t_q, "pipeline_parts": parts, "ms_per_batch_fused": t_f,
             "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "packed": tiling[2],
                             "by": "pulscan_plan_autotune"},
             "unit": "G bin-widths/s", "candidates": n_cands, "graph": True,
@@ -618,6 +623,34 @@ def time_single(torch, pkg, synth, dev, stream, flush, name, args, steps, warmup
     return res, plan, (d_x, d_spec, d_power)
 
 
+def time_fused(torch, plan, bufs, stream, flush, steps, sep_ms):
+    """The same search step with normalisation and bank fused (pulscan_plan_set_fused:
+    block statistics only, then P formed from the spectrum inside the bank and the
+    deferred blocks), as one CUDA graph per step, L2 flushed before each step;
+    against sep_ms, the separate stages' step."""
+    plan.set_fused(1)
+    step = lambda: plan.search(*bufs, use_graph=True, stream=stream)
+    for _ in range(3):
+        step()
+    ms = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    n_cands = len(plan.candidates(stream=stream))
+    plan.set_fused(0)
+    t = statistics.mean(ms)
+    return {"ms_per_step": t, "separate_ms_per_step": sep_ms, "ratio_separate_over_fused": sep_ms / t,
+            "candidates": n_cands, "kept": t < sep_ms,
+            "note": "fused normalise + boxcar (f4): statistics kernel, then the bank forms P from the spectrum; "
+                    "off by default where slower"}
+
+
 def rooflines(res, peak, n_sm, sm_max, name):
     """roofline (the bank kernel alone, its live events) and roofline_search
     (bank + deferred blocks + finaliser, the per-stage events) against the
@@ -777,6 +810,8 @@ def run_ours(args, rank, world, local):
                            "candidates": r["candidates"], "deferred_blocks": r["deferred_blocks"],
                            "bank_tiling": r["bank_tiling"], "roofline": b, "roofline_search": sr}
             if other == "single_2p23":
+                line[other]["fused"] = time_fused(torch, p2, bufs, stream, flush, max(5, args.steps // 2),
+                                                  r["ms_per_step"])
                 # f1-f3 on this series: harmonic sums, the paper-GPU fidelity
                 # mode, and the searched-width subsets
                 d_x2 = bufs[0]

@@ -222,6 +222,22 @@ PULSCAN_API int pulscan_plan_set_tiling(pulscan_plan plan, int32_t warps, int32_
  * Errors: INVALID_ARG, NOMEM, CUDA. */
 PULSCAN_API int pulscan_plan_set_pipeline(pulscan_plan plan, int64_t part_bins);
 
+/* Fused normalisation and search (§2.2.3 Eq. 8 and §2.2.5 / Algorithm 4 in
+ * one pass over the power): with on = 1, pulscan_search (with or without a
+ * graph) runs the R2C transform, then only the block statistics of Eq. 8
+ * (the exact medians and MADs, kept per segment as (med, 1 / (kappa MAD))
+ * pairs), then the boxcar bank, which forms every staged bin's power from
+ * the spectrum and its segment's pair as it stages its tile, and the
+ * deferred blocks likewise: P never goes to device memory, and d_power is
+ * neither read nor written.  The powers formed are bit-identical to
+ * pulscan_power_normalise's, so the candidates are those of the separate
+ * stages.  on = 0 (the default) restores the separate stages.  Only for the
+ * exact mode without harmonic stages and segments of at most 16385 bins
+ * (UNSUPPORTED otherwise); overrides the pipelined schedule.  Allocates 16
+ * bytes per segment on first use, synchronises the device and drops the
+ * plan's captured graph.  Errors: INVALID_ARG, UNSUPPORTED, NOMEM. */
+PULSCAN_API int pulscan_plan_set_fused(pulscan_plan plan, int32_t on);
+
 /* Number of parts a captured pulscan_search of the plan is pipelined over
  * (0: it runs sequentially).  Errors: INVALID_ARG. */
 PULSCAN_API int pulscan_plan_pipeline_parts(pulscan_plan plan, int64_t *n_parts);

@@ -79,6 +79,7 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_int32)]),
     "pulscan_plan_set_tiling": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "pulscan_plan_set_pipeline": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "pulscan_plan_set_fused": (ctypes.c_int, [_P, ctypes.c_int32]),
     "pulscan_plan_pipeline_parts": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "pulscan_plan_test_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int32]),
     "pulscan_plan_thresholds": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
@@ -254,6 +255,10 @@ class Plan:
     def set_pipeline(self, part_bins):
         """Parts of about part_bins bins for the pipelined captured search (0: off)."""
         _check(load().pulscan_plan_set_pipeline(self._h, int(part_bins)))
+
+    def set_fused(self, on):
+        """Fused normalisation + search in search(): P formed in the bank, d_power unused."""
+        _check(load().pulscan_plan_set_fused(self._h, int(bool(on))))
 
     def pipeline_parts(self):
         n = ctypes.c_int64(0)

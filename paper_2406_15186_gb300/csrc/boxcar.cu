@@ -399,13 +399,47 @@ __device__ __forceinline__ void packed_bank(const float *__restrict__ buf, const
 // one 33-bin group of each and adds both with packed instructions, in dump
 // mode the warp runs the two slices one after the other.  A virtual warp is
 // the unit of the deferred-block items either way.
+// The fused search (normalisation on the fly, Eq. 8): P of series bin k from
+// the spectrum and its segment's (med_re, 1 / (kappa MAD_re), med_im,
+// 1 / (kappa MAD_im)), the DC bin taken as 0 + 0i; the segment of bin k is
+// min(k / L, n_seg - 1).  Bit-identical to the normalisation kernel's P.
+__device__ __forceinline__ float fused_power(const float2 *__restrict__ spec, const float4 *__restrict__ norm,
+                                            const SeriesDev &S, int64_t k, int seg_len) {
+  const float2 x = (k == 0) ? make_float2(0.0f, 0.0f) : __ldg(spec + S.spec_off + k);
+  const uint32_t sg = min(static_cast<uint32_t>(k) / static_cast<uint32_t>(seg_len),
+                          static_cast<uint32_t>(S.n_seg - 1));
+  return power_of(x.x, x.y, __ldg(norm + S.seg_off + sg));
+}
+
+// buf[i] = P[t0 + i] for i < avail, 0 up to buf_len, formed from the
+// spectrum segment by segment (one statistics load per segment).
+__device__ __forceinline__ void stage_fused(float *buf, int buf_len, int avail, const SeriesDev &S, int64_t t0,
+                                            int seg_len, const float2 *__restrict__ spec,
+                                            const float4 *__restrict__ norm) {
+  const int64_t last = S.n_seg - 1;
+  int64_t seg = min64(t0 / seg_len, last);
+  for (int a = 0; a < avail; ++seg) {
+    const int64_t seg_end = (seg == last) ? S.m : (seg + 1) * seg_len;
+    const int b = static_cast<int>(min64(seg_end - t0, static_cast<int64_t>(avail)));
+    const float4 nrm = __ldg(norm + S.seg_off + seg);
+    for (int i = a + static_cast<int>(threadIdx.x); i < b; i += blockDim.x) {
+      const int64_t k = t0 + i;
+      const float2 x = (k == 0) ? make_float2(0.0f, 0.0f) : __ldg(spec + S.spec_off + k);
+      buf[i] = power_of(x.x, x.y, nrm);
+    }
+    a = b;
+  }
+  for (int i = avail + static_cast<int>(threadIdx.x); i < buf_len; i += blockDim.x) buf[i] = 0.0f;
+}
+
 template <bool kSearch, bool kPacked>
 __device__ __forceinline__ bool boxcar_tile(
     int64_t tile, unsigned char *smem_raw, const float *__restrict__ power, const SeriesDev *__restrict__ series,
     const int64_t *__restrict__ tile_off, int n_series, int W, int seg_len, const float *__restrict__ thr_all,
     const float *__restrict__ thrb_all, unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty,
     uint32_t *__restrict__ counters, unsigned long long *__restrict__ items, float *__restrict__ snaps,
-    uint32_t item_cap, int tile_bins, int buf_len, int groups, uint32_t wait_test) {
+    uint32_t item_cap, int tile_bins, int buf_len, int groups, uint32_t wait_test, const float2 *__restrict__ spec,
+    const float4 *__restrict__ norm) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   float *buf = reinterpret_cast<float *>(smem_raw + 128);
   const int nq33 = buf_len / kR;        // 33-bin block sums
@@ -423,6 +457,11 @@ __device__ __forceinline__ bool boxcar_tile(
   // a 16-byte multiple from a 16-byte aligned source; the rest by plain loads
   const int n_tma = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0u && avail > 0) ? (avail & ~3) : 0;
 
+  if (norm != nullptr) {
+    // fused: P formed from the spectrum while it is staged
+    stage_fused(buf, buf_len, avail, S, t0, seg_len, spec, norm);
+    __syncthreads();
+  } else {
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   // wait_test != 0 (a test of the timeout path): no copy is issued, so the
@@ -443,6 +482,7 @@ __device__ __forceinline__ bool boxcar_tile(
     return false;   // nothing else is in flight: the only copy is this one
   }
   __syncthreads();
+  }
 
   // block sums for the bounds: q11[j] = sum of 11 bins from 11 j,
   // q33[j] = sum of 33 bins from 33 j
@@ -580,12 +620,12 @@ __global__ void __launch_bounds__(kMaxThreads, kPacked ? 3 : kMinBlocks) boxcar_
     unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty, uint32_t *__restrict__ counters,
     unsigned long long *__restrict__ items, float *__restrict__ snaps, uint32_t item_cap, int tile_bins,
     int buf_len, uint32_t *__restrict__ tile_ctr, const int64_t *__restrict__ range_lo, int n_ranges, int groups,
-    uint32_t wait_test, int64_t tile_base) {
+    uint32_t wait_test, int64_t tile_base, const float2 *__restrict__ spec, const float4 *__restrict__ norm) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (tile_ctr == nullptr) {
     boxcar_tile<kSearch, kPacked>(tile_base + blockIdx.x, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all,
                                   thrb_all, slots, dirty, counters, items, snaps, item_cap, tile_bins, buf_len, groups,
-                                  wait_test);
+                                  wait_test, spec, norm);
     return;
   }
   int64_t *claim = reinterpret_cast<int64_t *>(smem_raw + 64);
@@ -631,7 +671,7 @@ __global__ void __launch_bounds__(kMaxThreads, kPacked ? 3 : kMinBlocks) boxcar_
     if (threadIdx.x == 0) mine = claim_home();
     if (!boxcar_tile<kSearch, kPacked>(tile, smem_raw, power, series, tile_off, n_series, W, seg_len, thr_all,
                                        thrb_all, slots, dirty, counters, items, snaps, item_cap, tile_bins, buf_len,
-                                       groups, wait_test))
+                                       groups, wait_test, spec, norm))
       return;
     __syncthreads();   // the tile's shared memory is free for the next one
   }
@@ -746,7 +786,8 @@ __global__ void __launch_bounds__(kDeferThreads, 8) deferred_kernel(
     int n_series, int W, int seg_len, const float *__restrict__ thr_all, unsigned long long *__restrict__ slots,
     uint32_t *__restrict__ dirty, const uint32_t *__restrict__ counters,
     const unsigned long long *__restrict__ items, const float *__restrict__ snaps, uint32_t item_cap,
-    int tile_bins) {
+    int tile_bins, const float2 *__restrict__ spec,
+    const float4 *__restrict__ norm) {
   __shared__ DeferShared sh;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t n_items = min(counters[0], item_cap);
@@ -774,7 +815,9 @@ __global__ void __launch_bounds__(kDeferThreads, 8) deferred_kernel(
 #pragma unroll
     for (int q = 0; q < kRegionLoads; ++q) {
       const int j = t + q * kDeferThreads;
-      ld_r[q] = (j < kRegion && r0 + j < S.m) ? __ldg(src + r0 + j) : 0.0f;
+      ld_r[q] = (j < kRegion && r0 + j < S.m)
+                    ? (norm != nullptr ? fused_power(spec, norm, S, r0 + j, seg_len) : __ldg(src + r0 + j))
+                    : 0.0f;
     }
 #pragma unroll
     for (int q = 0; q < kSnapLoads; ++q) ld_s[q] = sp[t + q * kDeferThreads];
@@ -954,7 +997,8 @@ __global__ void __launch_bounds__(128) deferred_small_kernel(
     int n_series, int W, int seg_len, const float *__restrict__ thr_all, unsigned long long *__restrict__ slots,
     uint32_t *__restrict__ dirty, const uint32_t *__restrict__ counters,
     const unsigned long long *__restrict__ items, const float *__restrict__ snaps, uint32_t item_cap,
-    int tile_bins) {
+    int tile_bins, const float2 *__restrict__ spec,
+    const float4 *__restrict__ norm) {
   __shared__ float region_all[4][kRegion];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float *region = region_all[warp];
@@ -971,7 +1015,8 @@ __global__ void __launch_bounds__(128) deferred_small_kernel(
     const int64_t r0 = t0 + wv * (32 * kR) + bi * kR + cx;
     const float *src = power + S.p_off;
     __syncwarp();
-    for (int j = lane; j < kRegion; j += 32) region[j] = (r0 + j < S.m) ? src[r0 + j] : 0.0f;
+    for (int j = lane; j < kRegion; j += 32)
+      region[j] = (r0 + j < S.m) ? (norm != nullptr ? fused_power(spec, norm, S, r0 + j, seg_len) : src[r0 + j]) : 0.0f;
     __syncwarp();
     const LaneCtx c = lane_ctx(S, t0, tile_bins, wv, lane, W, seg_len, slots, dirty);
     float s[kR];
@@ -1038,17 +1083,19 @@ int prepare_bank(pulscan_plan p) {
 
 // The deferred blocks the bank left in the item list (after every bank launch
 // of the search).
-int launch_deferred(pulscan_plan p, const float *d_power, cudaStream_t s) {
+int launch_deferred(pulscan_plan p, const float *d_power, cudaStream_t s, const float *d_spec) {
   const int tile_bins = search_tile_bins(p->search_warps, p->search_groups);
   const uint32_t cap = static_cast<uint32_t>(p->item_cap);
+  const float2 *spec = reinterpret_cast<const float2 *>(d_spec);
+  const float4 *norm = d_spec ? reinterpret_cast<const float4 *>(p->d_norm) : nullptr;
   if (p->seg_len >= 2 * kR)
     deferred_kernel<<<p->defer_grid, kDeferThreads, 0, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
-        p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
+        p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins, spec, norm);
   else
     deferred_small_kernel<<<p->defer_grid, 128, 0, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
-        p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins);
+        p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins, spec, norm);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }
@@ -1072,17 +1119,22 @@ int launch_search_tiles(pulscan_plan p, const float *d_power, int64_t tile_lo, i
     boxcar_kernel<true, true><<<grid, block, smem, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
         p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
-        tile_bins, buf_len, nullptr, nullptr, 1, groups, 0u, tile_lo);
+        tile_bins, buf_len, nullptr, nullptr, 1, groups, 0u, tile_lo, nullptr, nullptr);
   else
     boxcar_kernel<true, false><<<grid, block, smem, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
         p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
-        tile_bins, buf_len, nullptr, nullptr, 1, groups, 0u, tile_lo);
+        tile_bins, buf_len, nullptr, nullptr, 1, groups, 0u, tile_lo, nullptr, nullptr);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }
 
-static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaStream_t s) {
+// d_spec != nullptr: the fused search (P formed from d_spec and p->d_norm;
+// d_power is neither read nor written).
+static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaStream_t s,
+                       const float *d_spec = nullptr) {
+  const float2 *spec = reinterpret_cast<const float2 *>(d_spec);
+  const float4 *norm = d_spec ? reinterpret_cast<const float4 *>(p->d_norm) : nullptr;
   int buf_len = 0;
   const int groups = p->search_groups;
   const int smem = search_smem_bytes(p->z_max, p->search_warps, groups, &buf_len);
@@ -1112,23 +1164,23 @@ static int launch_bank(pulscan_plan p, const float *d_power, bool search, cudaSt
       boxcar_kernel<true, true><<<grid, block, smem, s>>>(
           d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
           p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
-          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test, 0);
+          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test, 0, spec, norm);
     else
       boxcar_kernel<true, false><<<grid, block, smem, s>>>(
           d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
           p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap,
-          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test, 0);
+          tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, wait_test, 0, spec, norm);
     PS_CUDA(cudaGetLastError());
     record(p, 5, s);
     record(p, 6, s);
-    rc = launch_deferred(p, d_power, s);
+    rc = launch_deferred(p, d_power, s, d_spec);
     if (rc) return rc;
     record(p, 7, s);
   } else {
     boxcar_kernel<false, false><<<grid, block, smem, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
         p->d_thresh, p->d_thresh_bound, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, 0u,
-        tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, 0u, 0);
+        tile_bins, buf_len, ctr, p->d_ranges, p->n_ranges, groups, 0u, 0, nullptr, nullptr);
   }
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
@@ -1149,7 +1201,7 @@ int launch_segmax_raw(const float *d_power, const SeriesDev *d_series, const int
   if (rc) return rc;
   boxcar_kernel<false, false><<<static_cast<unsigned>(tiles), 32 * warps, smem, s>>>(
       d_power, d_series, d_tile_off, 1, W, seg_len, nullptr, nullptr, d_slots, nullptr, d_counters, nullptr,
-      nullptr, 0u, search_tile_bins(warps, 1), buf_len, nullptr, nullptr, 1, 1, 0u, 0);
+      nullptr, 0u, search_tile_bins(warps, 1), buf_len, nullptr, nullptr, 1, 1, 0u, 0, nullptr, nullptr);
   PS_CUDA(cudaGetLastError());
   unpack_kernel<<<1024, 256, 0, s>>>(d_slots, n_slots, d_max, d_argmax);
   PS_CUDA(cudaGetLastError());
@@ -1160,8 +1212,8 @@ int launch_maxima_only(pulscan_plan p, const float *d_power, cudaStream_t s) {
   return launch_bank(p, d_power, false, s);   // tile claim counters zeroed with the others by the caller
 }
 
-int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s) {
-  return launch_bank(p, d_power, true, s);
+int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s, const float *d_spec) {
+  return launch_bank(p, d_power, true, s, d_spec);
 }
 
 int launch_segmax(pulscan_plan p, const float *d_power, float *d_max, uint64_t *d_argmax, cudaStream_t s) {

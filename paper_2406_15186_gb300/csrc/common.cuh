@@ -112,6 +112,22 @@ struct Chunk {
   int fft;
 };
 
+#ifdef __CUDACC__
+// The normalised power of Eq. 8 from a bin's deviations d = x - med of both
+// components and the block's 1 / (kappa MAD) pair: a = d_re inv_re,
+// b = d_im inv_im, P = (a^2 + b^2) / 2, every rounding fixed (no
+// contraction), so the normalisation and the fused bank form the same bits.
+__device__ __forceinline__ float power_of_dev(float d_re, float d_im, float inv_re, float inv_im) {
+  const float a = __fmul_rn(d_re, inv_re), b = __fmul_rn(d_im, inv_im);
+  return __fmul_rn(0.5f, __fmaf_rn(a, a, __fmul_rn(b, b)));
+}
+
+// The same from the bin itself and the block's (med_re, inv_re, med_im, inv_im).
+__device__ __forceinline__ float power_of(float re, float im, float4 nrm) {
+  return power_of_dev(__fsub_rn(re, nrm.x), __fsub_rn(im, nrm.z), nrm.y, nrm.w);
+}
+#endif
+
 }  // namespace ps
 
 struct pulscan_plan_s {
@@ -179,6 +195,10 @@ struct pulscan_plan_s {
   std::vector<ps::Chunk> chunks;
   std::vector<ps::FftClass> chunk_fft;   // R2C plans per (length, series count) of the parts
   void *d_fft_work = nullptr;      // their shared work area (the parts' transforms run one at a time)
+  // fused search (pulscan_plan_set_fused): per segment (med_re, 1 / (kappa
+  // MAD_re), med_im, 1 / (kappa MAD_im)); P is formed in the bank
+  bool fused = false;
+  float *d_norm = nullptr;
 };
 
 namespace ps {
@@ -189,7 +209,10 @@ int launch_normalise(pulscan_plan p, const float *d_spec, float *d_power, float 
 // [med_lo, med_hi, dev_lo, dev_hi] of Re then Im (8 floats) into d_sel
 int launch_normalise_sel(pulscan_plan p, const float *d_spec, float *d_power, float *d_stats, float *d_sel,
                          cudaStream_t s);
-int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s);
+// d_spec != nullptr: the fused search, P formed on the fly from the spectrum
+// and p->d_norm (launch_normalise_stats); d_power is then not used
+int launch_search(pulscan_plan p, const float *d_power, cudaStream_t s, const float *d_spec = nullptr);
+int launch_normalise_stats(pulscan_plan p, const float *d_spec, cudaStream_t s);
 int launch_finalize(pulscan_plan p, cudaStream_t s);
 int launch_harmonic_sums(pulscan_plan p, float *d_power, cudaStream_t s);   // stage spectra X_H
 // paper-GPU fidelity mode
@@ -216,5 +239,5 @@ bool normalise_range_ok(pulscan_plan p);
 int launch_normalise_range(pulscan_plan p, const float *d_spec, float *d_power, int64_t seg_lo, int64_t n_seg,
                            cudaStream_t s);
 int launch_search_tiles(pulscan_plan p, const float *d_power, int64_t tile_lo, int64_t n_tiles, cudaStream_t s);
-int launch_deferred(pulscan_plan p, const float *d_power, cudaStream_t s);
+int launch_deferred(pulscan_plan p, const float *d_power, cudaStream_t s, const float *d_spec = nullptr);
 }  // namespace ps

@@ -813,7 +813,7 @@ template <int NT, int K>
 __global__ void __launch_bounds__(NT, lean_min_blocks<NT, K>()) normalise_lean_kernel(
     const float2 *__restrict__ spec, float *__restrict__ power, float4 *__restrict__ stats,
     const SeriesDev *__restrict__ series, const int64_t *__restrict__ seg_off, int n_series, int seg_len,
-    float *__restrict__ sel, int64_t seg_base) {
+    float *__restrict__ sel, int64_t seg_base, float4 *__restrict__ norm) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   LeanShared<NT> &sh = *reinterpret_cast<LeanShared<NT> *>(smem_raw);
   SelSharedT<NT> &legacy = *reinterpret_cast<SelSharedT<NT> *>(smem_raw);   // the fallback's (same memory)
@@ -962,25 +962,21 @@ __global__ void __launch_bounds__(NT, lean_min_blocks<NT, K>()) normalise_lean_k
     inv[0] = 0.0f;
     inv[1] = 0.0f;
   }
-  float *out = power + S.p_off + b0;
-  if (full) {
+  // the power (unless only the statistics are wanted: power == nullptr)
+  if (power != nullptr) {
+    float *out = power + S.p_off + b0;
+    if (full) {
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-      const float a = v[j].x * inv[0], b = v[j].y * inv[1];
-      out[j * NT + t] = 0.5f * (a * a + b * b);
-    }
-  } else {
+      for (int j = 0; j < K; ++j) out[j * NT + t] = power_of_dev(v[j].x, v[j].y, inv[0], inv[1]);
+    } else {
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-      const float a = v[j].x * inv[0], b = v[j].y * inv[1];
-      if (j < nv) out[j * NT + t] = 0.5f * (a * a + b * b);
+      for (int j = 0; j < K; ++j)
+        if (j < nv) out[j * NT + t] = power_of_dev(v[j].x, v[j].y, inv[0], inv[1]);
     }
-  }
-  if (has_x) {
-    const float a = vx.x * inv[0], b = vx.y * inv[1];
-    out[kFull] = 0.5f * (a * a + b * b);
+    if (has_x) out[kFull] = power_of_dev(vx.x, vx.y, inv[0], inv[1]);
   }
   if (t == 0 && stats != nullptr) stats[g] = make_float4(med[0], mad[0], med[1], mad[1]);
+  if (t == 0 && norm != nullptr) norm[g] = make_float4(med[0], inv[0], med[1], inv[1]);
 }
 
 // Kernel shapes (threads, bins per thread) of the lean register kernel, by
@@ -1026,11 +1022,11 @@ constexpr int lean_smem() {
 // Segments [seg_lo, seg_lo + n_seg) of the series (all of them by default).
 template <int NT, int K>
 void launch_lean(pulscan_plan p, const float *d_spec, float *d_power, float4 *st4, float *d_sel, cudaStream_t s,
-                 int64_t seg_lo = 0, int64_t n_seg = -1) {
+                 int64_t seg_lo = 0, int64_t n_seg = -1, float4 *norm = nullptr) {
   if (n_seg < 0) n_seg = p->base_seg;
   normalise_lean_kernel<NT, K><<<static_cast<unsigned>(n_seg), NT, lean_smem<NT>(), s>>>(
       reinterpret_cast<const float2 *>(d_spec), d_power, st4, p->d_series, p->d_seg_off,
-      static_cast<int>(p->n_base), p->seg_len, d_sel, seg_lo);
+      static_cast<int>(p->n_base), p->seg_len, d_sel, seg_lo, norm);
 }
 
 int normalise_smem(pulscan_plan p, int *bins_out) {
@@ -1047,18 +1043,18 @@ int normalise_smem(pulscan_plan p, int *bins_out) {
 }
 
 static int dispatch_lean(pulscan_plan p, int nt, int k, const float *d_spec, float *d_power, float4 *st4,
-                         float *d_sel, cudaStream_t s, int64_t seg_lo, int64_t n_seg) {
+                         float *d_sel, cudaStream_t s, int64_t seg_lo, int64_t n_seg, float4 *norm = nullptr) {
   switch (nt * 100 + k) {
-  case 25601: launch_lean<256, 1>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
-  case 25602: launch_lean<256, 2>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
-  case 25604: launch_lean<256, 4>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
-  case 25606: launch_lean<256, 6>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
-  case 25608: launch_lean<256, 8>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
-  case 25612: launch_lean<256, 12>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
-  case 25616: launch_lean<256, 16>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
-  case 102408: launch_lean<1024, 8>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
-  case 102412: launch_lean<1024, 12>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
-  case 102416: launch_lean<1024, 16>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg); break;
+  case 25601: launch_lean<256, 1>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
+  case 25602: launch_lean<256, 2>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
+  case 25604: launch_lean<256, 4>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
+  case 25606: launch_lean<256, 6>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
+  case 25608: launch_lean<256, 8>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
+  case 25612: launch_lean<256, 12>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
+  case 25616: launch_lean<256, 16>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
+  case 102408: launch_lean<1024, 8>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
+  case 102412: launch_lean<1024, 12>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
+  case 102416: launch_lean<1024, 16>(p, d_spec, d_power, st4, d_sel, s, seg_lo, n_seg, norm); break;
   default: return 0;
   }
   return nt;
@@ -1088,6 +1084,22 @@ int launch_normalise_range(pulscan_plan p, const float *d_spec, float *d_power, 
   lean_shape(p, &nt, &k);
   if (nt == 0 || dispatch_lean(p, nt, k, d_spec, d_power, reinterpret_cast<float4 *>(p->d_stats), nullptr, s, seg_lo,
                                n_seg) == 0)
+    return fail(PULSCAN_ERR_UNSUPPORTED, "blocks too large for the register kernel");
+  PS_CUDA(cudaGetLastError());
+  return PULSCAN_OK;
+}
+
+// The block statistics alone, as (med_re, 1 / (kappa MAD_re), med_im,
+// 1 / (kappa MAD_im)) per segment into p->d_norm (both inverses 0 for a
+// degenerate block), for the fused search; the median / MAD pairs into
+// p->d_stats as usual.  Register kernel only.
+int launch_normalise_stats(pulscan_plan p, const float *d_spec, cudaStream_t s) {
+  if (!normalise_range_ok(p) || p->base_seg > 0x7fffffffLL)
+    return fail(PULSCAN_ERR_UNSUPPORTED, "blocks too large for the register kernel");
+  int nt = 0, k = 0;
+  lean_shape(p, &nt, &k);
+  if (dispatch_lean(p, nt, k, d_spec, nullptr, reinterpret_cast<float4 *>(p->d_stats), nullptr, s, 0, p->base_seg,
+                    reinterpret_cast<float4 *>(p->d_norm)) == 0)
     return fail(PULSCAN_ERR_UNSUPPORTED, "blocks too large for the register kernel");
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;

@@ -135,7 +135,8 @@ static void free_plan(pulscan_plan p) {
   void *ptrs[] = {p->d_series, p->d_tile_off, p->d_seg_off, p->d_thresh, p->d_thresh_bound, p->d_ln_trials,
                   p->d_stats,  p->d_slots,    p->d_dirty,   p->d_counters, p->d_cands,     p->own_x,
                   p->own_spec, p->own_power, p->d_items, p->d_snaps,    p->d_gtab,     p->d_x_off,
-                  p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec,   p->d_ranges,  p->d_searched, p->d_word_off, p->d_block_off};
+                  p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec,   p->d_ranges,  p->d_searched, p->d_word_off, p->d_block_off,
+                  p->d_norm};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (auto &e : p->ev)
@@ -572,7 +573,7 @@ int pulscan_plan_set_fidelity(pulscan_plan p, int32_t mode) {
   return PULSCAN_OK;
 }
 
-static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s);
+static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s, const float *d_spec = nullptr);
 
 int pulscan_plan_autotune(pulscan_plan p, const float *d_power, pulscan_stream stream) {
   if (!p || !d_power) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
@@ -721,7 +722,7 @@ int pulscan_power_normalise(pulscan_plan p, const float *d_spec, float *d_power,
   return rc;
 }
 
-static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s) {
+static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s, const float *d_spec) {
   PS_CUDA(cudaMemsetAsync(p->d_counters, 0, (4 + static_cast<size_t>(p->n_ranges)) * sizeof(uint32_t), s));
   if (p->fidelity == PULSCAN_FIDELITY_PAPER_GPU) {
     // every (segment, width) maximum, then the polynomial significance of each
@@ -735,7 +736,7 @@ static int search_impl(pulscan_plan p, const float *d_power, cudaStream_t s) {
     return rc;
   }
   record(p, 4, s);
-  int rc = launch_search(p, d_power, s);   // records 5, 6, 7 around the deferred kernel
+  int rc = launch_search(p, d_power, s, d_spec);   // records 5, 6, 7 around the deferred kernel
   if (rc) return rc;
   record(p, 8, s);
   rc = launch_finalize(p, s);
@@ -798,6 +799,40 @@ int pulscan_segment_maxima(pulscan_plan p, const float *d_power, float *d_max, u
   return launch_segmax(p, d_power, d_max, d_argmax, reinterpret_cast<cudaStream_t>(stream));
 }
 
+// The fused search applies: exact mode, no harmonic stages, blocks within
+// the register normalisation kernel.
+static bool fused_ok(pulscan_plan p) {
+  return p->fused && p->numharm == 1 && p->fidelity == PULSCAN_FIDELITY_EXACT && normalise_range_ok(p);
+}
+
+// rfft, the block statistics, the fused search (P formed in the bank).
+static int enqueue_fused(pulscan_plan p, const float *d_x, float *d_spec, cudaStream_t s) {
+  int rc = pulscan_rfft(p, d_x, d_spec, reinterpret_cast<pulscan_stream>(s));
+  if (rc) return rc;
+  record(p, 2, s);
+  rc = launch_normalise_stats(p, d_spec, s);
+  record(p, 3, s);
+  return rc ? rc : search_impl(p, nullptr, s, d_spec);
+}
+
+int pulscan_plan_set_fused(pulscan_plan p, int32_t on) {
+  if (!p || on < 0 || on > 1) return fail(PULSCAN_ERR_INVALID_ARG, "bad argument");
+  if (on && (p->numharm != 1 || p->fidelity != PULSCAN_FIDELITY_EXACT || !normalise_range_ok(p)))
+    return fail(PULSCAN_ERR_UNSUPPORTED, "the fused search needs the exact mode, no harmonic stages and blocks of "
+                                         "at most 16385 bins");
+  if (on && !p->d_norm) {
+    const int rc = dalloc(&p->d_norm, 4 * static_cast<size_t>(p->base_seg));
+    if (rc) return rc;
+  }
+  PS_CUDA(cudaDeviceSynchronize());
+  p->fused = on != 0;
+  if (p->graph.exec) {
+    cudaGraphExecDestroy(p->graph.exec);
+    p->graph.exec = nullptr;
+  }
+  return PULSCAN_OK;
+}
+
 // A captured search of a batch runs pipelined: parts of about pipe_bins
 // bins (series of one length), whose R2C transform and normalisation go on a
 // high-priority side stream while the bank runs the previous part on the
@@ -806,7 +841,7 @@ int pulscan_segment_maxima(pulscan_plan p, const float *d_power, float *d_max, u
 // finaliser follow the last part.
 static bool pipelined(pulscan_plan p) {
   return p->pipe_bins > 0 && p->chunks.size() >= 2 && p->numharm == 1 && p->fidelity == PULSCAN_FIDELITY_EXACT &&
-         normalise_range_ok(p);
+         !p->fused && normalise_range_ok(p);
 }
 
 // Stream and events of a pipelined capture (created before the capture).
@@ -875,6 +910,7 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
   // an armed timeout test runs outside the graph (a captured graph would
   // keep the test in every replay)
   if (!use_graph || p->wait_test_us != 0u) {
+    if (fused_ok(p) && p->wait_test_us == 0u) return enqueue_fused(p, d_x, d_spec, s);
     int rc = pulscan_rfft(p, d_x, d_spec, stream);
     if (!rc) rc = pulscan_power_normalise(p, d_spec, d_power, nullptr, stream);
     if (!rc) rc = pulscan_boxcar_search(p, d_power, stream);
@@ -901,6 +937,8 @@ int pulscan_search(pulscan_plan p, const float *d_x, float *d_spec, float *d_pow
     int rc = PULSCAN_OK;
     if (pipe) {
       rc = enqueue_pipelined(p, d_x, d_spec, d_power, g.capture);
+    } else if (fused_ok(p)) {
+      rc = enqueue_fused(p, d_x, d_spec, g.capture);
     } else {
       rc = pulscan_rfft(p, d_x, d_spec, cs);
       if (!rc) rc = pulscan_power_normalise(p, d_spec, d_power, nullptr, cs);

@@ -210,6 +210,49 @@ def test_batch_pipelined_graph_matches_oracle_and_sequential(pkg):
     assert plan.pipeline_parts() == 0
 
 
+@pytest.mark.parametrize("lengths,w_max,seg_len,sigma,tiling", [
+    ([1 << 17], 300, 4096, 3.0, (4, 0, 0)),
+    ([1 << 17], 300, 4096, 3.0, (4, 0, 1)),
+    ([1 << 16], 100, 777, 2.0, (2, 1, 0)),
+    ([1 << 13, 1 << 15, 6000, 1 << 14], 48, 256, 3.0, (1, 0, 1)),
+    ([1 << 14], 40, 50, 3.0, (1, 0, 0)),
+])
+def test_fused_search_matches_separate_stages(pkg, lengths, w_max, seg_len, sigma, tiling):
+    """The fused search (block statistics, then P formed from the spectrum in
+    the bank and the deferred blocks) gives exactly the records of the
+    separate stages, with and without a graph; those records match the
+    oracle on the separate stages' power.  Shapes: scalar and packed banks,
+    persistent tiles, an odd segment length, a batch of uneven lengths and
+    segments shorter than a deferred block's reach (the small deferred kernel)."""
+    xs = [_series(n, seed=400 + i) for i, n in enumerate(lengths)]
+    plan = pkg.Plan(lengths=lengths, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+    plan.set_tiling(*tiling)
+    xo, so, po, go = plan.offsets()
+    x_all = np.zeros(plan.x_floats, dtype=np.float32)
+    for i, x in enumerate(xs):
+        x_all[xo[i]: xo[i] + len(x)] = x
+    sep = parity.run_gpu(plan, x_all, maxima=True)
+    key = ["series", "bin", "width"]
+    plan.set_fused(1)
+    for use_graph in (False, True):
+        d_x, d_spec, d_power = plan.buffers("cuda")
+        d_x.copy_(torch.from_numpy(x_all))
+        d_power.fill_(-1.0)
+        plan.search(d_x, d_spec, d_power, use_graph=use_graph)
+        fused = plan.candidates()
+        assert float(d_power.max()) == -1.0   # P never written
+        assert len(fused) == len(sep["cands"]) and len(fused) > 0
+        assert np.array_equal(np.sort(fused, order=key), np.sort(sep["cands"], order=key))
+    plan.set_fused(0)
+    for i, n in enumerate(lengths):
+        m = n // 2 + 1
+        p = sep["power"][po[i]: po[i] + m].astype(np.float64)
+        rows = slice(go[i], go[i] + max(1, m // seg_len))
+        mx_ref, am_ref = parity.check_maxima(p, sep["mx"][rows], sep["am"][rows], w_max, seg_len)
+        parity.check_candidates(sep["cands"], p, mx_ref, am_ref, w_max, seg_len, sigma,
+                                parity.n_trials_of(m, w_max), series=i)
+
+
 def test_deferred_overflow_falls_back_to_inline_exact(pkg):
     """With no room for deferred blocks every flagged block is inspected by its own warp."""
     n, w_max, seg_len, sigma = 1 << 16, 100, 1024, 3.0

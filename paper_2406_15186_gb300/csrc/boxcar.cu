@@ -812,12 +812,18 @@ __global__ void __launch_bounds__(kDeferThreads, 8) deferred_kernel(
     // so staging costs one memory latency, not one per loop trip
     const float *sp = snaps + static_cast<size_t>(it) * (kR * 32);
     float ld_r[kRegionLoads], ld_s[kSnapLoads];
+    if (norm == nullptr) {
 #pragma unroll
-    for (int q = 0; q < kRegionLoads; ++q) {
-      const int j = t + q * kDeferThreads;
-      ld_r[q] = (j < kRegion && r0 + j < S.m)
-                    ? (norm != nullptr ? fused_power(spec, norm, S, r0 + j, seg_len) : __ldg(src + r0 + j))
-                    : 0.0f;
+      for (int q = 0; q < kRegionLoads; ++q) {
+        const int j = t + q * kDeferThreads;
+        ld_r[q] = (j < kRegion && r0 + j < S.m) ? __ldg(src + r0 + j) : 0.0f;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kRegionLoads; ++q) {
+        const int j = t + q * kDeferThreads;
+        ld_r[q] = (j < kRegion && r0 + j < S.m) ? fused_power(spec, norm, S, r0 + j, seg_len) : 0.0f;
+      }
     }
 #pragma unroll
     for (int q = 0; q < kSnapLoads; ++q) ld_s[q] = sp[t + q * kDeferThreads];

@@ -404,7 +404,7 @@ constexpr int kEvCap = 128;
 template <int NG, class Thr, class F>
 __device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lane, int wf, const uint32_t (&mk)[2][NG],
                                              Thr thr, const float *__restrict__ fh, const __half *__restrict__ fl,
-                                             int *evl, F &&f) {
+                                             int *evl, float margin, F &&f) {
   constexpr int kSpanW = (NG / 3) * kTile;   // bins per warp: one or two tiles per lane
   uint32_t cnt = 0u;
 #pragma unroll
@@ -432,7 +432,7 @@ __device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lan
     __syncwarp();
     // a lane per event: its 11 windows are screened with the prefix's high
     // parts alone (independent loads; within 1.5 ulp of F, margin 4 ulp of
-    // F[b]), then the few that pass are summed exactly
+    // the segment's largest F), then the few that pass are summed exactly
     const int n_round = min(kEvCap, n_ev - base);
     for (int e = lane; e < n_round; e += 32) {
       const int ev = evl[e];
@@ -449,10 +449,13 @@ __device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lan
         ha[i] = fh[k0 + i];
         hb[i] = fh[k0 + w + i];
       }
+      // screen margin: 4 ulp of the segment's largest prefix value, which
+      // bounds every |F[b]| (P >= 0), against the high parts' 1.5 ulp
+      const float ths = th - margin;
       uint32_t hot = 0u;
 #pragma unroll
-      for (int i = 0; i < kGrp; ++i)
-        hot |= (i < lim && hb[i] - ha[i] > th - 4.8e-7f * fabsf(hb[i])) ? (1u << i) : 0u;
+      for (int i = 0; i < kGrp; ++i) hot |= (hb[i] - ha[i] > ths) ? (1u << i) : 0u;
+      if (lim < kGrp) hot &= (lim > 0) ? ((1u << lim) - 1u) : 0u;
       while (hot != 0u) {
         const int k = k0 + __ffs(static_cast<int>(hot)) - 1;
         hot &= hot - 1u;
@@ -508,6 +511,7 @@ __global__ void __launch_bounds__(T == 1 ? 128 : 64, T == 1 ? 5 : 6) lse_forward
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, fh);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
   build_prefix(fh, buf_len, fl, wtot);
+  const float margin = 4.8e-7f * fh[buf_len];   // 4 ulp of the largest prefix value (F is non-decreasing)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NG = 3 * T;   // 11-bin groups per lane
   const int xa = warp * (T * kTile) + lane * kR, xb = xa + kTile;
@@ -589,8 +593,8 @@ __global__ void __launch_bounds__(T == 1 ? 128 : 64, T == 1 ? 5 : 6) lse_forward
         }
         __syncwarp();
         block_events(sgl, warp, lane, bi * kR + 1, mk, [&](int c) { return mr[c] - cut; }, fh, fl,
-                     evl + warp * kEvCap, [&](int c, int, int, float hi, float lo) {
-                       atomicAdd(&ls[c], expf(__fadd_rn(__fsub_rn(hi, mr[c]), lo) * inv_tau));
+                     evl + warp * kEvCap, margin, [&](int c, int, int, float hi, float lo) {
+                       atomicAdd(&ls[c], __expf(__fadd_rn(__fsub_rn(hi, mr[c]), lo) * inv_tau));
                      });
       };
   if constexpr (T == 2) walk_pairs(fh, xa, xb, la.a, lb.a, W, full_block, step, block_end);
@@ -628,6 +632,7 @@ __global__ void __launch_bounds__(T == 1 ? 128 : 64, T == 1 ? 5 : 6) lse_backwar
   for (int j = threadIdx.x; j < t.nb; j += blockDim.x) out[j] = 0.0f;
   for (int j = threadIdx.x; j < W; j += blockDim.x) tl[j] = 0.0f;   // W - 1 read; the last takes k + w = nb + W - 1
   build_prefix(fh, buf_len, fl, wtot);   // ends with a barrier: the zeros come first
+  const float margin = 4.8e-7f * fh[buf_len];   // 4 ulp of the largest prefix value (F is non-decreasing)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // this warp's row of the block's widths: Y, its low part, G and the
   // threshold Y - cut (+inf where G = 0: no window of that width counts)
@@ -674,11 +679,11 @@ __global__ void __launch_bounds__(T == 1 ? 128 : 64, T == 1 ? 5 : 6) lse_backwar
           if (drop32) mk[1][j] = 0u;
         }
         const int wf = bi * kR + 1;
-        block_events(sgl, warp, lane, wf, mk, [&](int c) { return trow[c]; }, fh, fl, evl + warp * kEvCap,
+        block_events(sgl, warp, lane, wf, mk, [&](int c) { return trow[c]; }, fh, fl, evl + warp * kEvCap, margin,
                      [&](int c, int k, int w, float hi, float lo) {
                        // (S - Y) from the two pairs: hi - Y is exact (Sterbenz)
                        const float g =
-                           grow[c] * expf(__fadd_rn(__fsub_rn(hi, yrow[c]), __fsub_rn(lo, ylrow[c])) * inv_tau);
+                           grow[c] * __expf(__fadd_rn(__fsub_rn(hi, yrow[c]), __fsub_rn(lo, ylrow[c])) * inv_tau);
                        atomicAdd(out + k, g);   // k < nb
                        const int e = k + w;
                        atomicAdd(e < t.nb ? out + e : tl + (e - t.nb), -g);

@@ -393,7 +393,10 @@ PULSCAN_API int pulscan_inject(pulscan_plan plan, const float *d_noise, const fl
                                const float *d_amp, float *d_x, pulscan_stream stream);
 
 /* dL/dA[i] = sum_n dL/dx[n] template[n] over series i (FP64 accumulation),
- * d_gamp float[n_series] in the caller's series order. */
+ * d_gamp float[n_series] in the caller's series order.  The plan allocates
+ * 128 bytes per series of partial sums on the first call (16 CTAs per
+ * series; the partials are added in a fixed order, so the result is
+ * deterministic). */
 PULSCAN_API int pulscan_amplitude_grad(pulscan_plan plan, const float *d_gx, const float *d_template,
                                        float *d_gamp, pulscan_stream stream);
 

@@ -184,6 +184,7 @@ struct pulscan_plan_s {
   float *d_dp = nullptr;           // dL/dP (power layout)
   float *d_tail = nullptr;         // per segment, W-1 bins spilling into the next segment
   float *d_gspec = nullptr;        // C2R input (spectrum layout)
+  double *d_amp_part = nullptr;    // dL/dA partial sums, 16 per series
   std::vector<ps::FftClass> ifft;  // C2R plans per length class
   // timing
   int timing = 0;                  // 0 off, 1 every stage's events, 2 the bank kernel's pair only

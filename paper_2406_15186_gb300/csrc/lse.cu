@@ -45,8 +45,8 @@
 // * normalise_backward_kernel: dL/dP -> dL/d(Re, Im) through Eq. 8, written
 //   as the input of a cuFFT C2R transform with the Hermitian weights (DC 0,
 //   interior halved, Nyquist real), whose output is dL/dx;
-// * inject_kernel / amp_grad_kernel: x = noise + A template and
-//   dL/dA = sum_n dL/dx[n] template[n], per series.
+// * inject_kernel / amp_grad_partial_kernel + amp_grad_sum_kernel:
+//   x = noise + A template and dL/dA = sum_n dL/dx[n] template[n], per series.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -875,17 +875,26 @@ __global__ void inject_kernel(const float *__restrict__ noise, const float *__re
     x[off + i] = fmaf(a, tmpl[off + i], noise[off + i]);
 }
 
-__global__ void amp_grad_kernel(const float *__restrict__ gx, const float *__restrict__ tmpl,
-                                const SeriesDev *__restrict__ series, const int64_t *__restrict__ x_off,
-                                const int64_t *__restrict__ x_len, int n_series, float *__restrict__ gamp) {
-  const int si = blockIdx.x;
+// dL/dA per series in two steps: CTA (chunk, series) reduces its 1/kAmpChunks of
+// the series (FP32 runs of 64 products folded into FP64) into a partial;
+// then one warp per series adds its partials in chunk order (deterministic).
+// Many CTAs per series keep the read of dL/dx and the template at HBM rate.
+constexpr int kAmpChunks = 16;
+
+__global__ void __launch_bounds__(256) amp_grad_partial_kernel(const float *__restrict__ gx,
+                                                               const float *__restrict__ tmpl,
+                                                               const int64_t *__restrict__ x_off,
+                                                               const int64_t *__restrict__ x_len, int n_series,
+                                                               double *__restrict__ part_out) {
+  const int si = blockIdx.y, ch = blockIdx.x;
   if (si >= n_series) return;
   const int64_t off = x_off[si], len = x_len[si];
+  const int64_t lo = len * ch / kAmpChunks, hi = len * (ch + 1) / kAmpChunks;
   double acc = 0.0;
   float part = 0.0f;
   int cnt = 0;
-  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
-    part = fmaf(gx[off + i], tmpl[off + i], part);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    part = fmaf(__ldg(gx + off + i), __ldg(tmpl + off + i), part);
     if (++cnt == 64) {   // fold into FP64 every 64 terms
       acc += part;
       part = 0.0f;
@@ -895,14 +904,24 @@ __global__ void amp_grad_kernel(const float *__restrict__ gx, const float *__res
   acc += part;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
-  __shared__ double red[32];
+  __shared__ double red[8];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double z = 0.0;
     for (int v = 0; v < static_cast<int>(blockDim.x >> 5); ++v) z += red[v];
-    gamp[series[si].user_index] = static_cast<float>(z);
+    part_out[static_cast<int64_t>(si) * kAmpChunks + ch] = z;
   }
+}
+
+__global__ void amp_grad_sum_kernel(const double *__restrict__ part, const SeriesDev *__restrict__ series,
+                                    int n_series, float *__restrict__ gamp) {
+  const int si = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (si >= n_series) return;
+  double z = (lane < kAmpChunks) ? part[static_cast<int64_t>(si) * kAmpChunks + lane] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(kFullMask, z, o);
+  if (lane == 0) gamp[series[si].user_index] = static_cast<float>(z);
 }
 
 // Tiles per lane of the logsumexp kernels: one (scalar adds; 66 ring and
@@ -1054,7 +1073,13 @@ int pulscan_amplitude_grad(pulscan_plan p, const float *d_gx, const float *d_tem
   if (!p || !d_gx || !d_template || !d_gamp) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int ns = static_cast<int>(p->n_base);
-  amp_grad_kernel<<<ns, 512, 0, s>>>(d_gx, d_template, p->d_series, p->d_x_off, p->d_x_len, ns, d_gamp);
+  if (ns > 65535) return fail(PULSCAN_ERR_UNSUPPORTED, "too many series for one launch");
+  if (!p->d_amp_part)
+    PS_CUDA(cudaMalloc(reinterpret_cast<void **>(&p->d_amp_part), sizeof(double) * kAmpChunks * ns));
+  amp_grad_partial_kernel<<<dim3(kAmpChunks, ns), 256, 0, s>>>(d_gx, d_template, p->d_x_off, p->d_x_len, ns,
+                                                                p->d_amp_part);
+  PS_CUDA(cudaGetLastError());
+  amp_grad_sum_kernel<<<(ns + 7) / 8, 256, 0, s>>>(p->d_amp_part, p->d_series, ns, d_gamp);
   PS_CUDA(cudaGetLastError());
   return PULSCAN_OK;
 }

@@ -136,7 +136,7 @@ static void free_plan(pulscan_plan p) {
                   p->d_stats,  p->d_slots,    p->d_dirty,   p->d_counters, p->d_cands,     p->own_x,
                   p->own_spec, p->own_power, p->d_items, p->d_snaps,    p->d_gtab,     p->d_x_off,
                   p->d_x_len,  p->d_dp,      p->d_tail,     p->d_gspec,   p->d_ranges,  p->d_searched, p->d_word_off, p->d_block_off,
-                  p->d_norm};
+                  p->d_norm,   p->d_amp_part};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   for (auto &e : p->ev)

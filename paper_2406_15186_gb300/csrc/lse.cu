@@ -401,14 +401,72 @@ __device__ __forceinline__ SegLim seg_lim(const SegTile &t) {
 // exact sum lies above thr(c) (S = hi + lo, k the segment-local start bin).
 constexpr int kEvCap = 128;
 
+// One event (step c, lane l, group jg, warp wv: c | l << 6 | jg << 11 | wv << 14):
+// its 11 windows are screened with the prefix's high parts alone
+// (independent loads; within 1.5 ulp of F, margin 4 ulp of the segment's
+// largest F), then the few that pass are summed exactly.
 template <int NG, class Thr, class F>
-__device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lane, int wf, const uint32_t (&mk)[2][NG],
-                                             Thr thr, const float *__restrict__ fh, const __half *__restrict__ fl,
-                                             int *evl, float margin, F &&f) {
+__device__ __forceinline__ void work_event(int ev, const SegLim &sl, int wf, Thr &&thr, const float *__restrict__ fh,
+                                           const __half *__restrict__ fl, float margin, F &&f) {
   constexpr int kSpanW = (NG / 3) * kTile;   // bins per warp: one or two tiles per lane
+  const int c = ev & 63, l = (ev >> 6) & 31, jg = (ev >> 11) & 7, wv = ev >> 14;
+  const int w = wf + c;
+  const int x = wv * kSpanW + (jg >= 3 ? kTile : 0) + l * kR;   // the tile's first bin
+  const int b0 = kGrp * (jg >= 3 ? jg - 3 : jg);                 // the group's first bin in the tile
+  const int k0 = x + b0;
+  const int lim = sl.at(x, w) - b0;                              // valid windows: i < lim
+  const float th = thr(c);
+  float ha[kGrp], hb[kGrp];
+#pragma unroll
+  for (int i = 0; i < kGrp; ++i) {
+    ha[i] = fh[k0 + i];
+    hb[i] = fh[k0 + w + i];
+  }
+  const float ths = th - margin;
+  uint32_t hot = 0u;
+#pragma unroll
+  for (int i = 0; i < kGrp; ++i) hot |= (hb[i] - ha[i] > ths) ? (1u << i) : 0u;
+  if (lim < kGrp) hot &= (lim > 0) ? ((1u << lim) - 1u) : 0u;
+  while (hot != 0u) {
+    const int k = k0 + __ffs(static_cast<int>(hot)) - 1;
+    hot &= hot - 1u;
+    float lo;
+    const float hi = window_sum2(fh, fl, k, k + w, lo);
+    if (__fadd_rn(__fsub_rn(hi, th), lo) > 0.0f) f(c, k, w, hi, lo);
+  }
+}
+
+// This lane's events of the block (see block_events) written to evl[pos -
+// base] for list positions pos in [base, base + cap), from position `first` on.
+template <int NG>
+__device__ __forceinline__ void write_events(const uint32_t (&mk)[2][NG], int warp, int lane, int first, int base,
+                                             int cap, int *evl) {
+  int pos = first;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int c = r ? kR - 1 : lane;
+#pragma unroll
+    for (int j = 0; j < NG; ++j) {
+      for (uint32_t mm = mk[r][j]; mm != 0u; mm &= mm - 1u, ++pos)
+        if (pos >= base && pos < base + cap)
+          evl[pos - base] = c | ((__ffs(static_cast<int>(mm)) - 1) << 6) | (j << 11) | (warp << 14);
+    }
+  }
+}
+
+template <int NG>
+__device__ __forceinline__ uint32_t count_events(const uint32_t (&mk)[2][NG]) {
   uint32_t cnt = 0u;
 #pragma unroll
   for (int j = 0; j < NG; ++j) cnt += __popc(mk[0][j]) + __popc(mk[1][j]);
+  return cnt;
+}
+
+template <class Thr, class F, int NG>
+__device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lane, int wf, const uint32_t (&mk)[2][NG],
+                                             Thr thr, const float *__restrict__ fh, const __half *__restrict__ fl,
+                                             int *evl, float margin, F &&f) {
+  const uint32_t cnt = count_events(mk);
   uint32_t incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -419,53 +477,47 @@ __device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lan
   const int first = static_cast<int>(incl - cnt);   // this lane's events are [first, incl)
   for (int base = 0; base < n_ev; base += kEvCap) {
     __syncwarp();
-    int pos = first;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int c = r ? kR - 1 : lane;
-#pragma unroll
-      for (int j = 0; j < NG; ++j) {
-        for (uint32_t mm = mk[r][j]; mm != 0u; mm &= mm - 1u, ++pos)
-          if (pos >= base && pos < base + kEvCap) evl[pos - base] = c | ((__ffs(static_cast<int>(mm)) - 1) << 6) | (j << 11);
-      }
-    }
+    write_events(mk, warp, lane, first, base, kEvCap, evl);
     __syncwarp();
-    // a lane per event: its 11 windows are screened with the prefix's high
-    // parts alone (independent loads; within 1.5 ulp of F, margin 4 ulp of
-    // the segment's largest F), then the few that pass are summed exactly
     const int n_round = min(kEvCap, n_ev - base);
-    for (int e = lane; e < n_round; e += 32) {
-      const int ev = evl[e];
-      const int c = ev & 63, l = (ev >> 6) & 31, jg = ev >> 11;
-      const int w = wf + c;
-      const int x = warp * kSpanW + (jg >= 3 ? kTile : 0) + l * kR;   // the tile's first bin
-      const int b0 = kGrp * (jg >= 3 ? jg - 3 : jg);                  // the group's first bin in the tile
-      const int k0 = x + b0;
-      const int lim = sl.at(x, w) - b0;                               // valid windows: i < lim
-      const float th = thr(c);
-      float ha[kGrp], hb[kGrp];
-#pragma unroll
-      for (int i = 0; i < kGrp; ++i) {
-        ha[i] = fh[k0 + i];
-        hb[i] = fh[k0 + w + i];
-      }
-      // screen margin: 4 ulp of the segment's largest prefix value, which
-      // bounds every |F[b]| (P >= 0), against the high parts' 1.5 ulp
-      const float ths = th - margin;
-      uint32_t hot = 0u;
-#pragma unroll
-      for (int i = 0; i < kGrp; ++i) hot |= (hb[i] - ha[i] > ths) ? (1u << i) : 0u;
-      if (lim < kGrp) hot &= (lim > 0) ? ((1u << lim) - 1u) : 0u;
-      while (hot != 0u) {
-        const int k = k0 + __ffs(static_cast<int>(hot)) - 1;
-        hot &= hot - 1u;
-        float lo;
-        const float hi = window_sum2(fh, fl, k, k + w, lo);
-        if (__fadd_rn(__fsub_rn(hi, th), lo) > 0.0f) f(c, k, w, hi, lo);
-      }
-    }
+    for (int e = lane; e < n_round; e += 32) work_event<NG>(evl[e], sl, wf, thr, fh, fl, margin, f);
   }
   __syncwarp();
+}
+
+// The CTA's events of the block worked off by all its threads: the warp
+// holding the segment's maximum flags nearly all of them, and the others
+// would wait for it at the next block's barrier.  wcnt: one int per warp.
+// Ends with the list free (a barrier after each full chunk but the last).
+template <class Thr, class F, int NG>
+__device__ __forceinline__ void block_events_cta(const SegLim &sl, int warp, int lane, int wf,
+                                                 const uint32_t (&mk)[2][NG], Thr thr, const float *__restrict__ fh,
+                                                 const __half *__restrict__ fl, int *evl, int cap, int *wcnt,
+                                                 float margin, F &&f) {
+  const uint32_t cnt = count_events(mk);
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(kFullMask, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) wcnt[warp] = static_cast<int>(incl);
+  __syncthreads();
+  const int warps = blockDim.x >> 5;
+  int woff = 0, n_ev = 0;
+  for (int v = 0; v < warps; ++v) {
+    const int cv = wcnt[v];
+    if (v < warp) woff += cv;
+    n_ev += cv;
+  }
+  const int first = woff + static_cast<int>(incl - cnt);
+  for (int base = 0; base < n_ev; base += cap) {
+    write_events(mk, warp, lane, first, base, cap, evl);
+    __syncthreads();
+    const int n_round = min(cap, n_ev - base);
+    for (int e = threadIdx.x; e < n_round; e += blockDim.x) work_event<NG>(evl[e], sl, wf, thr, fh, fl, margin, f);
+    if (base + cap < n_ev) __syncthreads();
+  }
 }
 
 // The warp's maximum of v (a single reduction instruction on sm_100+).
@@ -501,12 +553,13 @@ __global__ void __launch_bounds__(T == 1 ? 128 : 64, T == 1 ? 5 : 6) lse_forward
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   double *wtot = reinterpret_cast<double *>(smem_raw + 32);
   uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
+  int *wcnt = reinterpret_cast<int *>(smem_raw + 80);      // per-warp event counts (four)
   float *fh = reinterpret_cast<float *>(smem_raw + 128);   // P, then the prefix's high part: buf_len + 1
   float *wmax = fh + buf_len + 1;       // [2][warps][33]: each warp's maximum per width
   float *mrow = wmax + 2 * kRows;       // [2][warps][33]: M per width, a copy per warp
   float *lsbw = mrow + 2 * kRows;       // [2][warps][33]: each warp's sums of exp
   const int warps = blockDim.x >> 5;
-  int *evl = reinterpret_cast<int *>(lsbw + 2 * kRows);           // warps x kEvCap event lists
+  int *evl = reinterpret_cast<int *>(lsbw + 2 * kRows);           // the CTA's event list: warps x kEvCap
   __half *fl = reinterpret_cast<__half *>(evl + warps * kEvCap);   // the prefix's low part: buf_len + 1
   const SegTile t = seg_tile(series, seg_off, n_series, seg_len, power, fh);
   if (!stage_segment(t, buf_len, bar, flag, counters)) return;
@@ -591,11 +644,10 @@ __global__ void __launch_bounds__(T == 1 ? 128 : 64, T == 1 ? 5 : 6) lse_forward
           if (drop) mk[0][j] = 0u;
           if (drop32) mk[1][j] = 0u;
         }
-        __syncwarp();
-        block_events(sgl, warp, lane, bi * kR + 1, mk, [&](int c) { return mr[c] - cut; }, fh, fl,
-                     evl + warp * kEvCap, margin, [&](int c, int, int, float hi, float lo) {
-                       atomicAdd(&ls[c], __expf(__fadd_rn(__fsub_rn(hi, mr[c]), lo) * inv_tau));
-                     });
+        block_events_cta(sgl, warp, lane, bi * kR + 1, mk, [&](int c) { return mr[c] - cut; }, fh, fl, evl,
+                         warps * kEvCap, wcnt, margin, [&](int c, int, int, float hi, float lo) {
+                           atomicAdd(&ls[c], __expf(__fadd_rn(__fsub_rn(hi, mr[c]), lo) * inv_tau));
+                         });
       };
   if constexpr (T == 2) walk_pairs(fh, xa, xb, la.a, lb.a, W, full_block, step, block_end);
   else walk_single(fh, xa, la.a, W, full_block, step, block_end);

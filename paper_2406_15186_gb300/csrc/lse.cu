@@ -666,6 +666,7 @@ __global__ void __launch_bounds__(T == 1 ? 128 : 64, T == 1 ? 5 : 6) lse_backwar
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   double *wtot = reinterpret_cast<double *>(smem_raw + 32);
   uint32_t *flag = reinterpret_cast<uint32_t *>(smem_raw + 64);
+  int *wcnt = reinterpret_cast<int *>(smem_raw + 80);      // per-warp event counts (four)
   float *fh = reinterpret_cast<float *>(smem_raw + 128);   // P, then the prefix's high part: buf_len + 1
   float *rows = fh + buf_len + 1;                // warps x [Y, Y low part, G, Y - cut] x 33 widths of a block
   float *wsum = rows + kBwdRows;                 // per-warp scan totals
@@ -731,7 +732,8 @@ __global__ void __launch_bounds__(T == 1 ? 128 : 64, T == 1 ? 5 : 6) lse_backwar
           if (drop32) mk[1][j] = 0u;
         }
         const int wf = bi * kR + 1;
-        block_events(sgl, warp, lane, wf, mk, [&](int c) { return trow[c]; }, fh, fl, evl + warp * kEvCap, margin,
+        block_events_cta(sgl, warp, lane, wf, mk, [&](int c) { return trow[c]; }, fh, fl, evl,
+                         (blockDim.x >> 5) * kEvCap, wcnt, margin,
                      [&](int c, int k, int w, float hi, float lo) {
                        // (S - Y) from the two pairs: hi - Y is exact (Sterbenz)
                        const float g =

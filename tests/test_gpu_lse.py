@@ -81,7 +81,10 @@ def _spec(d, m):
 
 
 @pytest.mark.parametrize("tau", [0.1, 1.0])
-@pytest.mark.parametrize("n,w_max,seg_len", [(1 << 14, 48, 512), (1 << 13, 33, 300), (1 << 12, 7, 64)])
+# segments of one warp's 1056 bins or less, and (the last two) CTAs of four
+# warps: segments of 2500 bins with a last block of 3193, one block of 4097
+@pytest.mark.parametrize("n,w_max,seg_len", [(1 << 14, 48, 512), (1 << 13, 33, 300), (1 << 12, 7, 64),
+                                             (1 << 14, 40, 2500), (1 << 13, 100, 4000)])
 def test_forward_and_backward_against_oracle(pkg, n, w_max, seg_len, tau):
     x = _series(n, 17)
     plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=6.0)

@@ -56,6 +56,8 @@ def parse():
                     help="skip every section after the headline's timed steps (profiling)")
     ap.add_argument("--only-diff", action="store_true",
                     help="run only the differentiable measurement and print its JSON (profiling)")
+    ap.add_argument("--only-fidelity", action="store_true",
+                    help="run only the paper-GPU fidelity mode on --workload and print its JSON (profiling)")
     ap.add_argument("--diff-binaries", type=int, default=None,
                     help="run the differentiable measurement on its first N binaries only (profiling)")
     ap.add_argument("--no-graph", action="store_true",
@@ -705,6 +707,27 @@ def run_ours(args, rank, world, local):
     m = n // 2 + 1
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    if args.only_fidelity:
+        plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
+        with torch.cuda.stream(stream):
+            bufs = plan.buffers(dev)
+            synth.single_series_device(name, bufs[0])
+        torch.cuda.synchronize()
+
+        def fstep():
+            plan.search(*bufs, use_graph=True, stream=stream)
+
+        fstep()
+        if args.tiling:
+            plan.set_tiling(*[int(v) for v in args.tiling.split(",")])
+        else:
+            plan.autotune(bufs[2], stream=stream)
+        plan.enable_timing(True)
+        r = run_fidelity(torch, pkg, plan, fstep, stream, max(3, args.steps // 2), flush)
+        if rank == 0:
+            print(json.dumps({"paper_gpu_fidelity": dict(r, workload=name, bank_tiling=plan.tiling())}), flush=True)
+        plan.close()
+        return
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or 2070.0)

@@ -79,6 +79,14 @@ __device__ __forceinline__ int first_equal(const float (&s)[kR], float v, int ia
   return idx;
 }
 
+// Three-input maximum (one instruction on sm_100 and later); like fmaxf it
+// returns one of its operands and ignores NaN operands.
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // One exact step's merge.  Each lane offers the maximum of its valid bins in
 // segment seg_a (bins [0, ib)) and, for the one lane that straddles a
 // segment boundary, in seg_a + 1 (bins [ib, lim)); v < 0 means no valid bin.
@@ -432,6 +440,170 @@ __device__ __forceinline__ void stage_fused(float *buf, int buf_len, int avail, 
   for (int i = avail + static_cast<int>(threadIdx.x); i < buf_len; i += blockDim.x) buf[i] = 0.0f;
 }
 
+// ---------------------------------------------------------------------------
+// Dump mode: every (segment, width) maximum, no threshold.
+//
+// A slice whose lanes each lie in one of two segments X0, X0 + 1 (at most one
+// lane straddles the boundary) walks the widths at which all its windows are
+// inside the tile and the series with a lean per-step merge: each lane's
+// maximum from eleven 3-bin group maxima, one warp max-reduction per segment,
+// and the lowest lane holding the warp maximum alone finds its bin and merges
+// the key.  A whole lane finds the bin through its group maxima (the first
+// group holding the value, then the first of that group's three bins); the
+// straddling lane takes masked maxima and a masked scan of its part.  The
+// remaining widths (windows past the end of the series or the tile) and
+// slices that touch three segments take the general exact steps.
+constexpr int kGroups = kR / 3;
+
+// Maximum of the lane's 33 sums; g receives the eleven 3-bin group maxima and
+// t the maxima of groups 0-2, 3-5 and 6-8.
+__device__ __forceinline__ float lane_max33(const float (&s)[kR], float (&g)[kGroups], float (&t)[3]) {
+#pragma unroll
+  for (int j = 0; j < kGroups; ++j) g[j] = max3f(s[3 * j], s[3 * j + 1], s[3 * j + 2]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) t[r] = max3f(g[3 * r], g[3 * r + 1], g[3 * r + 2]);
+  return max3f(max3f(t[0], t[1], t[2]), g[9], g[10]);
+}
+
+// First of three values equal to v (the third if neither of the first two).
+__device__ __forceinline__ int first_of3(float a, float b, float v) { return a == v ? 0 : (b == v ? 1 : 2); }
+
+// Lowest i with s_i == v, for v the lane's own maximum: the first of the
+// triple maxima t (then groups 9, 10) holding v, its first group, then that
+// group's first bin.  Each level reads static registers picked by a switch,
+// so the one lane that searches executes a few instructions per level.
+__device__ __forceinline__ int first_bin33(const float (&s)[kR], const float (&g)[kGroups], const float (&t)[3],
+                                           float v) {
+  int q;
+  if (t[0] == v) q = first_of3(g[0], g[1], v);
+  else if (t[1] == v) q = 3 + first_of3(g[3], g[4], v);
+  else if (t[2] == v) q = 6 + first_of3(g[6], g[7], v);
+  else q = g[9] == v ? 9 : 10;
+  switch (q) {
+#define PS_BIN_CASE(k) \
+  case k: return 3 * (k) + first_of3(s[3 * (k)], s[3 * (k) + 1], v);
+    PS_BIN_CASE(0) PS_BIN_CASE(1) PS_BIN_CASE(2) PS_BIN_CASE(3) PS_BIN_CASE(4) PS_BIN_CASE(5)
+    PS_BIN_CASE(6) PS_BIN_CASE(7) PS_BIN_CASE(8) PS_BIN_CASE(9)
+#undef PS_BIN_CASE
+    default: return 30 + first_of3(s[30], s[31], v);
+  }
+}
+
+// Maximum of s[A..B), B > A, as a tree of 3-input maxima.
+template <int A, int B>
+__device__ __forceinline__ float range_max(const float (&s)[kR]) {
+  if constexpr (B - A == 1) {
+    return s[A];
+  } else if constexpr (B - A == 2) {
+    return fmaxf(s[A], s[A + 1]);
+  } else if constexpr (B - A == 3) {
+    return max3f(s[A], s[A + 1], s[A + 2]);
+  } else {
+    constexpr int T = (B - A) / 3;
+    return max3f(range_max<A, A + T>(s), range_max<A + T, A + 2 * T>(s), range_max<A + 2 * T, B>(s));
+  }
+}
+
+// Maxima of the lane's bins [0, ib) and [ib, 33), 0 < ib < 33 (the lane that
+// straddles a segment boundary), through a switch on ib.
+__device__ __forceinline__ void split_max(const float (&s)[kR], int ib, float &a, float &b) {
+  switch (ib) {
+#define PS_SPLIT_CASE(k)        \
+  case k:                       \
+    a = range_max<0, k>(s);     \
+    b = range_max<k, kR>(s);    \
+    break;
+    PS_SPLIT_CASE(1) PS_SPLIT_CASE(2) PS_SPLIT_CASE(3) PS_SPLIT_CASE(4) PS_SPLIT_CASE(5) PS_SPLIT_CASE(6)
+    PS_SPLIT_CASE(7) PS_SPLIT_CASE(8) PS_SPLIT_CASE(9) PS_SPLIT_CASE(10) PS_SPLIT_CASE(11) PS_SPLIT_CASE(12)
+    PS_SPLIT_CASE(13) PS_SPLIT_CASE(14) PS_SPLIT_CASE(15) PS_SPLIT_CASE(16) PS_SPLIT_CASE(17) PS_SPLIT_CASE(18)
+    PS_SPLIT_CASE(19) PS_SPLIT_CASE(20) PS_SPLIT_CASE(21) PS_SPLIT_CASE(22) PS_SPLIT_CASE(23) PS_SPLIT_CASE(24)
+    PS_SPLIT_CASE(25) PS_SPLIT_CASE(26) PS_SPLIT_CASE(27) PS_SPLIT_CASE(28) PS_SPLIT_CASE(29) PS_SPLIT_CASE(30)
+    PS_SPLIT_CASE(31)
+#undef PS_SPLIT_CASE
+    default:
+      a = range_max<0, 32>(s);
+      b = s[32];
+  }
+}
+
+// Merge the warp maximum of v into slot (X, col).  v < 0: the lane holds no
+// bin of segment X.  The lane's candidate bins are [ia, ie).
+__device__ __forceinline__ void dump_emit(const float (&s)[kR], const float (&g)[kGroups], const float (&t)[3],
+                                          float v, int ia, int ie, const LaneCtx &c, int64_t X, int col, int lane) {
+  const bool ok = v >= 0.0f;
+  const uint32_t bits = ok ? __float_as_uint(v) : 0u;
+  const uint32_t wb = __reduce_max_sync(kFull, bits);
+  const unsigned hit = __ballot_sync(kFull, ok && bits == wb);
+  if (hit != 0u && lane == __ffs(static_cast<int>(hit)) - 1) {
+    const float vm = __uint_as_float(wb);
+    const int i = (ia == 0 && ie == kR) ? first_bin33(s, g, t, vm) : first_equal(s, vm, ia, ie);
+    emit_slot<false>(c.slots, nullptr, static_cast<uint64_t>(X) * c.W + col,
+                     slot_key(vm, static_cast<uint32_t>(c.k0 + i)));
+  }
+}
+
+// Steps w = wa..wb (every window valid) of a slice in segment X0 alone.
+__device__ __forceinline__ void dump_steps_one(float (&s)[kR], const float *__restrict__ lane_buf, const LaneCtx &c,
+                                               int64_t X0, int wa, int wb, int lane) {
+  for (int w = wa; w <= wb; ++w) {
+    const float *pw = lane_buf + (w - 1);
+#pragma unroll
+    for (int i = 0; i < kR; ++i) s[i] += pw[i];
+    float g[kGroups], t[3];
+    const float M = lane_max33(s, g, t);
+    dump_emit(s, g, t, M, 0, kR, c, X0, w - 1, lane);
+  }
+}
+
+// Steps w = wa..wb (every window valid) of a slice that reaches segment
+// X0 + 1; lane bl (or none, bl < 0) straddles the boundary at its bin c.ib.
+__device__ __forceinline__ void dump_steps_two(float (&s)[kR], const float *__restrict__ lane_buf, const LaneCtx &c,
+                                               int64_t X0, int bl, int wa, int wb, int lane) {
+  for (int w = wa; w <= wb; ++w) {
+    const float *pw = lane_buf + (w - 1);
+#pragma unroll
+    for (int i = 0; i < kR; ++i) s[i] += pw[i];
+    float g[kGroups], t[3];
+    const float M = lane_max33(s, g, t);
+    const bool inA = c.seg_a == X0;
+    float vA = inA ? M : -1.0f, vB = inA ? -1.0f : M;
+    int ea = kR, ib = 0;
+    if (lane == bl) {
+      // the straddling lane's two parts
+      split_max(s, c.ib, vA, vB);
+      ea = c.ib;
+      ib = c.ib;
+    }
+    dump_emit(s, g, t, vA, 0, ea, c, X0, w - 1, lane);
+    dump_emit(s, g, t, vB, ib, kR, c, X0 + 1, w - 1, lane);
+  }
+}
+
+// Every (segment, width) maximum of slice vw of the tile.
+__device__ __forceinline__ void dump_slice(const float *__restrict__ buf, const SeriesDev &S, int64_t t0,
+                                           int tile_bins, int vw, int lane, int W, int seg_len,
+                                           unsigned long long *__restrict__ slots) {
+  const LaneCtx c = lane_ctx(S, t0, tile_bins, vw, lane, W, seg_len, slots, nullptr);
+  const float *lane_buf = buf + vw * (32 * kR) + lane * kR;
+  float s[kR];
+#pragma unroll
+  for (int i = 0; i < kR; ++i) s[i] = 0.0f;
+  const int64_t X0 = __shfl_sync(kFull, c.seg_a, 0);
+  // each lane in X0 (possibly straddling into X0 + 1) or wholly in X0 + 1
+  const bool two = seg_len >= 2 * kR && __all_sync(kFull, c.seg_a == X0 || (c.seg_a == X0 + 1 && c.ib == kR));
+  // the lane's windows are all valid up to width m - (k0 + 32) when its 33
+  // bins belong to the tile
+  const int64_t wl = c.lim_tile >= kR ? max64(0, min64(static_cast<int64_t>(W), c.m - c.k0 - (kR - 1))) : 0;
+  const int w_fast = two ? static_cast<int>(__reduce_min_sync(kFull, static_cast<unsigned>(wl))) : 0;
+  if (w_fast > 0) {
+    const bool split = __any_sync(kFull, c.seg_a != X0 || c.ib < kR);
+    const int bl = __ffs(static_cast<int>(__ballot_sync(kFull, c.ib < kR))) - 1;
+    if (split) dump_steps_two(s, lane_buf, c, X0, bl, 1, w_fast, lane);
+    else dump_steps_one(s, lane_buf, c, X0, 1, w_fast, lane);
+  }
+  if (w_fast < W) exact_steps<false>(s, lane_buf, w_fast + 1, 0, W - w_fast, nullptr, c);
+}
+
 template <bool kSearch, bool kPacked>
 __device__ __forceinline__ bool boxcar_tile(
     int64_t tile, unsigned char *smem_raw, const float *__restrict__ power, const SeriesDev *__restrict__ series,
@@ -503,14 +675,7 @@ __device__ __forceinline__ bool boxcar_tile(
 
   if (!kSearch) {
     // every (segment, width) maximum: each of the warp's slices in turn
-    for (int g = 0; g < groups; ++g) {
-      const int vw = warp * groups + g;
-      const LaneCtx c = lane_ctx(S, t0, tile_bins, vw, lane, W, seg_len, slots, dirty);
-      float s[kR];
-#pragma unroll
-      for (int i = 0; i < kR; ++i) s[i] = 0.0f;
-      exact_steps<false>(s, buf + vw * (32 * kR) + lane * kR, 1, 0, W, thr, c);
-    }
+    for (int g = 0; g < groups; ++g) dump_slice(buf, S, t0, tile_bins, warp * groups + g, lane, W, seg_len, slots);
     return true;
   }
   if (kPacked) {
@@ -612,9 +777,12 @@ __device__ __forceinline__ uint32_t sm_id() {
 // one-CTA-per-tile grid refills the SMs that free their slots first, which
 // leaves a partial last wave on some SMs only.)
 // kPacked (search mode only): two virtual warps per warp with packed adds,
-// at most 170 registers per thread (three 4-warp CTAs per SM).
+// at most 170 registers per thread (three 4-warp CTAs per SM).  Dump mode
+// targets kDumpMinBlocks resident 4-warp CTAs per SM.
+constexpr int kDumpMinBlocks = 4;
+
 template <bool kSearch, bool kPacked>
-__global__ void __launch_bounds__(kMaxThreads, kPacked ? 3 : kMinBlocks) boxcar_kernel(
+__global__ void __launch_bounds__(kMaxThreads, kSearch ? (kPacked ? 3 : kMinBlocks) : kDumpMinBlocks) boxcar_kernel(
     const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
     int n_series, int W, int seg_len, const float *__restrict__ thr_all, const float *__restrict__ thrb_all,
     unsigned long long *__restrict__ slots, uint32_t *__restrict__ dirty, uint32_t *__restrict__ counters,
@@ -714,12 +882,6 @@ constexpr int kThreadsPerLane = kR / kDeferBins;            // 3
 constexpr int kRegionLoads = (kRegion + kDeferThreads - 1) / kDeferThreads;
 constexpr int kSnapLoads = 32 * kR / kDeferThreads;
 static_assert(kSnapLoads * kDeferThreads == 32 * kR, "whole snapshot loads");
-
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-  float r;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
 
 __device__ __forceinline__ unsigned long long best_key(float v, uint32_t bin) {
   return (static_cast<unsigned long long>(__float_as_uint(v)) << 32) |

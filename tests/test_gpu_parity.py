@@ -9,6 +9,7 @@ import math
 import numpy as np
 import pytest
 
+from oracle import boxcar as obox
 from oracle import fft as offt
 from oracle import pipeline as opipe
 from oracle import significance as osig
@@ -377,6 +378,58 @@ def test_host_entry_points_match_the_device_path(pkg):
             plans[(i + 1) % 2].search_host_async(pins[i + 1], stream=streams[(i + 1) % 2])
         got = plans[i % 2].candidates(stream=streams[i % 2])
         assert np.array_equal(got, ref[i]), i
+
+
+# (n, z_max, segment_len): 1024 = 31 * 33 + 1 puts a segment boundary at every
+# position 1..32 of a lane and two boundaries in some 1056-bin slices; 4096
+# and 1000 give one boundary per slice; 48 puts a lane across three segments
+@pytest.mark.parametrize("n,w_max,seg_len", [
+    (1 << 16, 100, 1024),
+    (1 << 15, 70, 4096),
+    (3 * (1 << 12) + 10, 130, 1000),
+    (1 << 13, 40, 48),
+])
+@pytest.mark.parametrize("tiling", [(2, 0, 0), (4, 0, 1)])
+def test_segment_maxima_exact_ties(pkg, n, w_max, seg_len, tiling):
+    """Integer-valued power (sparse ones and twos, and three segments of
+    zeros): every window sum is exact in FP32 and in FP64, so maxima tie
+    exactly and often.  The dump mode must return the oracle's maxima and its
+    lowest-bin argmax (Algorithm 4's first index) bit for bit, and so must
+    the thresholded search's records."""
+    plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=3.0)
+    plan.set_tiling(*tiling)
+    m = n // 2 + 1
+    rng = np.random.default_rng(seg_len + w_max)
+    p = rng.choice(np.array([0.0, 0.0, 0.0, 1.0, 2.0], dtype=np.float32), size=m)
+    p[m // 3: m // 3 + 3 * seg_len] = 0.0
+    d_power = torch.zeros(plan.power_floats, dtype=torch.float32, device="cuda")
+    d_power[:m] = torch.from_numpy(p)
+    nn = plan.total_segments * w_max
+    mx = torch.empty(nn, dtype=torch.float32, device="cuda")
+    am = torch.empty(nn, dtype=torch.int64, device="cuda")
+    plan.segment_maxima(d_power, mx, am)
+    torch.cuda.synchronize()
+    mx_ref, am_ref = obox.segment_maxima(p.astype(np.float64), w_max, seg_len)
+    mg = mx.cpu().numpy().reshape(plan.total_segments, w_max).astype(np.float64)
+    ag = am.cpu().numpy().reshape(plan.total_segments, w_max)
+    empty = np.isnan(mx_ref)
+    assert np.array_equal(np.isnan(mg), empty)
+    assert np.array_equal(mg[~empty], mx_ref[~empty])
+    assert np.array_equal(ag, am_ref)
+    # the thresholded search on a denser integer power (deferred blocks and
+    # inline exact steps): every record's power and bin exactly the oracle's
+    q = rng.choice(np.arange(6, dtype=np.float32), size=m)
+    d_power[:m] = torch.from_numpy(q)
+    plan.boxcar_search(d_power)
+    cands = plan.candidates()
+    q64 = q.astype(np.float64)
+    mq, aq = obox.segment_maxima(q64, w_max, seg_len)
+    assert parity.check_candidates(cands, q64, mq, aq, w_max, seg_len, 3.0, parity.n_trials_of(m, w_max)) > 0
+    seg = np.minimum(cands["bin"].astype(np.int64) // seg_len, mq.shape[0] - 1)
+    wi = cands["width"].astype(np.int64) - 1
+    assert np.array_equal(cands["power"].astype(np.float64), mq[seg, wi])
+    assert np.array_equal(cands["bin"].astype(np.int64), aq[seg, wi])
+    plan.close()
 
 
 def test_packed_and_scalar_banks_give_identical_records(pkg):

@@ -352,6 +352,7 @@ def run_batched(torch, pkg, synth, dev, stream, steps):
     plan.rfft(d_x, d_spec, stream=stream)
     plan.power_normalise(d_spec, d_power, stream=stream)
     tiling = plan.autotune(d_power, stream=stream)
+    defer_warps = 1 if plan.defer_form() else 3
 
     def batched():
         plan.search(d_x, d_spec, d_power, use_graph=True, stream=stream)
@@ -390,7 +391,7 @@ def run_batched(torch, pkg, synth, dev, stream, steps):
             "ratio_batched_vs_per_series": t_s / t_b, "bin_widths_per_s": bins * w_max / (t_b * 1e-3) / 1e9,
             "ms_per_batch_pipelined": t_q, "pipeline_parts": parts, "ms_per_batch_fused": t_f,
             "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "packed": tiling[2],
-                            "by": "pulscan_plan_autotune"},
+                            "by": "pulscan_plan_autotune", "deferred_warps_per_block": defer_warps},
             "unit": "G bin-widths/s", "candidates": n_cands, "graph": True,
             "per_series": "the same kernels launched per series on one stream (no graph), one plan per length",
             "l2": "inputs (8.2 GB) far larger than L2"}
@@ -622,7 +623,8 @@ def time_single(torch, pkg, synth, dev, stream, flush, name, args, steps, warmup
     res = {"workload": workload_text(name), "m": m, "w_max": w_max, "step_ms": step_ms,
            "ms_per_step": statistics.mean(step_ms), "kernels_ms": kernels, "candidates": n_cands,
            "deferred_blocks": n_deferred, "clocks": clocks,
-           "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "packed": tiling[2], "by": tiling_by}}
+           "bank_tiling": {"warps_per_cta": tiling[0], "persistent": tiling[1], "packed": tiling[2], "by": tiling_by,
+                           "deferred_warps_per_block": 1 if plan.defer_form() else 3}}
     return res, plan, (d_x, d_spec, d_power)
 
 
@@ -677,7 +679,9 @@ def rooflines(res, peak, n_sm, sm_max, name):
             "peak_derived": derived, "frac_of_derived": ach / derived,
             "peak_derived_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (sm_max_mhz)"}
     search = {"bound": "alu", "achieved": ach_s, "peak": p, "unit": "TFLOP/s", "frac": ach_s / p,
-              "kernels": "boxcar_kernel<search> + deferred_kernel + word_scan_kernel + finalize_kernel",
+              "kernels": "boxcar_kernel<search> + " + (
+                  "deferred_warp_kernel" if res["bank_tiling"].get("deferred_warps_per_block") == 1
+                  else "deferred_kernel") + " + word_scan_kernel + finalize_kernel",
               "time_ms": t_search, "time_source": "per-stage events of the breakdown steps"}
     return bank, search
 

@@ -190,9 +190,11 @@ PULSCAN_API int pulscan_plan_set_fidelity(pulscan_plan plan, int32_t mode);
  * start bins, tile = 1056 x warps) and the packed form (a warp owns two 1056-
  * bin slices and adds them pairwise with add.f32x2, tile = 2112 x warps),
  * each with one CTA per tile and with a persistent grid of per-SM tile
- * ranges, and keeps the fastest.  Segment length, widths and halo are fixed
- * by the search itself, and the two forms perform the same FP32 adds in the
- * same order, so the candidates do not depend on the choice.  Synchronises
+ * ranges, and keeps the fastest; then, on that shape, the deferred blocks'
+ * two forms (pulscan_plan_set_defer_form), three runs each.  Segment length,
+ * widths and halo are fixed by the search itself, and the two forms perform
+ * the same FP32 adds in the same order, so the candidates do not depend on
+ * the choice.  Synchronises
  * `stream`, discards the candidates of the trial runs and drops the plan's
  * captured graph.  pulscan_plan_tiling reports the current choice
  * (persistent: -1 automatic, the default; 0 one CTA per tile; 1 persistent;
@@ -425,6 +427,21 @@ PULSCAN_API int pulscan_plan_counters(pulscan_plan plan, int64_t *h_out, int32_t
  * reallocates the list (4.2 KB per item; synchronises the device and drops
  * the plan's captured graph).  Errors: INVALID_ARG, NOMEM. */
 PULSCAN_API int pulscan_plan_set_defer_capacity(pulscan_plan plan, int64_t cap);
+
+/* How the deferred blocks (the 33-width blocks of Algorithm 4's scan whose
+ * exact bound reached the threshold, re-run from their snapshots) are
+ * inspected: form 0 = three warps per block (11 bins per thread, merged
+ * through shared memory), form 1 = one warp per block (33 bins per lane, a
+ * warp max-reduction per width; the block's bin search only for a maximum
+ * that reaches T_w).  Same records either way.  Form 1 wins when the blocks
+ * fill the GPU several times over, form 0 when few blocks leave one block's
+ * chain of steps exposed.  Default: 1 for plans of 2^25 power bins or more,
+ * else 0; pulscan_plan_autotune times both on the caller's data and keeps
+ * the faster.  Drops the plan's captured graph when the form changes.
+ * Errors: INVALID_ARG (null plan, form not 0 or 1). */
+PULSCAN_API int pulscan_plan_set_defer_form(pulscan_plan plan, int32_t form);
+/* The current form of pulscan_plan_set_defer_form in *form. */
+PULSCAN_API int pulscan_plan_defer_form(pulscan_plan plan, int32_t *form);
 
 /* The FP32 add rate of the current GPU, the ceiling of the boxcar bank
  * (§2.2.5: one add per bin and width), measured rather than derived: a

@@ -102,6 +102,8 @@ _SIGS = {
     "pulscan_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "pulscan_plan_counters": (ctypes.c_int, [_P, _I64P, ctypes.c_int32]),
     "pulscan_plan_set_defer_capacity": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "pulscan_plan_set_defer_form": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "pulscan_plan_defer_form": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "pulscan_plan_timings": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "pulscan_measure_add_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, _P]),
     "pulscan_last_error": (ctypes.c_char_p, []),
@@ -365,6 +367,15 @@ class Plan:
 
     def set_defer_capacity(self, cap):
         _check(load().pulscan_plan_set_defer_capacity(self._h, int(cap)))
+
+    def set_defer_form(self, form):
+        """Deferred blocks inspected by three warps per block (0) or one warp per block (1)."""
+        _check(load().pulscan_plan_set_defer_form(self._h, int(form)))
+
+    def defer_form(self):
+        f = ctypes.c_int32(0)
+        _check(load().pulscan_plan_defer_form(self._h, ctypes.byref(f)))
+        return f.value
 
     # -- convenience: device buffers sized for this plan (torch)
     def buffers(self, device="cuda"):

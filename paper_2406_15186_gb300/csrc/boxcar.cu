@@ -138,17 +138,19 @@ __device__ __forceinline__ void merge_step(const float (&s)[kR], const LaneCtx &
 // maxima over its valid bins are max-reductions with selects, and the bin
 // index is searched only by the lane(s) holding the warp maximum.
 // kSearch: only maxima >= T_w are merged; otherwise every maximum is.
+// wshift: lane_buf[w - 1 - wshift + i] is the window value of bin i at width
+// w (a window staged from width wshift + 1 on).
 template <bool kSearch>
 __device__ __forceinline__ void exact_steps(float (&s)[kR], const float *__restrict__ lane_buf, int wf,
                                             int cb, int ce, const float *__restrict__ thr,
-                                            const LaneCtx &c) {
+                                            const LaneCtx &c, int wshift = 0) {
   // segment_len < 66 lets a lane's 33 bins reach a third segment: then every
   // bin is merged on its own (only tiny test shapes take this branch)
   const bool small_seg = c.seg_len < 2 * kR;
   const bool any_split = __any_sync(kFull, c.ib < kR);
   for (int cc = cb; cc < ce; ++cc) {
     const int w = wf + cc;
-    const float *pw = lane_buf + (w - 1);
+    const float *pw = lane_buf + (w - 1 - wshift);
 #pragma unroll
     for (int i = 0; i < kR; ++i) s[i] += pw[i];
     // valid bins: inside the tile, and the window inside the spectrum
@@ -526,19 +528,23 @@ __device__ __forceinline__ void split_max(const float (&s)[kR], int ib, float &a
   }
 }
 
-// Merge the warp maximum of v into slot (X, col).  v < 0: the lane holds no
-// bin of segment X.  The lane's candidate bins are [ia, ie).
-__device__ __forceinline__ void dump_emit(const float (&s)[kR], const float (&g)[kGroups], const float (&t)[3],
-                                          float v, int ia, int ie, const LaneCtx &c, int64_t X, int col, int lane) {
+// Merge the warp maximum of v into slot (X, col); in search mode only a
+// maximum >= T is merged (and its slot marked dirty).  v < 0: the lane holds
+// no bin of segment X.  The lane's candidate bins are [ia, ie).
+template <bool kSearch>
+__device__ __forceinline__ void lean_emit(const float (&s)[kR], const float (&g)[kGroups], const float (&t)[3],
+                                          float v, int ia, int ie, const LaneCtx &c, int64_t X, int col, int lane,
+                                          float T) {
   const bool ok = v >= 0.0f;
   const uint32_t bits = ok ? __float_as_uint(v) : 0u;
   const uint32_t wb = __reduce_max_sync(kFull, bits);
+  const float vm = __uint_as_float(wb);
+  if (kSearch && !(vm >= T)) return;
   const unsigned hit = __ballot_sync(kFull, ok && bits == wb);
   if (hit != 0u && lane == __ffs(static_cast<int>(hit)) - 1) {
-    const float vm = __uint_as_float(wb);
     const int i = (ia == 0 && ie == kR) ? first_bin33(s, g, t, vm) : first_equal(s, vm, ia, ie);
-    emit_slot<false>(c.slots, nullptr, static_cast<uint64_t>(X) * c.W + col,
-                     slot_key(vm, static_cast<uint32_t>(c.k0 + i)));
+    emit_slot<kSearch>(c.slots, c.dirty, static_cast<uint64_t>(X) * c.W + col,
+                       slot_key(vm, static_cast<uint32_t>(c.k0 + i)));
   }
 }
 
@@ -551,7 +557,7 @@ __device__ __forceinline__ void dump_steps_one(float (&s)[kR], const float *__re
     for (int i = 0; i < kR; ++i) s[i] += pw[i];
     float g[kGroups], t[3];
     const float M = lane_max33(s, g, t);
-    dump_emit(s, g, t, M, 0, kR, c, X0, w - 1, lane);
+    lean_emit<false>(s, g, t, M, 0, kR, c, X0, w - 1, lane, 0.0f);
   }
 }
 
@@ -574,8 +580,8 @@ __device__ __forceinline__ void dump_steps_two(float (&s)[kR], const float *__re
       ea = c.ib;
       ib = c.ib;
     }
-    dump_emit(s, g, t, vA, 0, ea, c, X0, w - 1, lane);
-    dump_emit(s, g, t, vB, ib, kR, c, X0 + 1, w - 1, lane);
+    lean_emit<false>(s, g, t, vA, 0, ea, c, X0, w - 1, lane, 0.0f);
+    lean_emit<false>(s, g, t, vB, ib, kR, c, X0 + 1, w - 1, lane, 0.0f);
   }
 }
 
@@ -1157,6 +1163,118 @@ __global__ void __launch_bounds__(kDeferThreads, 8) deferred_kernel(
   }
 }
 
+// Deferred blocks, one warp per item (segment_len >= 66).  The warp takes
+// its lanes' 33 running sums straight from the snapshot ([bin][lane]:
+// coalesced), stages the item's window (1056 bins plus the 66-bin reach of
+// one block) in its own shared-memory region and runs the block's remaining
+// steps in the bank's lane layout.  Where every window of the item lies in
+// the series and each lane lies in one of two segments, a step costs the
+// adds, the lane maximum from its group maxima and one warp max-reduction
+// compared with T_w; only a maximum that passes takes the per-segment merge
+// (the leader's bin search and the slot reduction of the dump mode's lean
+// merge).  Other items take the general exact steps.
+constexpr int kDwWarps = 4;                               // items per CTA at a time
+constexpr int kDwLoads = (kRegion + 31) / 32;             // window loads per lane
+
+template <bool kTwo>
+__device__ __forceinline__ void defer_lean_steps(float (&s)[kR], const float *__restrict__ lane_win,
+                                                 const LaneCtx &c, int64_t X0, int bl, int wf, int c0, int c1,
+                                                 const float *__restrict__ thr, int lane) {
+  for (int cc = c0; cc < c1; ++cc) {
+    const float *pw = lane_win + (cc - c0);
+#pragma unroll
+    for (int i = 0; i < kR; ++i) s[i] += pw[i];
+    const int w = wf + cc;
+    const float T = __ldg(thr + (w - 1));
+    float g[kGroups], t[3];
+    const float M = lane_max33(s, g, t);
+    if (!kTwo) {
+      lean_emit<true>(s, g, t, M, 0, kR, c, X0, w - 1, lane, T);
+      continue;
+    }
+    // nothing reaches T anywhere in the slice: no part can pass
+    const uint32_t any = __reduce_max_sync(kFull, M >= 0.0f ? __float_as_uint(M) : 0u);
+    if (!(__uint_as_float(any) >= T)) continue;
+    const bool inA = c.seg_a == X0;
+    float vA = inA ? M : -1.0f, vB = inA ? -1.0f : M;
+    int ea = kR, ib = 0;
+    if (lane == bl) {
+      split_max(s, c.ib, vA, vB);
+      ea = c.ib;
+      ib = c.ib;
+    }
+    lean_emit<true>(s, g, t, vA, 0, ea, c, X0, w - 1, lane, T);
+    lean_emit<true>(s, g, t, vB, ib, kR, c, X0 + 1, w - 1, lane, T);
+  }
+}
+
+__global__ void __launch_bounds__(32 * kDwWarps) deferred_warp_kernel(
+    const float *__restrict__ power, const SeriesDev *__restrict__ series, const int64_t *__restrict__ tile_off,
+    int n_series, int W, int seg_len, const float *__restrict__ thr_all, unsigned long long *__restrict__ slots,
+    uint32_t *__restrict__ dirty, const uint32_t *__restrict__ counters,
+    const unsigned long long *__restrict__ items, const float *__restrict__ snaps, uint32_t item_cap,
+    int tile_bins, const float2 *__restrict__ spec, const float4 *__restrict__ norm) {
+  __shared__ float region_all[kDwWarps][kRegion];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *region = region_all[warp];
+  const uint32_t n_items = min(counters[0], item_cap);
+  for (uint32_t it = blockIdx.x * kDwWarps + warp; it < n_items; it += gridDim.x * kDwWarps) {
+    const unsigned long long item = items[it];
+    const int64_t tile = static_cast<int64_t>(item & 0xffffffffffull);
+    const int wv = static_cast<int>((item >> 40) & 7ull);
+    const int bi = static_cast<int>((item >> 43) & 0x1fffull);
+    const int cx = static_cast<int>((item >> 56) & 0xffull);
+    const int si = series_of_tile(tile_off, n_series, tile);
+    const SeriesDev S = series[si];
+    const int64_t t0 = (tile - S.tile_off) * static_cast<int64_t>(tile_bins);
+    const int64_t k0s = t0 + wv * (32 * kR);            // first start bin of the slice
+    const int64_t r0 = k0s + bi * kR + cx;              // first bin of the staged window
+    const int nsteps = min(kR, W - bi * kR);
+    const int wf = bi * kR + 1;
+    // every load of the item issued before any is used
+    const float *sp = snaps + static_cast<size_t>(it) * (kR * 32) + lane;
+    float s[kR], ld[kDwLoads];
+#pragma unroll
+    for (int i = 0; i < kR; ++i) s[i] = sp[i * 32];
+    const float *src = power + S.p_off;
+    if (norm == nullptr) {
+#pragma unroll
+      for (int q = 0; q < kDwLoads; ++q) {
+        const int j = lane + 32 * q;
+        ld[q] = (j < kRegion && r0 + j < S.m) ? __ldg(src + r0 + j) : 0.0f;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kDwLoads; ++q) {
+        const int j = lane + 32 * q;
+        ld[q] = (j < kRegion && r0 + j < S.m) ? fused_power(spec, norm, S, r0 + j, seg_len) : 0.0f;
+      }
+    }
+    __syncwarp();   // the previous item's reads of the region are done
+#pragma unroll
+    for (int q = 0; q < kDwLoads; ++q) {
+      const int j = lane + 32 * q;
+      if (j < kRegion) region[j] = ld[q];
+    }
+    __syncwarp();
+    const LaneCtx c = lane_ctx(S, t0, tile_bins, wv, lane, W, seg_len, slots, dirty);
+    const float *thr = thr_all + static_cast<int64_t>(si) * W;
+    const float *lane_win = region + lane * kR;       // bin i at step cc: lane_win[cc - cx + i]
+    const int64_t X0 = __shfl_sync(kFull, c.seg_a, 0);
+    const bool two = __all_sync(kFull, c.seg_a == X0 || (c.seg_a == X0 + 1 && c.ib == kR));
+    // every bin of the slice has its whole window at the block's last width
+    const bool all_valid = S.m + 1 - k0s - (wf + nsteps - 1) >= 32 * kR;
+    if (two && all_valid) {
+      const bool split = __any_sync(kFull, c.seg_a != X0 || c.ib < kR);
+      const int bl = __ffs(static_cast<int>(__ballot_sync(kFull, c.ib < kR))) - 1;
+      if (split) defer_lean_steps<true>(s, lane_win, c, X0, bl, wf, cx, nsteps, thr, lane);
+      else defer_lean_steps<false>(s, lane_win, c, X0, bl, wf, cx, nsteps, thr, lane);
+    } else {
+      exact_steps<true>(s, lane_win, wf, cx, nsteps, thr, c, bi * kR + cx);
+    }
+  }
+}
+
 // Deferred blocks when segments are shorter than 66 bins (a lane's 33 bins
 // may then reach a third segment, and every bin is merged on its own; only
 // tiny test shapes): one warp per item with all 33 sums.
@@ -1256,7 +1374,11 @@ int launch_deferred(pulscan_plan p, const float *d_power, cudaStream_t s, const 
   const uint32_t cap = static_cast<uint32_t>(p->item_cap);
   const float2 *spec = reinterpret_cast<const float2 *>(d_spec);
   const float4 *norm = d_spec ? reinterpret_cast<const float4 *>(p->d_norm) : nullptr;
-  if (p->seg_len >= 2 * kR)
+  if (p->seg_len >= 2 * kR && p->defer_form == 1)
+    deferred_warp_kernel<<<p->defer_grid_warp, 32 * kDwWarps, 0, s>>>(
+        d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
+        p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins, spec, norm);
+  else if (p->seg_len >= 2 * kR)
     deferred_kernel<<<p->defer_grid, kDeferThreads, 0, s>>>(
         d_power, p->d_series, p->d_tile_off, static_cast<int>(p->series.size()), p->z_max, p->seg_len,
         p->d_thresh, p->d_slots, p->d_dirty, p->d_counters, p->d_items, p->d_snaps, cap, tile_bins, spec, norm);

@@ -175,7 +175,9 @@ struct pulscan_plan_s {
   float *d_snaps = nullptr;        // their running-sum snapshots (33 x 32 floats each)
   int64_t item_cap = 0;           // deferred items in use (<= alloc_item_cap)
   int64_t alloc_item_cap = 0;
-  int defer_grid = 1;
+  int defer_grid = 1;          // CTAs of the three-warp-per-item deferred kernel (and of the short-segment one)
+  int defer_grid_warp = 1;     // CTAs of the one-warp-per-item deferred kernel
+  int defer_form = 0;          // deferred blocks: 0 = three warps per item, 1 = one warp per item
   pulscan_cand *d_cands = nullptr;
   // device buffers owned by the plan for pulscan_search_host
   float *own_x = nullptr, *own_spec = nullptr, *own_power = nullptr;

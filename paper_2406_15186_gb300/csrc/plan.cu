@@ -387,7 +387,13 @@ static int build_plan(pulscan_plan *out, const int64_t *lengths, int32_t n_serie
   const int64_t nb = (z_max + kR - 1) / kR;
   p->item_cap = std::min<int64_t>(total_warps * nb, 65536);
   p->alloc_item_cap = p->item_cap;
-  p->defer_grid = 8 * n_sm;   // 3-warp CTAs, one item each at a time: 24 warps per SM
+  p->defer_grid = 8 * n_sm;        // 3-warp CTAs, one item each at a time: 24 warps per SM
+  p->defer_grid_warp = 4 * n_sm;   // 4-warp CTAs, one item per warp: 16 warps per SM
+  // one warp per item wins when the items fill the GPU several times over
+  // (a 2^27-sample series: 0.19 against 0.31 ms), three warps per item when
+  // few items leave the per-item step chain exposed (2^23: 33 against 23 us);
+  // the autotuner times both on the caller's data
+  p->defer_form = pw >= (int64_t(1) << 25) ? 1 : 0;
   p->searched.assign(z_max, 1);
   for (auto &s : p->series) p->n_trials.push_back(static_cast<double>(s.m) * z_max);
   compute_thresholds(p);
@@ -613,10 +619,37 @@ int pulscan_plan_autotune(pulscan_plan p, const float *d_power, pulscan_stream s
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   p->persist_mode = best_m;
   const int rc2 = relayout_tiles(p, best_w, best_g);
+  // then the deferred blocks' form, on the chosen launch shape
+  float best_f = INFINITY;
+  int form = p->defer_form;
+  for (int f = 0; f < 2 && !rc && !rc2; ++f) {
+    p->defer_form = f;
+    rc = search_impl(p, d_power, s);
+    float tot = 0.0f;
+    for (int r = 0; r < 3 && !rc; ++r) {
+      cudaEventRecord(e0, s);
+      rc = search_impl(p, d_power, s);
+      cudaEventRecord(e1, s);
+      float ms = 0.0f;
+      if (!rc && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        tot += ms;
+      else if (!rc)
+        rc = fail(PULSCAN_ERR_CUDA, "event timing failed");
+    }
+    if (!rc && tot < best_f) {
+      best_f = tot;
+      form = f;
+    }
+  }
+  p->defer_form = form;
+  if (p->graph.exec) {   // a graph captured before holds the other form's kernel
+    cudaGraphExecDestroy(p->graph.exec);
+    p->graph.exec = nullptr;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   PS_CUDA(cudaMemsetAsync(p->d_counters, 0, (4 + static_cast<size_t>(p->n_ranges)) * sizeof(uint32_t), s));
   PS_CUDA(cudaStreamSynchronize(s));
   p->timing = timing;
@@ -1010,12 +1043,30 @@ int pulscan_plan_set_defer_capacity(pulscan_plan p, int64_t cap) {
     p->d_items = items;
     p->d_snaps = snaps;
     p->alloc_item_cap = cap;
-    if (p->graph.exec) {
-      cudaGraphExecDestroy(p->graph.exec);
-      p->graph.exec = nullptr;
-    }
+  }
+  // the captured graph holds the old list and capacity in its launches
+  if (p->graph.exec && cap != p->item_cap) {
+    cudaGraphExecDestroy(p->graph.exec);
+    p->graph.exec = nullptr;
   }
   p->item_cap = cap;
+  return PULSCAN_OK;
+}
+
+int pulscan_plan_set_defer_form(pulscan_plan p, int32_t form) {
+  if (!p) return fail(PULSCAN_ERR_INVALID_ARG, "null plan");
+  if (form != 0 && form != 1) return fail(PULSCAN_ERR_INVALID_ARG, "form must be 0 or 1");
+  if (p->graph.exec && form != p->defer_form) {   // the captured graph launches the other kernel
+    cudaGraphExecDestroy(p->graph.exec);
+    p->graph.exec = nullptr;
+  }
+  p->defer_form = form;
+  return PULSCAN_OK;
+}
+
+int pulscan_plan_defer_form(pulscan_plan p, int32_t *form) {
+  if (!p || !form) return fail(PULSCAN_ERR_INVALID_ARG, "null argument");
+  *form = p->defer_form;
   return PULSCAN_OK;
 }
 

@@ -71,6 +71,9 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     assert lib.pulscan_plan_set_pipeline(None, 1 << 26) == -1
     assert lib.pulscan_plan_pipeline_parts(None, ctypes.byref(n_out)) == -1
     assert lib.pulscan_plan_set_fused(None, 1) == -1
+    assert lib.pulscan_plan_set_defer_form(None, 1) == -1
+    f32 = ctypes.c_int32(0)
+    assert lib.pulscan_plan_defer_form(None, ctypes.byref(f32)) == -1
     t = ctypes.c_float(0.0)
     assert lib.pulscan_threshold_power(0.0, 1.0e6, 6.0, ctypes.byref(t)) == -1
     assert lib.pulscan_version() >= 10000

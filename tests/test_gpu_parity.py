@@ -254,19 +254,39 @@ def test_fused_search_matches_separate_stages(pkg, lengths, w_max, seg_len, sigm
                                 parity.n_trials_of(m, w_max), series=i)
 
 
-def test_deferred_overflow_falls_back_to_inline_exact(pkg):
-    """With no room for deferred blocks every flagged block is inspected by its own warp."""
-    n, w_max, seg_len, sigma = 1 << 16, 100, 1024, 3.0
+@pytest.mark.parametrize("n,w_max,seg_len,sigma", [
+    (1 << 16, 100, 1024, 3.0),
+    (3 * (1 << 12) + 10, 130, 1000, 3.0),
+    (1 << 17, 300, 4096, 3.0),
+])
+@pytest.mark.parametrize("tiling", [(2, 0, 0), (4, 0, 1)])
+def test_deferred_forms_and_inline_exact_agree(pkg, n, w_max, seg_len, sigma, tiling):
+    """The deferred blocks inspected by three warps per block, by one warp per
+    block (through a captured graph too), and with no room for deferred
+    blocks (every flagged block inspected inline by its own warp): the same
+    records bit for bit, and the oracle's."""
     x = _series(n, seed=9)
     plan = pkg.Plan(n=n, z_max=w_max, segment_len=seg_len, threshold_sigma=sigma)
-    a = parity.run_gpu(plan, x, maxima=False)
-    deferred = plan.counters()[0]
+    plan.set_tiling(*tiling)
+    outs = []
+    for form in (0, 1):
+        plan.set_defer_form(form)
+        assert plan.defer_form() == form
+        outs.append(parity.run_gpu(plan, x, maxima=(form == 0)))
+        deferred = plan.counters()[0]
+        assert deferred > 0
+        outs.append(parity.run_gpu(plan, x, maxima=False, use_graph=True))
     plan.set_defer_capacity(0)
-    b = parity.run_gpu(plan, x, maxima=False)
-    assert deferred > 0 and plan.counters()[0] >= deferred
-    ka = np.sort(a["cands"], order=["series", "bin", "width"])
-    kb = np.sort(b["cands"], order=["series", "bin", "width"])
-    assert np.array_equal(ka, kb)
+    outs.append(parity.run_gpu(plan, x, maxima=False))
+    assert plan.counters()[0] >= deferred
+    keys = [np.sort(o["cands"], order=["series", "bin", "width"]) for o in outs]
+    for k in keys[1:]:
+        assert np.array_equal(keys[0], k)
+    m = n // 2 + 1
+    p64 = outs[0]["power"][:m].astype(np.float64)
+    mx_ref, am_ref = parity.check_maxima(p64, outs[0]["mx"], outs[0]["am"], w_max, seg_len)
+    parity.check_candidates(outs[0]["cands"], p64, mx_ref, am_ref, w_max, seg_len, sigma,
+                            parity.n_trials_of(m, w_max))
 
 
 def test_plans_of_different_sizes_coexist(pkg):
@@ -420,15 +440,18 @@ def test_segment_maxima_exact_ties(pkg, n, w_max, seg_len, tiling):
     # inline exact steps): every record's power and bin exactly the oracle's
     q = rng.choice(np.arange(6, dtype=np.float32), size=m)
     d_power[:m] = torch.from_numpy(q)
-    plan.boxcar_search(d_power)
-    cands = plan.candidates()
     q64 = q.astype(np.float64)
     mq, aq = obox.segment_maxima(q64, w_max, seg_len)
-    assert parity.check_candidates(cands, q64, mq, aq, w_max, seg_len, 3.0, parity.n_trials_of(m, w_max)) > 0
-    seg = np.minimum(cands["bin"].astype(np.int64) // seg_len, mq.shape[0] - 1)
-    wi = cands["width"].astype(np.int64) - 1
-    assert np.array_equal(cands["power"].astype(np.float64), mq[seg, wi])
-    assert np.array_equal(cands["bin"].astype(np.int64), aq[seg, wi])
+    for form in (0, 1):
+        plan.set_defer_form(form)
+        plan.boxcar_search(d_power)
+        cands = plan.candidates()
+        assert parity.check_candidates(cands, q64, mq, aq, w_max, seg_len, 3.0,
+                                       parity.n_trials_of(m, w_max)) > 0
+        seg = np.minimum(cands["bin"].astype(np.int64) // seg_len, mq.shape[0] - 1)
+        wi = cands["width"].astype(np.int64) - 1
+        assert np.array_equal(cands["power"].astype(np.float64), mq[seg, wi])
+        assert np.array_equal(cands["bin"].astype(np.int64), aq[seg, wi])
     plan.close()
 
 

@@ -222,7 +222,8 @@ def test_fused_search_matches_separate_stages(pkg, lengths, w_max, seg_len, sigm
     """The fused search (block statistics, then P formed from the spectrum in
     the bank and the deferred blocks) gives exactly the records of the
     separate stages, with and without a graph; those records match the
-    oracle on the separate stages' power.  Shapes: scalar and packed banks,
+    oracle on the separate stages' power, with either form of the deferred
+    blocks.  Shapes: scalar and packed banks,
     persistent tiles, an odd segment length, a batch of uneven lengths and
     segments shorter than a deferred block's reach (the small deferred kernel)."""
     xs = [_series(n, seed=400 + i) for i, n in enumerate(lengths)]
@@ -235,15 +236,17 @@ def test_fused_search_matches_separate_stages(pkg, lengths, w_max, seg_len, sigm
     sep = parity.run_gpu(plan, x_all, maxima=True)
     key = ["series", "bin", "width"]
     plan.set_fused(1)
-    for use_graph in (False, True):
-        d_x, d_spec, d_power = plan.buffers("cuda")
-        d_x.copy_(torch.from_numpy(x_all))
-        d_power.fill_(-1.0)
-        plan.search(d_x, d_spec, d_power, use_graph=use_graph)
-        fused = plan.candidates()
-        assert float(d_power.max()) == -1.0   # P never written
-        assert len(fused) == len(sep["cands"]) and len(fused) > 0
-        assert np.array_equal(np.sort(fused, order=key), np.sort(sep["cands"], order=key))
+    for form in (0, 1):   # both forms of the deferred blocks form P themselves
+        plan.set_defer_form(form)
+        for use_graph in (False, True):
+            d_x, d_spec, d_power = plan.buffers("cuda")
+            d_x.copy_(torch.from_numpy(x_all))
+            d_power.fill_(-1.0)
+            plan.search(d_x, d_spec, d_power, use_graph=use_graph)
+            fused = plan.candidates()
+            assert float(d_power.max()) == -1.0   # P never written
+            assert len(fused) == len(sep["cands"]) and len(fused) > 0
+            assert np.array_equal(np.sort(fused, order=key), np.sort(sep["cands"], order=key))
     plan.set_fused(0)
     for i, n in enumerate(lengths):
         m = n // 2 + 1

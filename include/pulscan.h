@@ -440,7 +440,9 @@ PULSCAN_API int pulscan_plan_set_defer_capacity(pulscan_plan plan, int64_t cap);
  * the faster.  Drops the plan's captured graph when the form changes.
  * Errors: INVALID_ARG (null plan, form not 0 or 1). */
 PULSCAN_API int pulscan_plan_set_defer_form(pulscan_plan plan, int32_t form);
-/* The current form of pulscan_plan_set_defer_form in *form. */
+/* The current form of pulscan_plan_set_defer_form (0 or 1) in *form (host
+ * memory, written only on success).  Errors: INVALID_ARG (null plan or
+ * form). */
 PULSCAN_API int pulscan_plan_defer_form(pulscan_plan plan, int32_t *form);
 
 /* The FP32 add rate of the current GPU, the ceiling of the boxcar bank

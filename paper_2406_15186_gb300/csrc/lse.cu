@@ -394,11 +394,11 @@ __device__ __forceinline__ SegLim seg_lim(const SegTile &t) {
 // in tile a and j - 3 in tile b; this
 // lane holds those of step `lane` in mk[0] and lane 0 also those of step 32
 // in mk[1], zero where the lane owns no step); then their windows (11 per
-// event) are worked off a lane per event, in rounds of at most kEvCap events.
-// Collecting a block's events first gives the window work the whole
-// block's parallelism instead of one width's.  evl: the warp's list
-// (kEvCap entries).  f(c, k, w, hi, lo) is called for every window whose
-// exact sum lies above thr(c) (S = hi + lo, k the segment-local start bin).
+// event) are worked off a thread per event (block_events_cta), in rounds of
+// at most kEvCap events per warp of the CTA.  Collecting a block's events
+// first gives the window work the whole block's parallelism instead of one
+// width's.  f(c, k, w, hi, lo) is called for every window whose exact sum
+// lies above thr(c) (S = hi + lo, k the segment-local start bin).
 constexpr int kEvCap = 128;
 
 // One event (step c, lane l, group jg, warp wv: c | l << 6 | jg << 11 | wv << 14):
@@ -436,7 +436,7 @@ __device__ __forceinline__ void work_event(int ev, const SegLim &sl, int wf, Thr
   }
 }
 
-// This lane's events of the block (see block_events) written to evl[pos -
+// This lane's events of the block (see block_events_cta) written to evl[pos -
 // base] for list positions pos in [base, base + cap), from position `first` on.
 template <int NG>
 __device__ __forceinline__ void write_events(const uint32_t (&mk)[2][NG], int warp, int lane, int first, int base,
@@ -460,29 +460,6 @@ __device__ __forceinline__ uint32_t count_events(const uint32_t (&mk)[2][NG]) {
 #pragma unroll
   for (int j = 0; j < NG; ++j) cnt += __popc(mk[0][j]) + __popc(mk[1][j]);
   return cnt;
-}
-
-template <class Thr, class F, int NG>
-__device__ __forceinline__ void block_events(const SegLim &sl, int warp, int lane, int wf, const uint32_t (&mk)[2][NG],
-                                             Thr thr, const float *__restrict__ fh, const __half *__restrict__ fl,
-                                             int *evl, float margin, F &&f) {
-  const uint32_t cnt = count_events(mk);
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t u = __shfl_up_sync(kFullMask, incl, o);
-    if (lane >= o) incl += u;
-  }
-  const int n_ev = static_cast<int>(__shfl_sync(kFullMask, incl, 31));
-  const int first = static_cast<int>(incl - cnt);   // this lane's events are [first, incl)
-  for (int base = 0; base < n_ev; base += kEvCap) {
-    __syncwarp();
-    write_events(mk, warp, lane, first, base, kEvCap, evl);
-    __syncwarp();
-    const int n_round = min(kEvCap, n_ev - base);
-    for (int e = lane; e < n_round; e += 32) work_event<NG>(evl[e], sl, wf, thr, fh, fl, margin, f);
-  }
-  __syncwarp();
 }
 
 // The CTA's events of the block worked off by all its threads: the warp
